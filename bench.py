@@ -1,0 +1,357 @@
+"""Benchmark of the MLS projection hot path on one or more GPUs.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Workload: 2,000,000-point torus (R = 1, r = 0.3, normal noise 0.005, 1 %
+uniform outliers), k = 32, degree-2 polynomial, mixed precision.  One step is
+one pass of the whole hot path over the cloud: grid build, exact kNN and the
+MLS projection (through the C ABI of libmls, inputs resident in HBM).  L2 is
+flushed (a 256 MB write) before every timed step, outside the timed events.
+
+With N > 1 (torchrun) every rank projects its own cloud (seed 2 + rank): the
+points are independent problems, so there is no data-path collective; the
+step time is the maximum over ranks.  `--impl reference` times the FP64 CPU
+oracle on the host cores instead (rank 0 only).
+
+Prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MLS-projected points/sec at k=32 (fwd and fwd+bwd), % FP32 roofline, vs plain FP64"
+WORKLOAD = ("torus2m_k32: 2,000,000 points on a torus (R=1, r=0.3) with normal noise sigma=0.005 "
+            "and 1% uniform outliers in its bounding box; k=32, Gaussian h = 2 x mean kNN distance, "
+            "degree-2 polynomial, FP32 moments with FP64 eigen/6x6 solves where ill-conditioned")
+N_POINTS = 2_000_000
+K = 32
+
+# Algorithmic work per point: flops of the degree-2
+# projection as the oracle's operation list counts them, and the minimal HBM
+# bytes of the kNN (read the point, write its k indices).
+FLOPS_PER_NEIGHBOUR = 97
+FLOPS_PER_POINT = 645
+KNN_BYTES_PER_POINT = 16 + 4 * K
+PROJECT_BYTES_PER_POINT = 12 + 4 * K + 12 + 12 + 1
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    peaks = {"hbm_gbs": 6800.0, "source": "fallback"}
+    if os.path.exists(path):
+        with open(path) as f:
+            p = json.load(f)
+        peaks.update(p)
+        peaks["source"] = "measured"
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    # FP32: 152 SMs x 128 lanes x 2 flops (FMA) x max SM clock
+    peaks["fp32_tflops"] = 152 * 128 * 2 * sm_max * 1e6 / 1e12
+    return peaks
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower() in ("active", "1"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": mx, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2401_03365_gb300 import build, capi, workloads
+
+    world, rank, local = dist_setup(args)
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    build.build()
+    dev = torch.device("cuda", local)
+    cloud = workloads.torus(n=N_POINTS, seed=2 + rank, k=K)
+    x = torch.from_numpy(cloud.xyz).to(dev)
+    stream = torch.cuda.current_stream()
+
+    idx = torch.empty((N_POINTS, K), dtype=torch.int32, device=dev)
+    out_xyz = torch.empty_like(x)
+    out_n = torch.empty_like(x)
+    out_st = torch.empty(N_POINTS, dtype=torch.uint8, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    # bandwidth of the workload: 2 x mean kNN distance, from the GPU kNN
+    grid = capi.mls_build_grid(x, 0.0, K)
+    capi.mls_knn(grid, K, out_idx=idx)
+    h = 2.0 * float(capi.mls_mean_knn_dist(x, idx).item())
+
+    def step(ev=None):
+        nonlocal grid
+        if ev: ev[0].record(stream)
+        grid = capi.mls_build_grid(x, 0.0, K, grid=grid)
+        if ev: ev[1].record(stream)
+        capi.mls_knn(grid, K, out_idx=idx)
+        if ev: ev[2].record(stream)
+        capi.mls_project(x, idx, h, 2, "mixed", order=capi.mls_grid_order(grid), out_xyz=out_xyz,
+                         out_normal=out_n, out_status=out_st)
+        if ev: ev[3].record(stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    events = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+    launches0 = capi.mls_kernel_launches()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clocks:
+        t0 = time.perf_counter()
+        for s in range(args.steps):
+            flush.zero_()
+            step(events[s])
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+    if world > 1:
+        dist.barrier()
+    launches = capi.mls_kernel_launches() - launches0
+    stage = np.array([[e[i].elapsed_time(e[i + 1]) for i in range(3)] for e in events])  # ms
+    step_ms = float(stage.sum(1).mean())
+    t_max = torch.tensor([step_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
+    step_ms_max = float(t_max.item())
+    value = world * N_POINTS / (step_ms_max * 1e-3)
+
+    # end to end through the public API with host buffers: H2D of the points,
+    # the three calls, D2H of positions, normals and status, every step
+    host_in = torch.from_numpy(cloud.xyz).pin_memory()
+    host_xyz = torch.empty((N_POINTS, 3), dtype=torch.float32).pin_memory()
+    host_n = torch.empty((N_POINTS, 3), dtype=torch.float32).pin_memory()
+    host_st = torch.empty(N_POINTS, dtype=torch.uint8).pin_memory()
+    x_e2e = torch.empty_like(x)
+    e2e_steps = max(3, min(args.steps, 10))
+    e2e_ms = []
+    for s in range(e2e_steps + 1):
+        flush.zero_()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        x_e2e.copy_(host_in, non_blocking=True)
+        grid = capi.mls_build_grid(x_e2e, 0.0, K, grid=grid)
+        capi.mls_knn(grid, K, out_idx=idx)
+        capi.mls_project(x_e2e, idx, h, 2, "mixed", order=capi.mls_grid_order(grid), out_xyz=out_xyz,
+                         out_normal=out_n, out_status=out_st)
+        host_xyz.copy_(out_xyz, non_blocking=True)
+        host_n.copy_(out_n, non_blocking=True)
+        host_st.copy_(out_st, non_blocking=True)
+        b.record(stream)
+        b.synchronize()
+        if s > 0:                      # the first is a warm-up of the copy path
+            e2e_ms.append(a.elapsed_time(b))
+    e2e_t = torch.tensor([float(np.mean(e2e_ms))], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
+    e2e_value = world * N_POINTS / (float(e2e_t.item()) * 1e-3)
+
+    grid.close()
+    if rank != 0:
+        if world > 1:
+            dist.barrier()
+            dist.destroy_process_group()
+        return None
+
+    peaks = load_peaks()
+    knn_ms, proj_ms, build_ms = float(stage[:, 1].mean()), float(stage[:, 2].mean()), float(stage[:, 0].mean())
+    proj_flops = N_POINTS * (FLOPS_PER_NEIGHBOUR * K + FLOPS_PER_POINT)
+    kernels = {
+        "grid_build": {"ms": build_ms, "launches_per_step": 34},
+        "knn": {"ms": knn_ms, "bound": "hbm", "achieved_gbs": N_POINTS * KNN_BYTES_PER_POINT / (knn_ms * 1e-3) / 1e9},
+        "project": {"ms": proj_ms, "bound": "alu",
+                    "achieved_tflops": proj_flops / (proj_ms * 1e-3) / 1e12,
+                    "frac": proj_flops / (proj_ms * 1e-3) / 1e12 / peaks["fp32_tflops"]},
+    }
+    dominant = max(("grid_build", build_ms), ("knn", knn_ms), ("project", proj_ms), key=lambda t: t[1])[0]
+    if dominant == "project":
+        ach = kernels["project"]["achieved_tflops"]
+        roofline = {"kernel": "k_project (mixed, degree 2)", "bound": "alu", "achieved": ach,
+                    "peak": peaks["fp32_tflops"], "unit": "TFLOP/s", "frac": ach / peaks["fp32_tflops"],
+                    "traffic": None, "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 x max SM clock"}
+    else:
+        name = "k_knn" if dominant == "knn" else "grid build"
+        ms = knn_ms if dominant == "knn" else build_ms
+        ach = N_POINTS * KNN_BYTES_PER_POINT / (ms * 1e-3) / 1e9
+        roofline = {"kernel": name, "bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                    "frac": ach / peaks["hbm_gbs"], "traffic": None,
+                    "peak_source": f"{peaks['source']} hbm_gbs (copy)"}
+    line = {
+        "metric": METRIC,
+        "value": value,
+        "unit": "points/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": step_ms_max,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "points_per_gpu": N_POINTS, "k": K, "degree": 2, "precision": "mixed",
+                   "h": h, "step": "grid build + exact kNN + MLS projection (forward)",
+                   "l2": "flushed before every step (256 MB write, outside the timed events)",
+                   "parallelism": f"independent clouds per GPU x{world}"},
+        "roofline": roofline,
+        "kernels": kernels,
+        "e2e": {"value": e2e_value, "unit": "points/s", "h2d_bytes_per_step": N_POINTS * 12,
+                "d2h_bytes_per_step": N_POINTS * (12 + 12 + 1)},
+        "gpu_launches": int(launches),
+        "clocks": clocks.summary(),
+        "wall_s_timed_region": wall,
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(cloud.xyz, h, args.cpu_sample)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return line
+
+
+def cpu_baseline(xyz, h, sample):
+    """The FP64 oracle as it stands, single-threaded on this host: k-d tree over
+    the whole cloud, then kNN + projection of a seeded sample of points; the
+    per-point time is extrapolated to the full cloud."""
+    import oracle
+    n = xyz.shape[0]
+    rng = np.random.default_rng(123)
+    q = np.sort(rng.choice(n, sample, replace=False))
+    t0 = time.perf_counter()
+    oracle.knn_kdtree(xyz, K, queries=np.zeros(0, np.int64))
+    t_build = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    rows, _ = oracle.knn_kdtree(xyz, K, queries=q)
+    oracle.project(xyz, rows, h, 2, queries=q)
+    t_sample = time.perf_counter() - t0 - t_build
+    t_full = t_build + t_sample * n / sample
+    return {"value": n / t_full, "unit": "points/s", "cores": 1, "kind": "oracle",
+            "sample": (f"k-d tree build over all {n} points ({t_build:.2f} s) + kNN and FP64 projection of a "
+                       f"seeded sample of {sample} points ({t_sample:.2f} s), extrapolated to the full cloud"),
+            "seconds": t_build + t_sample}
+
+
+def run_reference(args):
+    world, rank, local = dist_setup(args)
+    if rank != 0:
+        return None
+    from paper_2401_03365_gb300 import workloads
+    cloud = workloads.torus(n=N_POINTS, seed=2, k=K)
+    import oracle
+    # the bandwidth as the oracle defines it, from a seeded sample of its rows
+    rng = np.random.default_rng(5)
+    q = np.sort(rng.choice(N_POINTS, 20_000, replace=False))
+    rows, _ = oracle.knn_kdtree(cloud.xyz, K, queries=q)
+    x = cloud.xyz.astype(np.float64)
+    d = np.linalg.norm(x[rows] - x[q][:, None, :], axis=2)
+    h = float(np.float32(2.0 * d[rows != q[:, None]].mean()))
+    for _ in range(args.warmup):
+        cpu_baseline(cloud.xyz, h, 2_000)
+    times = []
+    info = None
+    for _ in range(args.steps):
+        info = cpu_baseline(cloud.xyz, h, args.cpu_sample)
+        times.append(N_POINTS / info["value"])
+    step_s = float(np.mean(times))
+    value = N_POINTS / step_s
+    return {
+        "metric": METRIC, "impl": "reference", "value": value, "unit": "points/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_s * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "points_per_gpu": N_POINTS, "k": K, "degree": 2,
+                   "step": "oracle: k-d tree + kNN + FP64 projection, sampled and extrapolated"},
+        "cpu_baseline": {"value": value, "unit": "points/s", "cores": 1, "kind": "oracle", "sample": info["sample"]},
+        "e2e": {"value": value, "unit": "points/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "gpu_launches": 0,
+    }
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--cpu-sample", type=int, default=50_000)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)     # at least three untimed warm-up steps
+    line = run_reference(args) if args.impl == "reference" else run_ours(args)
+    if line is not None:
+        print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

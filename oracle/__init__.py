@@ -102,10 +102,14 @@ def knn_brute(xyz, k):
 
 
 def knn_kdtree(xyz, k, queries=None):
+    """Rows for all points, or for the listed queries (an empty list only
+    builds the tree)."""
     xyz = _xyz(xyz)
     n = xyz.shape[0]
     q = None if queries is None else np.ascontiguousarray(queries, np.int64)
     m = n if q is None else q.shape[0]
+    if q is not None and m == 0:
+        q = np.zeros(1, np.int64)          # a valid pointer with nq = 0
     idx = np.empty((m, k), np.int32)
     key = np.empty((m, k), np.float32)
     rc = _load().oracle_knn_kdtree(_p(xyz, _f32p), n, k, _p(q, _i64p), m, _p(idx, _i32p),
@@ -123,14 +127,17 @@ def mean_knn_dist(xyz, idx):
 
 
 def project(xyz, idx, h, degree=2, queries=None):
-    """Returns (xyz', normal, status, diag) in float64 / uint8; diag columns are
-    (lambda0, lambda1, lambda2, cond of the normal matrix, total weight)."""
+    """Project all points (idx: n rows) or the listed `queries` (idx: one row
+    per query, in the same order).  Returns (xyz', normal, status, diag) in
+    float64 / uint8; diag columns are (lambda0, lambda1, lambda2, cond of the
+    normal matrix, total weight)."""
     xyz = _xyz(xyz)
     idx = np.ascontiguousarray(idx, np.int32)
     n, k = xyz.shape[0], idx.shape[1]
-    assert idx.shape[0] == n
     q = None if queries is None else np.ascontiguousarray(queries, np.int64)
     m = n if q is None else q.shape[0]
+    assert idx.shape[0] == m, "one neighbour row per projected point"
+    assert idx.min() >= 0 and idx.max() < n
     out = np.empty((m, 3), np.float64)
     nrm = np.empty((m, 3), np.float64)
     st = np.empty(m, np.uint8)

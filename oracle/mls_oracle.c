@@ -592,8 +592,9 @@ static void free_state(point_state *st)
     free(st->w);
 }
 
-/* Project the points listed in `queries` (all when NULL) with neighbour rows
- * idx[i*k .. i*k+k).  Row s of each output belongs to queries[s].
+/* Project the points listed in `queries` (all when NULL).  Neighbour rows:
+ * idx holds one row of k indices per projected point, in output order (row s
+ * belongs to queries[s], or to point s when queries is NULL).
  * out_diag (optional, 5 per row): l0, l1, l2, cond(A), W. */
 int oracle_project(const float *xyz, int64_t n, const int32_t *idx, int k, double h, int degree,
                    const int64_t *queries, int64_t nq, double *out_xyz, double *out_normal,
@@ -608,7 +609,7 @@ int oracle_project(const float *xyz, int64_t n, const int32_t *idx, int k, doubl
     int64_t m = queries ? nq : n;
     for (int64_t s = 0; s < m; ++s) {
         int64_t i = queries ? queries[s] : s;
-        project_point(xyz, idx + i * k, k, h, degree, i, &st);
+        project_point(xyz, idx + s * k, k, h, degree, i, &st);
         for (int a = 0; a < 3; ++a) {
             out_xyz[3 * s + a] = st.out[a];
             if (out_normal) out_normal[3 * s + a] = st.nrm[a];

@@ -1,0 +1,229 @@
+"""Thin ctypes binding of libmls (include/mls.h), same names as the C ABI.
+
+Argument marshalling only: torch tensors are checked for device, dtype and
+layout, their device pointers and the current CUDA stream are passed through,
+and negative status codes become MLSError.  Every computation runs in the
+CUDA kernels of libmls; there is no CPU fallback, and loading fails loudly
+when the library has not been built.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+from .build import library_path
+
+__all__ = [
+    "MLSError", "Grid", "lib", "mls_build_grid", "mls_grid_destroy", "mls_grid_size", "mls_grid_order",
+    "mls_knn", "mls_project", "mls_mean_knn_dist", "mls_status_str", "mls_last_error", "mls_kernel_launches",
+    "PRECISION", "MLS_MAX_K", "MLS_PT_OK", "MLS_PT_PLANE_DEGENERATE", "MLS_PT_POLY_SINGULAR",
+    "MLS_PT_FP64_USED", "EXPORTED_SYMBOLS",
+]
+
+MLS_MAX_K = 64
+PRECISION = {"fp32": 0, "mixed": 1, "fp64": 2}
+MLS_PT_OK, MLS_PT_PLANE_DEGENERATE, MLS_PT_POLY_SINGULAR, MLS_PT_FP64_USED = 0, 1, 2, 4
+
+_vp = ctypes.c_void_p
+_i64 = ctypes.c_int64
+_int = ctypes.c_int
+_flt = ctypes.c_float
+
+# (name, restype, argtypes) of every entry point declared in include/mls.h
+_SIGNATURES = [
+    ("mls_build_grid", _int, [_vp, _i64, _flt, _int, _vp, ctypes.POINTER(_vp)]),
+    ("mls_grid_destroy", None, [_vp]),
+    ("mls_grid_size", _i64, [_vp]),
+    ("mls_grid_order", _vp, [_vp]),
+    ("mls_knn", _int, [_vp, _int, _vp, _vp, _vp]),
+    ("mls_project", _int, [_vp, _i64, _vp, _int, _flt, _int, _int, _vp, _vp, _vp, _vp, _vp]),
+    ("mls_mean_knn_dist", _int, [_vp, _i64, _vp, _int, _vp, _vp]),
+    ("mls_kernel_launches", _i64, []),
+    ("mls_last_error", ctypes.c_char_p, []),
+    ("mls_status_str", ctypes.c_char_p, [_int]),
+]
+EXPORTED_SYMBOLS = [s[0] for s in _SIGNATURES]
+
+_lib = None
+
+
+class MLSError(RuntimeError):
+    def __init__(self, fn: str, code: int):
+        self.code = code
+        msg = lib().mls_last_error().decode() or lib().mls_status_str(code).decode()
+        super().__init__(f"{fn} failed ({code}, {lib().mls_status_str(code).decode()}): {msg}")
+
+
+def lib():
+    """The loaded libmls (ctypes.CDLL).  Raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        path = library_path()
+        if not os.path.exists(path):
+            raise ImportError(f"libmls is not built ({path} missing): run "
+                              "`python -c 'import __graft_entry__ as g; g.build()'`")
+        if torch.cuda.is_available():
+            torch.cuda.init()           # one CUDA runtime, shared with torch
+        dll = ctypes.CDLL(path)
+        for name, res, args in _SIGNATURES:
+            fn = getattr(dll, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = dll
+    return _lib
+
+
+def _check(fn, rc):
+    if rc != 0:
+        raise MLSError(fn, rc)
+
+
+def _stream(stream):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _need(t, name, dtype, shape=None):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} must have shape {tuple(shape)}, got {tuple(t.shape)}")
+
+
+def mls_status_str(code: int) -> str:
+    return lib().mls_status_str(code).decode()
+
+
+def mls_last_error() -> str:
+    return lib().mls_last_error().decode()
+
+
+def mls_kernel_launches() -> int:
+    return int(lib().mls_kernel_launches())
+
+
+class Grid:
+    """Owner of an mls_grid handle; keeps the point tensor alive."""
+
+    def __init__(self, handle, xyz):
+        self.handle = handle
+        self.xyz = xyz
+
+    @property
+    def n(self) -> int:
+        return int(lib().mls_grid_size(self.handle))
+
+    def close(self):
+        if self.handle:
+            lib().mls_grid_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def mls_build_grid(xyz: torch.Tensor, cell_size: float = 0.0, k_hint: int = 32, grid: Grid | None = None,
+                   stream=None) -> Grid:
+    _need(xyz, "xyz", torch.float32)
+    if xyz.dim() != 2 or xyz.shape[1] != 3:
+        raise ValueError("xyz must be (n, 3)")
+    h = ctypes.c_void_p(grid.handle if grid is not None else None)
+    rc = lib().mls_build_grid(_ptr(xyz), xyz.shape[0], float(cell_size), int(k_hint), _stream(stream),
+                              ctypes.byref(h))
+    if rc != 0 and grid is not None:
+        grid.xyz = None
+    _check("mls_build_grid", rc)
+    if grid is not None:
+        grid.handle, grid.xyz = h.value, xyz
+        return grid
+    return Grid(h.value, xyz)
+
+
+def mls_grid_destroy(grid: Grid) -> None:
+    grid.close()
+
+
+def mls_grid_size(grid: Grid) -> int:
+    return grid.n
+
+
+class _DeviceArray:
+    """A device buffer owned by libmls, seen through __cuda_array_interface__."""
+
+    def __init__(self, ptr, n, typestr):
+        self.__cuda_array_interface__ = {"shape": (n,), "typestr": typestr, "data": (ptr, True),
+                                         "version": 3, "strides": None}
+
+
+def mls_grid_order(grid: Grid) -> torch.Tensor:
+    """The grid's Morton order (order[s] = point at sorted position s) as an
+    int32 CUDA tensor viewing the grid's own buffer: valid until the grid is
+    rebuilt or destroyed."""
+    p = lib().mls_grid_order(grid.handle)
+    if not p:
+        raise ValueError("mls_grid_order: the grid is empty")
+    return torch.as_tensor(_DeviceArray(p, grid.n, "<i4"), device=grid.xyz.device)
+
+
+def mls_knn(grid: Grid, k: int, with_key: bool = False, out_idx=None, out_key=None, stream=None):
+    n = grid.n
+    dev = grid.xyz.device
+    if out_idx is None:
+        out_idx = torch.empty((n, k), dtype=torch.int32, device=dev)
+    _need(out_idx, "out_idx", torch.int32, (n, k))
+    if with_key and out_key is None:
+        out_key = torch.empty((n, k), dtype=torch.float32, device=dev)
+    if out_key is not None:
+        _need(out_key, "out_key", torch.float32, (n, k))
+    _check("mls_knn", lib().mls_knn(grid.handle, int(k), _ptr(out_idx), _ptr(out_key), _stream(stream)))
+    return out_idx, out_key
+
+
+def mls_project(xyz: torch.Tensor, idx: torch.Tensor, h: float, degree: int = 2, precision: str = "mixed",
+                order: torch.Tensor | None = None, out_xyz=None, out_normal=None, out_status=None,
+                want_normal: bool = True, want_status: bool = True, stream=None):
+    _need(xyz, "xyz", torch.float32)
+    n = xyz.shape[0]
+    _need(idx, "idx", torch.int32)
+    if idx.dim() != 2 or idx.shape[0] != n:
+        raise ValueError("idx must be (n, k)")
+    k = idx.shape[1]
+    if order is not None:
+        _need(order, "order", torch.int32, (n,))
+    if out_xyz is None:
+        out_xyz = torch.empty_like(xyz)
+    _need(out_xyz, "out_xyz", torch.float32, (n, 3))
+    if out_normal is None and want_normal:
+        out_normal = torch.empty_like(xyz)
+    if out_normal is not None:
+        _need(out_normal, "out_normal", torch.float32, (n, 3))
+    if out_status is None and want_status:
+        out_status = torch.empty(n, dtype=torch.uint8, device=xyz.device)
+    if out_status is not None:
+        _need(out_status, "out_status", torch.uint8, (n,))
+    rc = lib().mls_project(_ptr(xyz), n, _ptr(idx), k, float(h), int(degree), PRECISION[precision],
+                           _ptr(order), _ptr(out_xyz), _ptr(out_normal), _ptr(out_status), _stream(stream))
+    _check("mls_project", rc)
+    return out_xyz, out_normal, out_status
+
+
+def mls_mean_knn_dist(xyz: torch.Tensor, idx: torch.Tensor, stream=None) -> torch.Tensor:
+    _need(xyz, "xyz", torch.float32)
+    _need(idx, "idx", torch.int32)
+    out = torch.empty(1, dtype=torch.float64, device=xyz.device)
+    _check("mls_mean_knn_dist", lib().mls_mean_knn_dist(_ptr(xyz), xyz.shape[0], _ptr(idx), idx.shape[1],
+                                                        _ptr(out), _stream(stream)))
+    return out

@@ -1,0 +1,181 @@
+// C ABI of libmls: argument validation, the grid handle, error reporting.
+#include <atomic>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <new>
+
+#include "grid.cuh"
+
+namespace mls {
+
+int build_grid(mls_grid *g, const float *xyz, int64_t n, float cell_size, int k_hint, cudaStream_t st);
+void free_grid_buffers(mls_grid *g);
+int launch_knn(const mls_grid *grid, int k, int32_t *idx, float *key, cudaStream_t st);
+int launch_project(const float *xyz, int64_t n, const int32_t *idx, int k, float h, int degree, int precision,
+                   const int32_t *order, float *out_xyz, float *out_n, uint8_t *status, cudaStream_t st);
+
+namespace {
+thread_local char g_last_error[512] = "";
+std::atomic<int64_t> g_launches{0};
+
+// Mean neighbour distance excluding self, accumulated in FP64.
+__global__ void k_mean_dist(const float *__restrict__ xyz, int64_t n, const int32_t *__restrict__ idx, int k,
+                            double *acc) {
+    double sum = 0.0;
+    unsigned long long cnt = 0;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * k;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = e / k, j = idx[e];
+        if (j == i) continue;
+        double d2 = 0.0;
+        for (int a = 0; a < 3; ++a) {
+            double d = (double)xyz[3 * j + a] - (double)xyz[3 * i + a];
+            d2 += d * d;
+        }
+        sum += sqrt(d2);
+        ++cnt;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        sum += __shfl_xor_sync(0xffffffffu, sum, o);
+        cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(&acc[0], sum);
+        atomicAdd((unsigned long long *)&acc[1], cnt);
+    }
+}
+
+__global__ void k_mean_finish(double *acc, double *out) {
+    unsigned long long cnt = *(unsigned long long *)&acc[1];
+    *out = cnt ? acc[0] / (double)cnt : 0.0;
+}
+
+}  // namespace
+
+void count_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+int set_error(int code, const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_last_error, sizeof g_last_error, fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+}  // namespace mls
+
+using mls::set_error;
+
+extern "C" {
+
+const char *mls_last_error(void) { return mls::g_last_error; }
+
+int64_t mls_kernel_launches(void) { return mls::g_launches.load(std::memory_order_relaxed); }
+
+const char *mls_status_str(int code) {
+    switch (code) {
+        case MLS_OK: return "ok";
+        case MLS_ERR_INVALID_ARG: return "invalid argument";
+        case MLS_ERR_K_TOO_LARGE: return "k too large";
+        case MLS_ERR_UNSUPPORTED_DEGREE: return "unsupported degree";
+        case MLS_ERR_CUDA: return "CUDA error";
+        case MLS_ERR_OOM: return "out of device memory";
+        case MLS_ERR_TIMEOUT: return "device wait timed out";
+        case MLS_ERR_NONFINITE: return "non-finite coordinate";
+        case MLS_ERR_TOO_LARGE: return "too many points";
+        default: return "unknown status";
+    }
+}
+
+int mls_build_grid(const float *d_xyz, int64_t n, float cell_size, int k_hint, mls_stream stream,
+                   mls_grid **inout) {
+    mls::g_last_error[0] = 0;
+    if (!d_xyz || !inout) return set_error(MLS_ERR_INVALID_ARG, "mls_build_grid: null pointer");
+    if (n < 1) return set_error(MLS_ERR_INVALID_ARG, "mls_build_grid: n = %lld < 1", (long long)n);
+    if (n > 0x7fffffffLL) return set_error(MLS_ERR_TOO_LARGE, "mls_build_grid: n = %lld", (long long)n);
+    if (k_hint < 1 || k_hint > MLS_MAX_K)
+        return set_error(MLS_ERR_K_TOO_LARGE, "mls_build_grid: k_hint = %d not in [1, %d]", k_hint, MLS_MAX_K);
+    if (std::isnan(cell_size)) return set_error(MLS_ERR_INVALID_ARG, "mls_build_grid: cell_size is NaN");
+    mls_grid *g = *inout;
+    bool fresh = false;
+    if (!g) {
+        g = new (std::nothrow) mls_grid();
+        if (!g) return set_error(MLS_ERR_OOM, "mls_build_grid: host allocation failed");
+        fresh = true;
+        cudaGetDevice(&g->device);
+    }
+    int rc = mls::build_grid(g, d_xyz, n, cell_size, k_hint, (cudaStream_t)stream);
+    if (rc != MLS_OK) {
+        if (fresh) {
+            mls::free_grid_buffers(g);
+            delete g;
+        } else {
+            g->n = 0;   // unusable until rebuilt
+        }
+        return rc;
+    }
+    *inout = g;
+    return MLS_OK;
+}
+
+void mls_grid_destroy(mls_grid *g) {
+    if (!g) return;
+    if (g->stream) cudaStreamSynchronize(g->stream);
+    mls::free_grid_buffers(g);
+    delete g;
+}
+
+int64_t mls_grid_size(const mls_grid *g) { return g ? g->n : -1; }
+
+const int32_t *mls_grid_order(const mls_grid *g) { return g && g->n > 0 ? g->perm : nullptr; }
+
+int mls_knn(const mls_grid *g, int k, int32_t *d_idx, float *d_key, mls_stream stream) {
+    mls::g_last_error[0] = 0;
+    if (!g || !d_idx) return set_error(MLS_ERR_INVALID_ARG, "mls_knn: null pointer");
+    if (g->n < 1) return set_error(MLS_ERR_INVALID_ARG, "mls_knn: grid is empty (failed build?)");
+    if (k < 1 || k > MLS_MAX_K || k > g->n)
+        return set_error(MLS_ERR_K_TOO_LARGE, "mls_knn: k = %d not in [1, min(%d, n = %lld)]", k, MLS_MAX_K,
+                         (long long)g->n);
+    return mls::launch_knn(g, k, d_idx, d_key, (cudaStream_t)stream);
+}
+
+int mls_project(const float *d_xyz, int64_t n, const int32_t *d_idx, int k, float h, int degree, int precision,
+                const int32_t *d_order, float *d_out_xyz, float *d_out_normal, uint8_t *d_status,
+                mls_stream stream) {
+    mls::g_last_error[0] = 0;
+    if (!d_xyz || !d_idx || !d_out_xyz) return set_error(MLS_ERR_INVALID_ARG, "mls_project: null pointer");
+    if (n < 1) return set_error(MLS_ERR_INVALID_ARG, "mls_project: n = %lld < 1", (long long)n);
+    if (n > 0x7fffffffLL) return set_error(MLS_ERR_TOO_LARGE, "mls_project: n = %lld", (long long)n);
+    if (k < 1 || k > MLS_MAX_K || k > n)
+        return set_error(MLS_ERR_K_TOO_LARGE, "mls_project: k = %d not in [1, min(%d, n)]", k, MLS_MAX_K);
+    if (!(h > 0.0f) || !std::isfinite(h))
+        return set_error(MLS_ERR_INVALID_ARG, "mls_project: h = %g must be finite and > 0", (double)h);
+    if (degree < 0 || degree > 2)
+        return set_error(MLS_ERR_UNSUPPORTED_DEGREE, "mls_project: degree = %d not in {0, 1, 2}", degree);
+    if (precision < MLS_PREC_FP32 || precision > MLS_PREC_FP64)
+        return set_error(MLS_ERR_INVALID_ARG, "mls_project: precision = %d", precision);
+    if ((const void *)d_out_xyz == (const void *)d_xyz)
+        return set_error(MLS_ERR_INVALID_ARG, "mls_project: output aliases the input");
+    return mls::launch_project(d_xyz, n, d_idx, k, h, degree, precision, d_order, d_out_xyz, d_out_normal,
+                               d_status, (cudaStream_t)stream);
+}
+
+int mls_mean_knn_dist(const float *d_xyz, int64_t n, const int32_t *d_idx, int k, double *d_out,
+                      mls_stream stream) {
+    mls::g_last_error[0] = 0;
+    if (!d_xyz || !d_idx || !d_out) return set_error(MLS_ERR_INVALID_ARG, "mls_mean_knn_dist: null pointer");
+    if (n < 1 || k < 1 || k > MLS_MAX_K) return set_error(MLS_ERR_INVALID_ARG, "mls_mean_knn_dist: n or k");
+    cudaStream_t st = (cudaStream_t)stream;
+    double *acc = nullptr;
+    MLS_CUDA_TRY(cudaMallocAsync(&acc, 2 * sizeof(double), st));
+    MLS_CUDA_TRY(cudaMemsetAsync(acc, 0, 2 * sizeof(double), st));
+    mls::k_mean_dist<<<152 * 8, 256, 0, st>>>(d_xyz, n, d_idx, k, acc);
+    mls::k_mean_finish<<<1, 1, 0, st>>>(acc, d_out);
+    mls::count_launches(2);
+    MLS_CUDA_TRY(cudaFreeAsync(acc, st));
+    MLS_CUDA_TRY(cudaGetLastError());
+    return MLS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,88 @@
+// Device helpers shared by the kernels of libmls (sm_103a).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/mls.h"
+
+namespace mls {
+
+constexpr int kWarp = 32;
+constexpr int kMortonBits = 21;                  // bits per axis of a level-0 cell coordinate
+constexpr uint32_t kAxisCells = 1u << kMortonBits;
+constexpr int kMaxLevels = kMortonBits + 1;      // level L: cell side s0 * 2^L, L = 0..21
+
+// Records the thread's last error message; returns `code`.
+int set_error(int code, const char *fmt, ...);
+
+// Adds to the process-wide count of kernel launches.
+void count_launches(int n);
+
+#define MLS_CUDA_TRY(expr)                                                              \
+    do {                                                                                \
+        cudaError_t e_ = (expr);                                                        \
+        if (e_ != cudaSuccess)                                                          \
+            return ::mls::set_error(e_ == cudaErrorMemoryAllocation ? MLS_ERR_OOM       \
+                                                                     : MLS_ERR_CUDA,    \
+                                    "%s: %s (%s:%d)", #expr, cudaGetErrorString(e_),    \
+                                    __FILE__, __LINE__);                                \
+    } while (0)
+
+// Spread the low 21 bits of v so that bit b lands on bit 3b.
+__host__ __device__ inline uint64_t spread3(uint32_t v) {
+    uint64_t x = v & 0x1fffffu;
+    x = (x | (x << 32)) & 0x1f00000000ffffull;
+    x = (x | (x << 16)) & 0x1f0000ff0000ffull;
+    x = (x | (x << 8)) & 0x100f00f00f00f00full;
+    x = (x | (x << 4)) & 0x10c30c30c30c30c3ull;
+    x = (x | (x << 2)) & 0x1249249249249249ull;
+    return x;
+}
+
+// Morton key: x on bit 0 of every triple, y on bit 1, z on bit 2.
+__host__ __device__ inline uint64_t morton3(uint32_t cx, uint32_t cy, uint32_t cz) {
+    return spread3(cx) | (spread3(cy) << 1) | (spread3(cz) << 2);
+}
+
+// Geometry of the level-0 grid: cell side s0 (a power of two) and an origin
+// that is a multiple of s0, so cell coordinates are exact in double.
+struct GridFrame {
+    double origin[3];
+    double s0;
+    double inv_s0;
+};
+
+// Level-0 cell coordinate and the position inside that cell, both exact in
+// double: x is a float, origin and s0 are power-of-two multiples.
+__device__ inline uint32_t cell_coord(float x, double origin, double inv_s0, double *frac) {
+    double g = ((double)x - origin) * inv_s0;
+    double c = floor(g);
+    c = fmin(fmax(c, 0.0), (double)(kAxisCells - 1));
+    if (frac) *frac = g - c;
+    return (uint32_t)c;
+}
+
+// Ordered-integer view of a float for atomic min / max.
+__device__ inline int float_to_ordered(float f) {
+    int i = __float_as_int(f);
+    return i >= 0 ? i : i ^ 0x7fffffff;
+}
+__device__ inline float ordered_to_float(int i) {
+    return __int_as_float(i >= 0 ? i : i ^ 0x7fffffff);
+}
+
+__device__ inline unsigned lanemask_lt() {
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+template <typename T>
+__device__ inline T warp_sum(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+}  // namespace mls

@@ -1,0 +1,501 @@
+// The per-point MLS projection (Sec. 1.4, Eq. 1; Algorithm 1): weighted plane,
+// origin q on it, local height polynomial, projection onto the polynomial.
+//
+// One thread per point (each point is independent, as the paper's information
+// graph shows), so the per-point 3x3 eigensolve and 6x6 solve run on every
+// lane at once.  FP32 / mixed form: pass A gathers the k neighbours, forms
+// d_j = p_j - r and w_j = exp(-|d_j|^2 / h^2) and stages (d_j, w_j) in shared
+// memory (entry j of thread t at j * blockDim + t: conflict-free float4
+// accesses); pass B accumulates the covariance about the weighted centroid;
+// pass C accumulates the 15 monomial moments and 6 right-hand sides of the
+// degree-2 normal equations in local coordinates scaled by 1/h.
+#include <cfloat>
+
+#include "common.cuh"
+
+namespace mls {
+
+namespace {
+
+constexpr int kProjThreads = 128;
+constexpr float kMixedGapFlag = 1e-2f;     // FP32 eigensolve trusted above this gap ratio
+constexpr float kMixedCondFlag = 1e5f;     // FP32 Cholesky trusted below this condition estimate
+
+template <int DEG>
+struct Basis {
+    static constexpr int M = DEG == 0 ? 1 : (DEG == 1 ? 3 : 6);
+};
+
+// Cyclic Jacobi on the symmetric 3x3 matrix a (xx, xy, xz, yy, yz, zz).
+// Eigenvalues ascending in lam, eigenvectors as columns of V.
+template <typename T>
+__device__ void jacobi3(const T a6[6], T lam[3], T V[3][3]) {
+    T A[3][3] = {{a6[0], a6[1], a6[2]}, {a6[1], a6[3], a6[4]}, {a6[2], a6[4], a6[5]}};
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) V[i][j] = (i == j) ? T(1) : T(0);
+    const T tol = sizeof(T) == 4 ? T(1e-15) : T(1e-30);
+    for (int sweep = 0; sweep < (sizeof(T) == 4 ? 8 : 20); ++sweep) {
+        T off = A[0][1] * A[0][1] + A[0][2] * A[0][2] + A[1][2] * A[1][2];
+        T all = A[0][0] * A[0][0] + A[1][1] * A[1][1] + A[2][2] * A[2][2] + T(2) * off;
+        if (off <= tol * all) break;
+#pragma unroll
+        for (int pq = 0; pq < 3; ++pq) {
+            const int p = pq == 2 ? 1 : 0, q = pq == 0 ? 1 : 2;
+            T apq = A[p][q];
+            if (apq == T(0)) continue;
+            T theta = (A[q][q] - A[p][p]) / (T(2) * apq);
+            T t = (theta >= T(0) ? T(1) : T(-1)) / (fabs(theta) + sqrt(theta * theta + T(1)));
+            T c = T(1) / sqrt(t * t + T(1)), s = t * c;
+#pragma unroll
+            for (int r = 0; r < 3; ++r) {
+                T arp = A[r][p], arq = A[r][q];
+                A[r][p] = c * arp - s * arq;
+                A[r][q] = s * arp + c * arq;
+            }
+#pragma unroll
+            for (int r = 0; r < 3; ++r) {
+                T apr = A[p][r], aqr = A[q][r];
+                A[p][r] = c * apr - s * aqr;
+                A[q][r] = s * apr + c * aqr;
+            }
+            A[p][q] = A[q][p] = T(0);
+#pragma unroll
+            for (int r = 0; r < 3; ++r) {
+                T vrp = V[r][p], vrq = V[r][q];
+                V[r][p] = c * vrp - s * vrq;
+                V[r][q] = s * vrp + c * vrq;
+            }
+        }
+    }
+    lam[0] = A[0][0];
+    lam[1] = A[1][1];
+    lam[2] = A[2][2];
+    // sort ascending (three compare-swaps)
+#pragma unroll
+    for (int pass = 0; pass < 3; ++pass) {
+        const int i = pass == 1 ? 1 : 0, j = i + 1;
+        if (lam[j] < lam[i]) {
+            T tl = lam[i];
+            lam[i] = lam[j];
+            lam[j] = tl;
+#pragma unroll
+            for (int r = 0; r < 3; ++r) {
+                T tv = V[r][i];
+                V[r][i] = V[r][j];
+                V[r][j] = tv;
+            }
+        }
+    }
+}
+
+// Cholesky A = L L^T of an M x M symmetric matrix (lower triangle used).
+// Returns false when a pivot is <= rel_tol * trace.  min/max pivot (of L)
+// are returned for the conditioning estimate.
+template <typename T, int M>
+__device__ bool cholesky(const T A[M][M], T L[M][M], T rel_tol, T &pmin, T &pmax) {
+    T tr = T(0);
+#pragma unroll
+    for (int i = 0; i < M; ++i) tr += A[i][i];
+    pmin = T(INFINITY);
+    pmax = T(0);
+    bool ok = true;
+#pragma unroll
+    for (int j = 0; j < M; ++j) {
+        T d = A[j][j];
+#pragma unroll
+        for (int c = 0; c < j; ++c) d -= L[j][c] * L[j][c];
+        if (!(d > rel_tol * tr)) {
+            ok = false;
+            d = T(1);
+        }
+        T l = sqrt(d);
+        L[j][j] = l;
+        pmin = fmin(pmin, l);
+        pmax = fmax(pmax, l);
+        T inv = T(1) / l;
+#pragma unroll
+        for (int i = j + 1; i < M; ++i) {
+            T s = A[i][j];
+#pragma unroll
+            for (int c = 0; c < j; ++c) s -= L[i][c] * L[j][c];
+            L[i][j] = s * inv;
+        }
+    }
+    return ok;
+}
+
+template <typename T, int M>
+__device__ void chol_solve(const T L[M][M], const T b[M], T x[M]) {
+    T y[M];
+#pragma unroll
+    for (int i = 0; i < M; ++i) {
+        T s = b[i];
+#pragma unroll
+        for (int c = 0; c < i; ++c) s -= L[i][c] * y[c];
+        y[i] = s / L[i][i];
+    }
+#pragma unroll
+    for (int i = M - 1; i >= 0; --i) {
+        T s = y[i];
+#pragma unroll
+        for (int c = i + 1; c < M; ++c) s -= L[c][i] * x[c];
+        x[i] = s / L[i][i];
+    }
+}
+
+// Normal matrix and right-hand side from the moments.
+// mom: M00 M10 M01 M20 M11 M02 M30 M21 M12 M03 M40 M31 M22 M13 M04 (Mab = sum w u^a v^b)
+template <typename T, int DEG>
+__device__ void assemble(const float mom[15], T A[Basis<DEG>::M][Basis<DEG>::M]) {
+    constexpr int M = Basis<DEG>::M;
+    // exponent pairs of the basis monomials
+    const int ea[6] = {0, 1, 0, 2, 1, 0}, eb[6] = {0, 0, 1, 0, 1, 2};
+#pragma unroll
+    for (int r = 0; r < M; ++r)
+#pragma unroll
+        for (int c = 0; c < M; ++c) {
+            const int a = ea[r] + ea[c], b = eb[r] + eb[c], dg = a + b;
+            // position of (a, b) in the moment list: degree blocks 1, 2, 3, 4, 5 long
+            const int at = dg * (dg + 1) / 2 + b;
+            A[r][c] = (T)mom[at];
+        }
+}
+
+// Solve the height fit: returns a0 and whether the system was singular.
+template <typename T, int DEG>
+__device__ T solve_a0(const float mom[15], const float rhs[6], bool refine, bool &singular, T &cond_est) {
+    constexpr int M = Basis<DEG>::M;
+    T A[M][M], L[M][M], b[M], x[M];
+    assemble<T, DEG>(mom, A);
+#pragma unroll
+    for (int r = 0; r < M; ++r) b[r] = (T)rhs[r];
+    T pmin, pmax;
+    singular = !cholesky<T, M>(A, L, T(1e-12), pmin, pmax);
+    cond_est = (pmax / pmin) * (pmax / pmin);
+    if (singular) return T(0);
+    chol_solve<T, M>(L, b, x);
+    if (refine) {
+        T res[M], dx[M];
+#pragma unroll
+        for (int r = 0; r < M; ++r) {
+            T s = b[r];
+#pragma unroll
+            for (int c = 0; c < M; ++c) s -= A[r][c] * x[c];
+            res[r] = s;
+        }
+        chol_solve<T, M>(L, res, dx);
+#pragma unroll
+        for (int r = 0; r < M; ++r) x[r] += dx[r];
+    }
+    return x[0];
+}
+
+template <typename T>
+__device__ void canonical(T n[3]) {
+    int a = 0;
+    if (fabs(n[1]) > fabs(n[a])) a = 1;
+    if (fabs(n[2]) > fabs(n[a])) a = 2;
+    if (n[a] < T(0)) {
+        n[0] = -n[0];
+        n[1] = -n[1];
+        n[2] = -n[2];
+    }
+}
+
+// Frame from the eigen-decomposition: n = v0 (canonical sign), e1 = v1,
+// e2 = n x e1.  Returns the status bit for a degenerate plane.
+template <typename T>
+__device__ int frame_from(const T C[6], T nrm[3], T e1[3], T e2[3], T lam[3]) {
+    T V[3][3];
+    jacobi3<T>(C, lam, V);
+    nrm[0] = V[0][0];
+    nrm[1] = V[1][0];
+    nrm[2] = V[2][0];
+    e1[0] = V[0][1];
+    e1[1] = V[1][1];
+    e1[2] = V[2][1];
+    canonical(nrm);
+    e2[0] = nrm[1] * e1[2] - nrm[2] * e1[1];
+    e2[1] = nrm[2] * e1[0] - nrm[0] * e1[2];
+    e2[2] = nrm[0] * e1[1] - nrm[1] * e1[0];
+    if (!(lam[2] > T(0)) || (lam[1] - lam[0]) <= T(1e-6) * lam[2]) return MLS_PT_PLANE_DEGENERATE;
+    return 0;
+}
+
+template <int DEG, int PREC>
+__global__ void __launch_bounds__(kProjThreads) k_project(const float *__restrict__ xyz, int64_t n,
+                                                          const int32_t *__restrict__ idx, int k, float h,
+                                                          const int32_t *__restrict__ order,
+                                                          float *__restrict__ out_xyz, float *__restrict__ out_n,
+                                                          uint8_t *__restrict__ status) {
+    extern __shared__ float4 stage[];
+    const int64_t slot = blockIdx.x * (int64_t)kProjThreads + threadIdx.x;
+    if (slot >= n) return;
+    const int64_t i = order ? (int64_t)order[slot] : slot;
+    const float rx = xyz[3 * i], ry = xyz[3 * i + 1], rz = xyz[3 * i + 2];
+    const int32_t *row = idx + i * k;
+    float4 *my = stage + threadIdx.x;
+    // exp(-|d|^2 / h^2) = exp2(-|d|^2 * log2(e) / h^2)
+    const float neg_scale = -1.4426950408889634f / (h * h);
+
+    // pass A: weights and weighted centroid offset m = sum w d / W
+    float W = 0.f, sx = 0.f, sy = 0.f, sz = 0.f;
+#pragma unroll 4
+    for (int j = 0; j < k; ++j) {
+        const int64_t p = __ldg(row + j);
+        const float dx = __ldg(xyz + 3 * p) - rx, dy = __ldg(xyz + 3 * p + 1) - ry, dz = __ldg(xyz + 3 * p + 2) - rz;
+        const float w = exp2f(fmaf(dx, dx, fmaf(dy, dy, dz * dz)) * neg_scale);
+        W += w;
+        sx = fmaf(w, dx, sx);
+        sy = fmaf(w, dy, sy);
+        sz = fmaf(w, dz, sz);
+        my[j * kProjThreads] = make_float4(dx, dy, dz, w);
+    }
+    const float invW = 1.f / W;
+    const float mx = sx * invW, my_ = sy * invW, mz = sz * invW;
+
+    // pass B: covariance about the weighted centroid (unnormalised: the
+    // eigenvectors and the ratio tests do not depend on the 1/W factor)
+    float C[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll 4
+    for (int j = 0; j < k; ++j) {
+        const float4 v = my[j * kProjThreads];
+        const float ex = v.x - mx, ey = v.y - my_, ez = v.z - mz;
+        const float wx = v.w * ex, wy = v.w * ey, wz = v.w * ez;
+        C[0] = fmaf(wx, ex, C[0]);
+        C[1] = fmaf(wx, ey, C[1]);
+        C[2] = fmaf(wx, ez, C[2]);
+        C[3] = fmaf(wy, ey, C[3]);
+        C[4] = fmaf(wy, ez, C[4]);
+        C[5] = fmaf(wz, ez, C[5]);
+    }
+    uint8_t st = 0;
+    float nf[3], e1f[3], e2f[3];
+    {
+        float lam[3];
+        int deg_flag = frame_from<float>(C, nf, e1f, e2f, lam);
+        // the FP32 eigenvector error grows like eps * l2 / (l1 - l0): in the
+        // mixed form, narrow gaps are solved again in FP64 from the same moments
+        if (PREC == MLS_PREC_MIXED && (!(lam[2] > 0.f) || (lam[1] - lam[0]) < kMixedGapFlag * lam[2])) {
+            double Cd[6], nd[3], e1d[3], e2d[3], ld[3];
+#pragma unroll
+            for (int c = 0; c < 6; ++c) Cd[c] = (double)C[c];
+            deg_flag = frame_from<double>(Cd, nd, e1d, e2d, ld);
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                nf[a] = (float)nd[a];
+                e1f[a] = (float)e1d[a];
+                e2f[a] = (float)e2d[a];
+            }
+            st |= MLS_PT_FP64_USED;
+        }
+        st |= (uint8_t)deg_flag;
+    }
+    float px = rx, py = ry, pz = rz;
+    if (!(st & MLS_PT_PLANE_DEGENERATE)) {
+        const float ofs = nf[0] * mx + nf[1] * my_ + nf[2] * mz;
+        const float ih = 1.f / h;
+        const float a1x = e1f[0] * ih, a1y = e1f[1] * ih, a1z = e1f[2] * ih;
+        const float a2x = e2f[0] * ih, a2y = e2f[1] * ih, a2z = e2f[2] * ih;
+        // pass C: moments of the height fit
+        float mom[15], rhs[6];
+#pragma unroll
+        for (int c = 0; c < 15; ++c) mom[c] = 0.f;
+#pragma unroll
+        for (int c = 0; c < 6; ++c) rhs[c] = 0.f;
+#pragma unroll 2
+        for (int j = 0; j < k; ++j) {
+            const float4 v = my[j * kProjThreads];
+            const float w = v.w;
+            const float f = fmaf(nf[2], v.z, fmaf(nf[1], v.y, fmaf(nf[0], v.x, -ofs)));
+            const float wf = w * f;
+            mom[0] += w;
+            rhs[0] += wf;
+            if (DEG >= 1) {
+                const float u = fmaf(a1z, v.z, fmaf(a1y, v.y, a1x * v.x));
+                const float vv = fmaf(a2z, v.z, fmaf(a2y, v.y, a2x * v.x));
+                const float wu = w * u, wv = w * vv;
+                mom[1] += wu;
+                mom[2] += wv;
+                rhs[1] = fmaf(wf, u, rhs[1]);
+                rhs[2] = fmaf(wf, vv, rhs[2]);
+                const float wuu = wu * u, wuv = wu * vv, wvv = wv * vv;
+                mom[3] += wuu;
+                mom[4] += wuv;
+                mom[5] += wvv;
+                if (DEG >= 2) {
+                    const float uu = u * u, uv = u * vv, v2 = vv * vv;
+                    mom[6] = fmaf(wuu, u, mom[6]);
+                    mom[7] = fmaf(wuu, vv, mom[7]);
+                    mom[8] = fmaf(wvv, u, mom[8]);
+                    mom[9] = fmaf(wvv, vv, mom[9]);
+                    mom[10] = fmaf(wuu, uu, mom[10]);
+                    mom[11] = fmaf(wuu, uv, mom[11]);
+                    mom[12] = fmaf(wuu, v2, mom[12]);
+                    mom[13] = fmaf(wvv, uv, mom[13]);
+                    mom[14] = fmaf(wvv, v2, mom[14]);
+                    rhs[3] = fmaf(wf, uu, rhs[3]);
+                    rhs[4] = fmaf(wf, uv, rhs[4]);
+                    rhs[5] = fmaf(wf, v2, rhs[5]);
+                }
+            }
+        }
+        bool singular;
+        float cond;
+        float a0 = solve_a0<float, DEG>(mom, rhs, true, singular, cond);
+        if (PREC == MLS_PREC_MIXED && (singular || !(cond < kMixedCondFlag))) {
+            double condd;
+            a0 = (float)solve_a0<double, DEG>(mom, rhs, false, singular, condd);
+            st |= MLS_PT_FP64_USED;
+        }
+        if (singular) {
+            st |= MLS_PT_POLY_SINGULAR;
+            a0 = 0.f;
+        }
+        const float s = ofs + a0;
+        px = fmaf(s, nf[0], rx);
+        py = fmaf(s, nf[1], ry);
+        pz = fmaf(s, nf[2], rz);
+    }
+    out_xyz[3 * i] = px;
+    out_xyz[3 * i + 1] = py;
+    out_xyz[3 * i + 2] = pz;
+    if (out_n) {
+        out_n[3 * i] = nf[0];
+        out_n[3 * i + 1] = nf[1];
+        out_n[3 * i + 2] = nf[2];
+    }
+    if (status) status[i] = st;
+}
+
+// The plain FP64 form: the same three passes, every quantity in double,
+// neighbours re-read from global memory in each pass.
+template <int DEG>
+__global__ void __launch_bounds__(kProjThreads) k_project_fp64(const float *__restrict__ xyz, int64_t n,
+                                                               const int32_t *__restrict__ idx, int k, float h,
+                                                               const int32_t *__restrict__ order,
+                                                               float *__restrict__ out_xyz,
+                                                               float *__restrict__ out_n,
+                                                               uint8_t *__restrict__ status) {
+    const int64_t slot = blockIdx.x * (int64_t)kProjThreads + threadIdx.x;
+    if (slot >= n) return;
+    const int64_t i = order ? (int64_t)order[slot] : slot;
+    const double r[3] = {xyz[3 * i], xyz[3 * i + 1], xyz[3 * i + 2]};
+    const int32_t *row = idx + i * k;
+    const double hd = (double)h, inv_h2 = 1.0 / (hd * hd);
+    double W = 0, m[3] = {0, 0, 0};
+    for (int j = 0; j < k; ++j) {
+        const int64_t p = __ldg(row + j);
+        double d[3], dd = 0;
+        for (int a = 0; a < 3; ++a) {
+            d[a] = (double)__ldg(xyz + 3 * p + a) - r[a];
+            dd += d[a] * d[a];
+        }
+        const double w = exp(-dd * inv_h2);
+        W += w;
+        for (int a = 0; a < 3; ++a) m[a] += w * d[a];
+    }
+    for (int a = 0; a < 3; ++a) m[a] /= W;
+    double C[6] = {0, 0, 0, 0, 0, 0};
+    for (int j = 0; j < k; ++j) {
+        const int64_t p = __ldg(row + j);
+        double d[3], dd = 0;
+        for (int a = 0; a < 3; ++a) {
+            d[a] = (double)__ldg(xyz + 3 * p + a) - r[a];
+            dd += d[a] * d[a];
+        }
+        const double w = exp(-dd * inv_h2);
+        const double e[3] = {d[0] - m[0], d[1] - m[1], d[2] - m[2]};
+        C[0] += w * e[0] * e[0];
+        C[1] += w * e[0] * e[1];
+        C[2] += w * e[0] * e[2];
+        C[3] += w * e[1] * e[1];
+        C[4] += w * e[1] * e[2];
+        C[5] += w * e[2] * e[2];
+    }
+    double nrm[3], e1[3], e2[3], lam[3];
+    uint8_t st = (uint8_t)frame_from<double>(C, nrm, e1, e2, lam);
+    double out[3] = {r[0], r[1], r[2]};
+    if (!st) {
+        constexpr int M = Basis<DEG>::M;
+        const double ofs = nrm[0] * m[0] + nrm[1] * m[1] + nrm[2] * m[2];
+        double A[M][M], b[M], L[M][M], x[M];
+        for (int a = 0; a < M; ++a) {
+            b[a] = 0;
+            for (int c = 0; c < M; ++c) A[a][c] = 0;
+        }
+        for (int j = 0; j < k; ++j) {
+            const int64_t p = __ldg(row + j);
+            double d[3], dd = 0;
+            for (int a = 0; a < 3; ++a) {
+                d[a] = (double)__ldg(xyz + 3 * p + a) - r[a];
+                dd += d[a] * d[a];
+            }
+            const double w = exp(-dd * inv_h2);
+            const double u = (e1[0] * d[0] + e1[1] * d[1] + e1[2] * d[2]) / hd;
+            const double v = (e2[0] * d[0] + e2[1] * d[1] + e2[2] * d[2]) / hd;
+            const double f = nrm[0] * d[0] + nrm[1] * d[1] + nrm[2] * d[2] - ofs;
+            double phi[6] = {1.0, u, v, u * u, u * v, v * v};
+            for (int a = 0; a < M; ++a) {
+                b[a] += w * phi[a] * f;
+                for (int c = 0; c < M; ++c) A[a][c] += w * phi[a] * phi[c];
+            }
+        }
+        double pmin, pmax;
+        double a0 = 0;
+        if (cholesky<double, M>(A, L, 1e-12, pmin, pmax)) {
+            chol_solve<double, M>(L, b, x);
+            a0 = x[0];
+        } else {
+            st |= MLS_PT_POLY_SINGULAR;
+        }
+        const double s = ofs + a0;
+        for (int a = 0; a < 3; ++a) out[a] = r[a] + s * nrm[a];
+    }
+    for (int a = 0; a < 3; ++a) {
+        out_xyz[3 * i + a] = (float)out[a];
+        if (out_n) out_n[3 * i + a] = (float)nrm[a];
+    }
+    if (status) status[i] = st;
+}
+
+template <int DEG>
+int launch_deg(const float *xyz, int64_t n, const int32_t *idx, int k, float h, int precision,
+               const int32_t *order, float *out_xyz, float *out_n, uint8_t *status, cudaStream_t st) {
+    const int blocks = (int)((n + kProjThreads - 1) / kProjThreads);
+    if (precision == MLS_PREC_FP64) {
+        k_project_fp64<DEG><<<blocks, kProjThreads, 0, st>>>(xyz, n, idx, k, h, order, out_xyz, out_n, status);
+    } else {
+        const size_t smem = (size_t)k * kProjThreads * sizeof(float4);
+        if (precision == MLS_PREC_MIXED) {
+            auto kern = k_project<DEG, MLS_PREC_MIXED>;
+            MLS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            kern<<<blocks, kProjThreads, smem, st>>>(xyz, n, idx, k, h, order, out_xyz, out_n, status);
+        } else {
+            auto kern = k_project<DEG, MLS_PREC_FP32>;
+            MLS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            kern<<<blocks, kProjThreads, smem, st>>>(xyz, n, idx, k, h, order, out_xyz, out_n, status);
+        }
+    }
+    count_launches(1);
+    MLS_CUDA_TRY(cudaGetLastError());
+    return MLS_OK;
+}
+
+}  // namespace
+
+int launch_project(const float *xyz, int64_t n, const int32_t *idx, int k, float h, int degree, int precision,
+                   const int32_t *order, float *out_xyz, float *out_n, uint8_t *status, cudaStream_t st) {
+    switch (degree) {
+        case 0:
+            return launch_deg<0>(xyz, n, idx, k, h, precision, order, out_xyz, out_n, status, st);
+        case 1:
+            return launch_deg<1>(xyz, n, idx, k, h, precision, order, out_xyz, out_n, status, st);
+        default:
+            return launch_deg<2>(xyz, n, idx, k, h, precision, order, out_xyz, out_n, status, st);
+    }
+}
+
+}  // namespace mls

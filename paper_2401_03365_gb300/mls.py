@@ -1,0 +1,81 @@
+"""User-facing MLS projection on the GPU (Sec. 1.4, Eq. 1; Algorithm 1).
+
+    out = project(xyz, k=32)            # grid -> kNN -> h -> projection
+    out.xyz, out.normal, out.status, out.idx, out.h
+
+Every step runs in libmls; this module only sequences the C-ABI calls.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import torch
+
+from . import capi
+
+
+@dataclass
+class Projection:
+    xyz: torch.Tensor        # (n, 3) float32, projected points
+    normal: torch.Tensor     # (n, 3) float32, plane normals (canonical sign)
+    status: torch.Tensor     # (n,) uint8, capi.MLS_PT_* bits
+    idx: torch.Tensor        # (n, k) int32 neighbour rows
+    h: float                 # bandwidth used
+
+
+class Pipeline:
+    """Reusable buffers for repeated projections of clouds of one size:
+    the grid handle, the neighbour rows and the outputs."""
+
+    def __init__(self, n: int, k: int, device="cuda"):
+        self.n, self.k = n, k
+        self.grid = None
+        self.idx = torch.empty((n, k), dtype=torch.int32, device=device)
+        self.out_xyz = torch.empty((n, 3), dtype=torch.float32, device=device)
+        self.out_normal = torch.empty((n, 3), dtype=torch.float32, device=device)
+        self.out_status = torch.empty(n, dtype=torch.uint8, device=device)
+
+    def neighbours(self, xyz: torch.Tensor, cell_size: float = 0.0):
+        self.grid = capi.mls_build_grid(xyz, cell_size, self.k, grid=self.grid)
+        capi.mls_knn(self.grid, self.k, out_idx=self.idx)
+        return self.idx
+
+    def bandwidth(self, xyz: torch.Tensor) -> float:
+        """h = 2 x mean distance to the other neighbours (a host read)."""
+        return 2.0 * float(capi.mls_mean_knn_dist(xyz, self.idx).item())
+
+    def project(self, xyz: torch.Tensor, h: float, degree: int = 2, precision: str = "mixed"):
+        order = capi.mls_grid_order(self.grid) if self.grid is not None else None
+        capi.mls_project(xyz, self.idx, h, degree, precision, order=order, out_xyz=self.out_xyz,
+                         out_normal=self.out_normal, out_status=self.out_status)
+        return self.out_xyz, self.out_normal, self.out_status
+
+    def close(self):
+        if self.grid is not None:
+            self.grid.close()
+            self.grid = None
+
+
+def knn(xyz: torch.Tensor, k: int, with_key: bool = False, cell_size: float = 0.0):
+    grid = capi.mls_build_grid(xyz, cell_size, k)
+    try:
+        idx, key = capi.mls_knn(grid, k, with_key=with_key)
+        order = capi.mls_grid_order(grid).clone()
+    finally:
+        torch.cuda.current_stream().synchronize()
+        grid.close()
+    return idx, key, order
+
+
+def project(xyz: torch.Tensor, k: int = 32, h: float | None = None, degree: int = 2,
+            precision: str = "mixed") -> Projection:
+    p = Pipeline(xyz.shape[0], k, xyz.device)
+    try:
+        p.neighbours(xyz)
+        if h is None:
+            h = p.bandwidth(xyz)
+        p.project(xyz, h, degree, precision)
+        torch.cuda.current_stream().synchronize()
+    finally:
+        p.close()
+    return Projection(p.out_xyz, p.out_normal, p.out_status, p.idx, h)

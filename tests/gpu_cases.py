@@ -1,0 +1,110 @@
+"""Shared inputs and checks for the GPU parity tests (CUDA path vs the oracle)."""
+import zlib
+
+import numpy as np
+
+import oracle
+from paper_2401_03365_gb300 import workloads
+
+# Well-posed mask for the floating-point tolerances: the plane normal is
+# determined to FP32 accuracy only when the eigen-gap is not tiny relative to
+# the largest eigenvalue, and the height fit only when its normal matrix is
+# not near-singular.
+GAP_MIN = 1e-3
+COND_MAX = 1e8
+POS_TOL = 1e-5        # of the bounding-box diagonal
+NORMAL_TOL = 1e-4     # radians, unoriented
+
+
+def lattice(n_side, spacing=0.25, seed=0):
+    g = np.arange(n_side, dtype=np.float32) * np.float32(spacing)
+    pts = np.stack(np.meshgrid(g, g, g, indexing="ij"), -1).reshape(-1, 3)
+    return pts[np.random.default_rng(seed).permutation(pts.shape[0])]
+
+
+def knn_case(name):
+    """(xyz float32, k) for the kNN parity cases."""
+    rng = np.random.default_rng(zlib.crc32(name.encode()))
+    if name == "sphere20k_k20":
+        c = workloads.sphere()
+        return c.xyz, c.k
+    if name == "torus100k_k32":
+        c = workloads.torus(n=100_000, seed=12)
+        return c.xyz, 32
+    if name == "heightfield200k_k64":
+        c = workloads.heightfield(n=200_000, seed=13)
+        return c.xyz, 64
+    if name == "lattice_ties_k27":
+        return lattice(12), 27
+    if name == "lattice_ties_k64":
+        return lattice(10), 64
+    if name == "duplicates_k20":
+        base = rng.uniform(0, 1, (500, 3)).astype(np.float32)
+        return base[rng.integers(0, 500, 5000)], 20
+    if name == "clusters_and_outliers_k16":
+        a = rng.normal(0, 1e-3, (3000, 3))
+        b = rng.normal(5, 1e-2, (3000, 3))
+        c = rng.uniform(-50, 50, (40, 3))
+        return np.concatenate([a, b, c]).astype(np.float32), 16
+    if name == "far_from_origin_k12":
+        return (rng.standard_normal((5000, 3)) * 1e-2 + 1000.0).astype(np.float32), 12
+    if name == "all_identical_k10":
+        return np.full((100, 3), 0.5, np.float32), 10
+    if name == "planar_k8":
+        p = rng.uniform(-1, 1, (4000, 3)).astype(np.float32)
+        p[:, 2] = 0.25
+        return p, 8
+    if name == "tiny_n_equals_k":
+        return rng.standard_normal((5, 3)).astype(np.float32), 5
+    if name == "n64_k64":
+        return rng.standard_normal((64, 3)).astype(np.float32), 64
+    if name == "k1":
+        return rng.standard_normal((3000, 3)).astype(np.float32), 1
+    if name == "k33_ragged":
+        return rng.standard_normal((20_011, 3)).astype(np.float32), 33
+    raise KeyError(name)
+
+
+KNN_CASES = ["sphere20k_k20", "torus100k_k32", "heightfield200k_k64", "lattice_ties_k27", "lattice_ties_k64",
+             "duplicates_k20", "clusters_and_outliers_k16", "far_from_origin_k12", "all_identical_k10",
+             "planar_k8", "tiny_n_equals_k", "n64_k64", "k1", "k33_ragged"]
+
+
+def oracle_knn(xyz, k):
+    if xyz.shape[0] <= 3000:
+        return oracle.knn_brute(xyz, k)
+    return oracle.knn_kdtree(xyz, k)
+
+
+def diag_len(xyz):
+    x = xyz.astype(np.float64)
+    return float(np.linalg.norm(x.max(0) - x.min(0)))
+
+
+def well_posed(diag, gap_min=GAP_MIN, cond_max=COND_MAX):
+    gap = (diag[:, 1] - diag[:, 0]) / np.maximum(diag[:, 2], 1e-300)
+    return (gap >= gap_min) & (diag[:, 3] <= cond_max) & (diag[:, 2] > 0)
+
+
+def compare_projection(gpu_xyz, gpu_n, gpu_st, o_xyz, o_n, o_st, o_diag, D, pos_tol=POS_TOL,
+                       normal_tol=NORMAL_TOL, min_well_posed=0.5, gap_min=GAP_MIN, cond_max=COND_MAX):
+    """Element-wise comparison on the well-posed mask; returns a report."""
+    mask = well_posed(o_diag, gap_min, cond_max)
+    assert mask.mean() >= min_well_posed, f"well-posed fraction {mask.mean():.3f}"
+    pos_err = np.linalg.norm(gpu_xyz.astype(np.float64) - o_xyz, axis=1) / D
+    gn = gpu_n.astype(np.float64)
+    ang = np.arctan2(np.linalg.norm(np.cross(gn, o_n), axis=1), np.abs((gn * o_n).sum(1)))
+    st_gpu = gpu_st & 3
+    rep = {
+        "well_posed": float(mask.mean()),
+        "max_pos_err": float(pos_err[mask].max()) if mask.any() else 0.0,
+        "max_angle": float(ang[mask].max()) if mask.any() else 0.0,
+        "status_mismatch_well_posed": int((st_gpu[mask] != o_st[mask]).sum()),
+        "excluded_max_pos_err": float(pos_err[~mask].max()) if (~mask).any() else 0.0,
+    }
+    worst = int(np.argmax(np.where(mask, pos_err, -1)))
+    rep["worst_gap"] = float((o_diag[worst, 1] - o_diag[worst, 0]) / o_diag[worst, 2])
+    assert rep["status_mismatch_well_posed"] == 0, rep
+    assert rep["max_pos_err"] <= pos_tol, rep
+    assert rep["max_angle"] <= normal_tol, rep
+    return rep

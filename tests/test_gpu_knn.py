@@ -1,0 +1,83 @@
+"""GPU kNN (mls_build_grid + mls_knn through the C ABI) against the oracle:
+identical index rows and bit-identical keys."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from tests.gpu_cases import KNN_CASES, knn_case, oracle_knn
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def capi():
+    from paper_2401_03365_gb300 import build, capi
+    build.build()
+    return capi
+
+
+def _gpu_knn(capi, xyz, k):
+    x = torch.from_numpy(xyz).cuda()
+    grid = capi.mls_build_grid(x, 0.0, k)
+    idx, key = capi.mls_knn(grid, k, with_key=True)
+    order = capi.mls_grid_order(grid).cpu().numpy()
+    torch.cuda.synchronize()
+    grid.close()
+    return idx.cpu().numpy(), key.cpu().numpy(), order
+
+
+@pytest.mark.parametrize("case", KNN_CASES)
+def test_knn_bit_exact(capi, case):
+    xyz, k = knn_case(case)
+    idx_o, key_o = oracle_knn(xyz, k)
+    idx_g, key_g, order = _gpu_knn(capi, xyz, k)
+    bad = np.nonzero((idx_g != idx_o).any(1))[0]
+    assert bad.size == 0, f"{bad.size} rows differ, first {bad[:5]}: gpu {idx_g[bad[0]]} oracle {idx_o[bad[0]]}"
+    assert np.array_equal(key_g.view(np.uint32), key_o.view(np.uint32))
+    assert np.array_equal(np.sort(order), np.arange(xyz.shape[0]))
+
+
+def test_knn_full_size_torus_sampled(capi):
+    """2M-point torus with outliers (the benchmark workload): the GPU rows of a
+    seeded sample of queries, the first and last points of the Morton order
+    and every outlier-region point in the sample, against the oracle's k-d
+    tree over the whole cloud."""
+    from paper_2401_03365_gb300 import workloads
+    c = workloads.torus()
+    idx_g, key_g, order = _gpu_knn(capi, c.xyz, c.k)
+    rng = np.random.default_rng(99)
+    q = np.unique(np.concatenate([rng.integers(0, c.n, 20_000), order[:64], order[-64:]]))
+    idx_o, key_o = oracle.knn_kdtree(c.xyz, c.k, queries=q)
+    assert np.array_equal(idx_g[q], idx_o)
+    assert np.array_equal(key_g[q].view(np.uint32), key_o.view(np.uint32))
+
+
+def test_knn_deterministic_and_grid_reuse(capi):
+    xyz, k = knn_case("torus100k_k32")
+    x = torch.from_numpy(xyz).cuda()
+    grid = capi.mls_build_grid(x, 0.0, k)
+    a, _ = capi.mls_knn(grid, k)
+    a = a.clone()
+    # rebuild in place on another cloud, then on the first again
+    y = torch.from_numpy(knn_case("sphere20k_k20")[0]).cuda()
+    grid = capi.mls_build_grid(y, 0.0, k, grid=grid)
+    b, _ = capi.mls_knn(grid, k)
+    assert b.shape[0] == y.shape[0]
+    grid = capi.mls_build_grid(x, 0.0, k, grid=grid)
+    c, _ = capi.mls_knn(grid, k)
+    torch.cuda.synchronize()
+    grid.close()
+    assert torch.equal(a, c)
+
+
+@pytest.mark.parametrize("cell_size", [0.002, 0.05, 1.0])
+def test_knn_independent_of_cell_size(capi, cell_size):
+    xyz, k = knn_case("sphere20k_k20")
+    x = torch.from_numpy(xyz).cuda()
+    grid = capi.mls_build_grid(x, cell_size, k)
+    idx, _ = capi.mls_knn(grid, k)
+    torch.cuda.synchronize()
+    grid.close()
+    idx_o, _ = oracle.knn_kdtree(xyz, k)
+    assert np.array_equal(idx.cpu().numpy(), idx_o)

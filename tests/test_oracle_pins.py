@@ -215,7 +215,7 @@ def test_golden_symmetric_vertex():
     n = xyz.shape[0]
     idx = np.tile(np.arange(n, dtype=np.int32), (n, 1))
     qi = int(g["query"])
-    out, nrm, st, _ = oracle.project(xyz, idx, g["h"], int(g["degree"]), queries=[qi])
+    out, nrm, st, _ = oracle.project(xyz, idx[qi:qi + 1], g["h"], int(g["degree"]), queries=[qi])
     assert st[0] == 0
     assert np.abs(out[0] - g["expect_xyz"]).max() <= g["tol_xyz"]
     assert np.abs(nrm[0] - g["expect_normal"]).max() <= g["tol_normal"]
@@ -248,13 +248,13 @@ def test_two_rings_closed_form():
     idx = np.tile(np.arange(9, dtype=np.int32), (9, 1))
     for h in (0.1, 0.2, 0.4):
         z_expect, zbar = _two_rings_closed_form(rho, s, delta, h)
-        out, nrm, st, _ = oracle.project(xyz, idx, h, 2, queries=[0])
+        out, nrm, st, _ = oracle.project(xyz, idx[:1], h, 2, queries=[0])
         assert st[0] == 0
         assert np.abs(nrm[0] - [0, 0, 1]).max() < 1e-14
         assert np.abs(out[0, :2]).max() < 1e-15
         assert out[0, 2] == pytest.approx(z_expect, abs=1e-15)
         assert abs(z_expect - zbar) > 1e-4     # the polynomial step matters here
-        out1, *_ = oracle.project(xyz, idx, h, 1, queries=[0])
+        out1, *_ = oracle.project(xyz, idx[:1], h, 1, queries=[0])
         assert out1[0, 2] == pytest.approx(zbar, abs=1e-15)
 
 
@@ -272,9 +272,9 @@ def test_status_degenerate_plane_and_singular_polynomial():
     cross = np.concatenate([[[0, 0, 0]], np.stack([a, 0 * a, 0 * a], 1), np.stack([0 * a, a, 0 * a], 1)])
     cross = cross.astype(np.float32)
     idx = np.tile(np.arange(9, dtype=np.int32), (9, 1))
-    out, nrm, st, _ = oracle.project(cross, idx, 0.5, 2, queries=[0])
+    out, nrm, st, _ = oracle.project(cross, idx[:1], 0.5, 2, queries=[0])
     assert st[0] == oracle.STATUS_POLY_SINGULAR
-    out1, _, st1, _ = oracle.project(cross, idx, 0.5, 1, queries=[0])
+    out1, _, st1, _ = oracle.project(cross, idx[:1], 0.5, 1, queries=[0])
     assert st1[0] == 0 and np.array_equal(out[0], out1[0])
 
 

@@ -164,7 +164,7 @@ class _DeviceArray:
     """A device buffer owned by libmls, seen through __cuda_array_interface__."""
 
     def __init__(self, ptr, n, typestr):
-        self.__cuda_array_interface__ = {"shape": (n,), "typestr": typestr, "data": (ptr, True),
+        self.__cuda_array_interface__ = {"shape": (n,), "typestr": typestr, "data": (ptr, False),
                                          "version": 3, "strides": None}
 
 

@@ -45,22 +45,34 @@ __host__ __device__ inline uint64_t morton3(uint32_t cx, uint32_t cy, uint32_t c
     return spread3(cx) | (spread3(cy) << 1) | (spread3(cz) << 2);
 }
 
-// Geometry of the level-0 grid: cell side s0 (a power of two) and an origin
-// that is a multiple of s0, so cell coordinates are exact in double.
+// Inverse of spread3: gather bits 0, 3, 6, ... into the low 21 bits.
+__host__ __device__ inline uint32_t compact3(uint64_t x) {
+    x &= 0x1249249249249249ull;
+    x = (x ^ (x >> 2)) & 0x10c30c30c30c30c3ull;
+    x = (x ^ (x >> 4)) & 0x100f00f00f00f00full;
+    x = (x ^ (x >> 8)) & 0x1f0000ff0000ffull;
+    x = (x ^ (x >> 16)) & 0x1f00000000ffffull;
+    x = (x ^ (x >> 32)) & 0x1fffffull;
+    return (uint32_t)x;
+}
+
+// Geometry of the level-0 grid, in float: cell side s0 (a power of two) and an
+// origin that is a multiple of s0 (so both are exact floats), plus `eps`, a
+// bound on how far float rounding can put a point outside the cell it is
+// filed under, or move a computed distance from a point to a cell face: eight
+// units in the last place of the largest coordinate magnitude of the domain.
 struct GridFrame {
-    double origin[3];
-    double s0;
-    double inv_s0;
+    float origin[3];
+    float s0;
+    float inv_s0;
+    float eps;
 };
 
-// Level-0 cell coordinate and the position inside that cell, both exact in
-// double: x is a float, origin and s0 are power-of-two multiples.
-__device__ inline uint32_t cell_coord(float x, double origin, double inv_s0, double *frac) {
-    double g = ((double)x - origin) * inv_s0;
-    double c = floor(g);
-    c = fmin(fmax(c, 0.0), (double)(kAxisCells - 1));
-    if (frac) *frac = g - c;
-    return (uint32_t)c;
+// Level-0 cell coordinate of a coordinate value (clamped to the grid).
+__device__ inline uint32_t cell_coord(float x, float origin, float inv_s0) {
+    float g = floorf((x - origin) * inv_s0);
+    g = fminf(fmaxf(g, 0.0f), (float)(kAxisCells - 1));
+    return (uint32_t)g;
 }
 
 // Ordered-integer view of a float for atomic min / max.

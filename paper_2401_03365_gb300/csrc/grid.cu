@@ -70,29 +70,32 @@ __global__ void k_bbox(const float *__restrict__ xyz, int64_t n, Misc *m) {
 }
 
 // The level-0 frame: cell side s0 = a power of two with 2^21 cells spanning
-// the largest extent plus one cell, origin = bbox min rounded down to s0.
+// the largest extent plus one cell, origin = bbox min rounded down to a
+// multiple of s0 (exact in float), eps from the largest coordinate magnitude.
 __global__ void k_frame(Misc *m) {
     if (threadIdx.x != 0 || m->nonfinite) return;
-    double lo[3], hi[3], ext = 0.0;
+    float lo[3], hi[3], ext = 0.0f;
     for (int a = 0; a < 3; ++a) {
         lo[a] = ordered_to_float(m->bbox[a]);
         hi[a] = ordered_to_float(m->bbox[3 + a]);
-        ext = fmax(ext, hi[a] - lo[a]);
+        ext = fmaxf(ext, hi[a] - lo[a]);
     }
-    // smallest power of two s0 with (ext / s0) + 1 <= 2^21 - 1
-    double need = ext / (double)(kAxisCells - 2);
-    double s0 = ldexp(1.0, -1074);
-    if (need > 0.0) {
-        int e;
-        frexp(need, &e);            // need = f * 2^e, f in [0.5, 1)
-        s0 = ldexp(1.0, e);         // >= need
-    } else {
-        s0 = 1.0;
-    }
+    // s0 >= ext / (2^21 - 2) (rounded up to a power of two) keeps every
+    // point inside the 2^21 cells per axis; 2^-100 floors degenerate extents
+    float need = ext / (float)(kAxisCells - 2) * (1.0f + 0x1p-20f);
+    int e;
+    frexpf(fmaxf(need, 0x1p-100f), &e);
     GridFrame f;
-    f.s0 = s0;
-    f.inv_s0 = 1.0 / s0;
-    for (int a = 0; a < 3; ++a) f.origin[a] = floor(lo[a] / s0) * s0;
+    f.s0 = ldexpf(1.0f, e);
+    f.inv_s0 = ldexpf(1.0f, -e);
+    float mag = 0.0f;
+    for (int a = 0; a < 3; ++a) {
+        f.origin[a] = floorf(lo[a] * f.inv_s0) * f.s0;
+        mag = fmaxf(mag, fmaxf(fabsf(f.origin[a]), fabsf(f.origin[a] + f.s0 * (float)kAxisCells)));
+    }
+    int em;
+    frexpf(fmaxf(mag, 0x1p-100f), &em);     // mag < 2^em
+    f.eps = ldexpf(8.0f, em - 24);           // 8 ulp of values below 2^em
     m->frame = f;
 }
 
@@ -103,7 +106,7 @@ __global__ void k_keys(const float *__restrict__ xyz, int64_t n, const Misc *__r
          i += (int64_t)gridDim.x * blockDim.x) {
         uint32_t c[3];
 #pragma unroll
-        for (int a = 0; a < 3; ++a) c[a] = cell_coord(xyz[3 * i + a], f.origin[a], f.inv_s0, nullptr);
+        for (int a = 0; a < 3; ++a) c[a] = cell_coord(xyz[3 * i + a], f.origin[a], f.inv_s0);
         keys[i] = morton3(c[0], c[1], c[2]);
         perm[i] = (int32_t)i;
     }
@@ -363,6 +366,7 @@ void free_grid_buffers(mls_grid *g) {
     cudaFree(g->block_hist);
     cudaFree(g->scan_tmp);
     cudaFree(g->misc);
+    cudaFree(g->work);
     cudaFreeHost(g->misc_host);
     for (int l = 0; l < kMaxLevels; ++l) {
         cudaFree(g->hkeys[l]);
@@ -393,6 +397,10 @@ int build_grid(mls_grid *g, const float *xyz, int64_t n, float cell_size, int k_
         MLS_CUDA_TRY(cudaMalloc(&g->perm_alt, n * sizeof(int32_t)));
         MLS_CUDA_TRY(cudaMalloc(&g->pts, n * sizeof(float4)));
         g->cap = n;
+    }
+    {
+        int rc0 = grow(&g->work, (size_t)n + 8, &g->work_cap);
+        if (rc0) return rc0;
     }
     if (!g->misc) {
         MLS_CUDA_TRY(cudaMalloc(&g->misc, sizeof(Misc)));
@@ -443,7 +451,7 @@ int build_grid(mls_grid *g, const float *xyz, int64_t n, float cell_size, int k_
     int top = kMaxLevels - 1;
     int base = top;
     if (cell_size > 0.0f) {
-        double r = std::log2((double)cell_size / hm->frame.s0);
+        double r = std::log2((double)cell_size / (double)hm->frame.s0);
         base = (int)std::lround(r);
         if (base < 0) base = 0;
         if (base > top) base = top;
@@ -458,10 +466,12 @@ int build_grid(mls_grid *g, const float *xyz, int64_t n, float cell_size, int k_
     }
     GridView &v = g->view;
     v.pts = g->pts;
+    v.keys = g->keys;
     v.frame = hm->frame;
     v.n = (int32_t)n;
     v.base_level = base;
     v.top_level = top;
+    for (int l = 0; l < kMaxLevels; ++l) v.side[l] = std::ldexp(hm->frame.s0, l);
     int nlev = top - base + 1;
     for (int l = 0; l < kMaxLevels; ++l) v.level[l] = LevelTable{};
     for (int l = base; l <= top; ++l) {

@@ -30,10 +30,12 @@ struct LevelTable {
 // Everything a query kernel needs, passed by value.
 struct GridView {
     const float4 *pts;         // sorted points: x, y, z, original index (int bits)
+    const uint64_t *keys;      // sorted level-0 Morton keys
     GridFrame frame;
     int32_t n;
     int32_t base_level;        // first level with a table
     int32_t top_level;         // last level (a single cell covers the cloud)
+    float side[kMaxLevels];    // cell side per level, s0 * 2^level (exact)
     LevelTable level[kMaxLevels];
 };
 
@@ -68,6 +70,9 @@ struct mls_grid {
     size_t scan_tmp_cap = 0;
     // small device scratch: bbox, flags, level histogram, frame
     void *misc = nullptr;
+    // kNN work list: counters and the deferred queries (n + 8 ints)
+    int *work = nullptr;
+    size_t work_cap = 0;
     void *misc_host = nullptr;   // pinned mirror
     // per-level tables
     uint64_t *hkeys[mls::kMaxLevels] = {};

@@ -1,20 +1,34 @@
 // Exact k nearest neighbours over the grid (the neighbour search of Sec. 2.2,
-// read as kNN): one warp per query, queries taken in Morton order.
+// read as kNN).
 //
-// For a query the warp first picks a level: the base level, or a coarser one
-// when the 3x3x3 block of cells around the query holds fewer than k points.
-// It then searches that block and, while needed, the next shells of cells
-// (Chebyshev radius 2, 3, ...).  The search stops when the current k-th key is
-// below a lower bound on the key of every point outside the searched block:
-// the squared distance from the query to the block's faces (exact in double),
-// shrunk by a relative 2^-20, which covers the rounding of the float key
-// (at most about 5 units of 2^-24).  Ties are broken by the lower index, so
-// the result is the unique first k of the order (key, index).
+// Order and ties.  The key of candidate p for query q is the float
+// fl((fl(dx^2) + fl(dy^2)) + fl(dz^2)), dx = fl(p.x - q.x), never fused; a
+// candidate is the 64-bit word (key bits << 32 | point index), and since keys
+// are non-negative floats, word order is exactly the order (key, index).  The
+// result is the unique first k words.
 //
-// The warp keeps the best 32*KPL candidates as a sorted list spread over the
-// lanes (entry e = r * 32 + lane in register r), each a 64-bit word
-// (key bits << 32 | index), which orders exactly as (key, index) because keys
-// are non-negative floats.
+// Work layout.  One warp per query; each warp walks a chunk of 64 consecutive
+// queries in Morton order.  For every query the warp first gets a key bound
+// tau with at least k points at or below it:
+//   - chained: from each of the two previous queries, with k-th key kappa at
+//     distance d, tau = (sqrt(kappa) + d)^2 (triangle inequality), inflated by
+//     relative margins of 2^-20 per step, which cover float rounding; the
+//     smaller of the two is used when it allows the base level;
+//   - otherwise (chunk start, sparse region): the finest level whose 5x5x5
+//     cube of cells around the query holds k points; its cells nearest to the
+//     query holding 2k points are scanned and tau is the largest key of the
+//     first histogram bucket reaching k.
+// It then searches the 5x5x5 cube of the finest level whose cells are at least
+// half the search radius sqrt(tau) (plus twice the frame's rounding bound
+// eps), which then contains the search ball; cells whose box is farther than
+// the radius are skipped.  The words with key <= tau (>= k of them, every
+// true neighbour among them) are ranked by a 32-bucket counting sort on the
+// key and a rank inside each bucket.  If more than 128 survive, tau is
+// tightened from the bucket histogram and the search repeated; past that a
+// sorted insertion list finishes the query.
+//
+// The cube's 125 cell ranges (four per lane) are cached in registers: queries
+// that follow each other in Morton order mostly share them.
 #include "grid.cuh"
 
 namespace mls {
@@ -23,6 +37,28 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kKnnThreads = 256;
+constexpr int kWarpsPerBlock = kKnnThreads / 32;
+constexpr int kChunk = 128;         // consecutive queries per warp chain
+constexpr int kCap = 128;           // kept-word capacity for the counting sort
+constexpr int kSlots = 4;           // cube cells per lane: 4 x 32 >= 125
+constexpr int kMaxSegWords = 64;    // segment-start bitmap: 2048 points per round
+constexpr float kGrow = 1.0f + 0x1p-20f;
+
+struct __align__(16) WarpBuf {
+    unsigned long long surv[kCap];  // kept words (key bits << 32 | point index)
+    unsigned long long tmp[kCap];
+    int32_t spos[kCap];             // sorted positions of the kept words
+    int32_t tpos[kCap];
+    int32_t nb[64];                 // sorted positions of the previous query's neighbours
+    unsigned segbits[kMaxSegWords]; // first point of each cell of the current round
+    int hist[32];
+    int fill[32];
+    unsigned binmax[32];
+    int nprev;                      // kept words of the last ranked query (in tpos)
+    int cell_start[32];             // cells of the current visiting round
+    int cell_count[32];
+    float kth;
+};
 
 // The ranking key: float differences, squares and sums, each rounded to
 // nearest, association ((dx^2 + dy^2) + dz^2), never fused.
@@ -33,42 +69,334 @@ __device__ __forceinline__ float rank_key(float4 p, float qx, float qy, float qz
     return __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
 }
 
+__device__ __forceinline__ unsigned long long pack(float key, float4 p) {
+    return ((unsigned long long)__float_as_uint(key) << 32) | (uint32_t)__float_as_int(p.w);
+}
+
+__device__ __forceinline__ int warp_incl_scan(int v, int lane) {
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(kFull, v, o);
+        if (lane >= o) v += y;
+    }
+    return v;
+}
+
+// Offsets of cube cell j (0..124) from the centre cell.
+__device__ __forceinline__ void cube_offset(int j, int &dx, int &dy, int &dz) {
+    dx = j % 5 - 2;
+    dy = (j / 5) % 5 - 2;
+    dz = j / 25 - 2;
+}
+
+// The 5x5x5 cube of cells around (cx, cy, cz) at level lev: cell j = r * 32 +
+// lane is held by this lane in slot r.  M = points in the whole cube.
+struct Cube {
+    int lev = -1, cx = 0, cy = 0, cz = 0, M = 0;
+    int start[kSlots], count[kSlots];
+};
+
+// Looks the 125 cells up with the four probes of a lane in flight together.
+__device__ void load_cube(const GridView &g, int lev, const uint32_t c0[3], Cube &cb, int lane) {
+    const int cx = (int)(c0[0] >> lev), cy = (int)(c0[1] >> lev), cz = (int)(c0[2] >> lev);
+    if (cb.lev == lev && cb.cx == cx && cb.cy == cy && cb.cz == cz) return;
+    cb.lev = lev;
+    cb.cx = cx;
+    cb.cy = cy;
+    cb.cz = cz;
+    const LevelTable &t = g.level[lev];
+    const int dims = (int)(kAxisCells >> lev);
+    uint64_t key[kSlots];
+    uint32_t h[kSlots];
+    bool live[kSlots];
+#pragma unroll
+    for (int r = 0; r < kSlots; ++r) {
+        const int j = r * 32 + lane;
+        int dx, dy, dz;
+        cube_offset(j, dx, dy, dz);
+        const int x = cx + dx, y = cy + dy, z = cz + dz;
+        live[r] = j < 125 && x >= 0 && y >= 0 && z >= 0 && x < dims && y < dims && z < dims;
+        key[r] = live[r] ? morton3((uint32_t)x, (uint32_t)y, (uint32_t)z) : 0;
+        h[r] = hash_key(key[r]) & t.hmask;
+    }
+    uint64_t slot[kSlots];
+#pragma unroll
+    for (int r = 0; r < kSlots; ++r) slot[r] = live[r] ? __ldg(t.hkeys + h[r]) : kEmptyKey;
+    int id[kSlots];
+#pragma unroll
+    for (int r = 0; r < kSlots; ++r) {
+        id[r] = -1;
+        if (!live[r]) continue;
+        for (uint32_t probe = 0; probe <= t.hmask; ++probe) {
+            if (slot[r] == key[r]) {
+                id[r] = __ldg(t.hvals + h[r]);
+                break;
+            }
+            if (slot[r] == kEmptyKey) break;
+            h[r] = (h[r] + 1) & t.hmask;
+            slot[r] = __ldg(t.hkeys + h[r]);
+        }
+    }
+    int tot = 0;
+#pragma unroll
+    for (int r = 0; r < kSlots; ++r) {
+        int st = 0, ct = 0;
+        if (id[r] >= 0) {
+            st = __ldg(t.cell_start + id[r]);
+            ct = __ldg(t.cell_start + id[r] + 1) - st;
+        }
+        cb.start[r] = st;
+        cb.count[r] = ct;
+        tot += ct;
+    }
+    cb.M = warp_sum(tot);
+}
+
+// Squared distance from q to the box of this lane's cube cell in slot r.
+__device__ __forceinline__ float cell_dist2(const GridView &g, const Cube &cb, int r, int lane, float4 q) {
+    int dx, dy, dz;
+    cube_offset(r * 32 + lane, dx, dy, dz);
+    const float S = g.side[cb.lev];
+    const float lx = g.frame.origin[0] + (float)(cb.cx + dx) * S;
+    const float ly = g.frame.origin[1] + (float)(cb.cy + dy) * S;
+    const float lz = g.frame.origin[2] + (float)(cb.cz + dz) * S;
+    const float gx = fmaxf(0.f, fmaxf(lx - q.x, q.x - (lx + S)));
+    const float gy = fmaxf(0.f, fmaxf(ly - q.y, q.y - (ly + S)));
+    const float gz = fmaxf(0.f, fmaxf(lz - q.z, q.z - (lz + S)));
+    return gx * gx + gy * gy + gz * gz;
+}
+
+// Visits every point of the cube cells with box distance^2 <= lim2, 32 at a
+// time (one per lane; `valid` false on idle lanes).  The non-empty selected
+// cells are packed onto the lanes (32 per round) and a bitmap of the first
+// point of each cell maps a lane's point number to its cell in O(1).
+template <typename F>
+__device__ void for_each_point(const GridView &g, const Cube &cb, WarpBuf &wb, float4 q, float lim2, int lane,
+                               F &&f) {
+    bool sel[kSlots];
+    int nsel = 0;
+#pragma unroll
+    for (int r = 0; r < kSlots; ++r) {
+        sel[r] = cb.count[r] > 0 && cell_dist2(g, cb, r, lane, q) <= lim2;
+        nsel += sel[r];
+    }
+    const int incl_sel = warp_incl_scan(nsel, lane);
+    const int total_sel = __shfl_sync(kFull, incl_sel, 31);
+    for (int round = 0; round < total_sel; round += 32) {
+        // cell number `round + lane` of the selection goes to this lane
+        int my_start = 0, my_count = 0;
+        int c = incl_sel - nsel;       // selection number of this lane's first selected slot
+#pragma unroll
+        for (int r = 0; r < kSlots; ++r) {
+            if (sel[r]) {
+                const int dst = c - round;
+                // each lane publishes its selected cells through shared memory
+                if (dst >= 0 && dst < 32) {
+                    wb.cell_start[dst] = cb.start[r];
+                    wb.cell_count[dst] = cb.count[r];
+                }
+                ++c;
+            }
+        }
+        __syncwarp();
+        const int ncell = min(32, total_sel - round);
+        if (lane < ncell) {
+            my_start = wb.cell_start[lane];
+            my_count = wb.cell_count[lane];
+        }
+        __syncwarp();
+        const int incl = warp_incl_scan(my_count, lane);
+        const int total = __shfl_sync(kFull, incl, 31);
+        const int excl = incl - my_count;
+        // bitmap of cell starts (cells are non-empty, so starts are distinct)
+        const int words = (total + 31) >> 5;
+        for (int w = lane; w < words && w < kMaxSegWords; w += 32) wb.segbits[w] = 0u;
+        __syncwarp();
+        if (lane < ncell && excl < 32 * kMaxSegWords) atomicOr(&wb.segbits[excl >> 5], 1u << (excl & 31));
+        __syncwarp();
+        int segbase = 0;     // cells starting before the current batch
+        const unsigned le = (2u << lane) - 1u;
+        for (int base = 0; base < total; base += 32) {
+            const int e = base + lane;
+            const bool valid = e < total;
+            int j;
+            unsigned w = 0u;
+            if (total <= 32 * kMaxSegWords) {
+                w = wb.segbits[base >> 5];
+                j = segbase + __popc(w & le) - 1;
+            } else {              // very large rounds: search the inclusive counts
+                j = 0;
+#pragma unroll
+                for (int step = 16; step >= 1; step >>= 1) {
+                    int v = __shfl_sync(kFull, incl, j + step - 1);
+                    if (v <= e) j += step;
+                }
+            }
+            j &= 31;
+            const int st = __shfl_sync(kFull, my_start, j);
+            const int ex = __shfl_sync(kFull, excl, j);
+            segbase += __popc(w);
+            f(__ldg(g.pts + (valid ? st + (e - ex) : 0)), valid, valid ? st + (e - ex) : 0);
+        }
+        __syncwarp();
+    }
+}
+
+// Keeps the visited words with key <= tau: the first kCap (word and sorted
+// position) go to the buffers.  Returns the number kept.  With HIST, every
+// kept key is also counted in 32 buckets (bucket = key * scale) with each
+// bucket's largest key, for tightening tau when far too many are kept.
+template <bool HIST>
+__device__ int scan_keep(const GridView &g, const Cube &cb, WarpBuf &wb, float4 q, float lim2, float tau,
+                         float scale, int lane) {
+    if (HIST) {
+        __syncwarp();
+        wb.hist[lane] = 0;
+        wb.binmax[lane] = 0u;
+        __syncwarp();
+    }
+    int S = 0;
+    for_each_point(g, cb, wb, q, lim2, lane, [&](float4 p, bool valid, int pos) {
+        const float key = rank_key(p, q.x, q.y, q.z);
+        const bool keep = valid && key <= tau;
+        const unsigned m = __ballot_sync(kFull, keep);
+        if (keep) {
+            const int slot = S + __popc(m & lanemask_lt());
+            if (slot < kCap) {
+                wb.surv[slot] = pack(key, p);
+                wb.spos[slot] = pos;
+            }
+            if (HIST) {
+                const int bin = min(31, (int)(key * scale));
+                atomicAdd(&wb.hist[bin], 1);
+                atomicMax(&wb.binmax[bin], __float_as_uint(key));
+            }
+        }
+        S += __popc(m);
+    });
+    __syncwarp();
+    return S;
+}
+
+// Histogram (count and largest key) of the first min(S, kCap) kept words in
+// 32 buckets, bucket = key * scale.
+__device__ void bucket_hist(WarpBuf &wb, int S, float scale, int lane) {
+    wb.hist[lane] = 0;
+    wb.binmax[lane] = 0u;
+    __syncwarp();
+    for (int s = lane; s < min(S, kCap); s += 32) {
+        const float key = __uint_as_float((uint32_t)(wb.surv[s] >> 32));
+        const int bin = min(31, (int)(key * scale));
+        atomicAdd(&wb.hist[bin], 1);
+        atomicMax(&wb.binmax[bin], __float_as_uint(key));
+    }
+    __syncwarp();
+}
+
+// Smallest key bound with at least k histogrammed words at or below it: the
+// largest key of the buckets up to the one where the running count reaches k.
+__device__ float tighten(const WarpBuf &wb, int k, int lane, float fallback) {
+    const int incl = warp_incl_scan(wb.hist[lane], lane);
+    const unsigned reach = __ballot_sync(kFull, incl >= k);
+    if (!reach) return fallback;
+    const int bstar = __ffs(reach) - 1;
+    unsigned mx = lane <= bstar ? wb.binmax[lane] : 0u;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(kFull, mx, o));
+    return __uint_as_float(mx);
+}
+
+// Counting sort of the S <= kCap kept words by bucket, then rank inside the
+// bucket; the first k go to the output row and their sorted positions to
+// wb.nb.  Returns the k-th key.
+__device__ float rank_and_write(WarpBuf &wb, int S, float scale, int k, int lane, int32_t qi,
+                                int32_t *__restrict__ out_idx, float *__restrict__ out_key) {
+    bucket_hist(wb, S, scale, lane);
+    const int h = wb.hist[lane];
+    wb.fill[lane] = warp_incl_scan(h, lane) - h;
+    __syncwarp();
+    for (int s = lane; s < S; s += 32) {
+        const unsigned long long v = wb.surv[s];
+        const int bin = min(31, (int)(__uint_as_float((uint32_t)(v >> 32)) * scale));
+        const int at = atomicAdd(&wb.fill[bin], 1);
+        wb.tmp[at] = v;
+        wb.tpos[at] = wb.spos[s];
+    }
+    __syncwarp();
+    for (int p = lane; p < S; p += 32) {
+        const unsigned long long v = wb.tmp[p];
+        const float key = __uint_as_float((uint32_t)(v >> 32));
+        const int bin = min(31, (int)(key * scale));
+        const int end = wb.fill[bin], beg = end - wb.hist[bin];
+        int rank = beg;
+        for (int t = beg; t < end; ++t) rank += wb.tmp[t] < v;
+        if (rank < k) {
+            out_idx[(int64_t)qi * k + rank] = (int32_t)(uint32_t)v;
+            if (out_key) out_key[(int64_t)qi * k + rank] = key;
+            wb.nb[rank] = wb.tpos[p];
+            if (rank == k - 1) wb.kth = key;
+        }
+    }
+    if (lane == 0) wb.nprev = S;
+    __syncwarp();
+    return wb.kth;
+}
+
+// Sorted insertion list over the lanes (entry r * 32 + lane in register r),
+// the fallback when too many words share the smallest keys.
 template <int KPL>
 struct TopK {
-    uint64_t e[KPL];
-    uint64_t kth;
+    unsigned long long e[KPL];
+    int pos[KPL];
+    unsigned long long kth;
 
     __device__ void init() {
 #pragma unroll
-        for (int r = 0; r < KPL; ++r) e[r] = ~0ull;
+        for (int r = 0; r < KPL; ++r) {
+            e[r] = ~0ull;
+            pos[r] = 0;
+        }
         kth = ~0ull;
     }
 
-    // Insert the candidates of the warp (one per lane, ~0 for none) that beat
-    // the current k-th entry, one at a time.
-    __device__ void offer(uint64_t cand, int k, int lane) {
+    __device__ void offer(unsigned long long cand, int cpos, int k, int lane) {
         unsigned m = __ballot_sync(kFull, cand < kth);
         while (m) {
-            int src = __ffs(m) - 1;
-            uint64_t c = __shfl_sync(kFull, cand, src);
-            int pos = 0;
+            const int src = __ffs(m) - 1;
+            const unsigned long long c = __shfl_sync(kFull, cand, src);
+            const int cp = __shfl_sync(kFull, cpos, src);
+            int at = 0;
 #pragma unroll
-            for (int r = 0; r < KPL; ++r) pos += __popc(__ballot_sync(kFull, e[r] < c));
-            uint64_t up[KPL];
+            for (int r = 0; r < KPL; ++r) at += __popc(__ballot_sync(kFull, e[r] < c));
+            unsigned long long up[KPL];
+            int upp[KPL];
 #pragma unroll
-            for (int r = 0; r < KPL; ++r) up[r] = __shfl_up_sync(kFull, e[r], 1);
+            for (int r = 0; r < KPL; ++r) {
+                up[r] = __shfl_up_sync(kFull, e[r], 1);
+                upp[r] = __shfl_up_sync(kFull, pos[r], 1);
+            }
 #pragma unroll
             for (int r = 1; r < KPL; ++r) {
-                uint64_t carry = __shfl_sync(kFull, e[r - 1], 31);
-                if (lane == 0) up[r] = carry;
+                const unsigned long long carry = __shfl_sync(kFull, e[r - 1], 31);
+                const int carryp = __shfl_sync(kFull, pos[r - 1], 31);
+                if (lane == 0) {
+                    up[r] = carry;
+                    upp[r] = carryp;
+                }
             }
 #pragma unroll
             for (int r = 0; r < KPL; ++r) {
-                int idx = r * 32 + lane;
-                e[r] = idx > pos ? up[r] : (idx == pos ? c : e[r]);
+                const int idx = r * 32 + lane;
+                if (idx > at) {
+                    e[r] = up[r];
+                    pos[r] = upp[r];
+                } else if (idx == at) {
+                    e[r] = c;
+                    pos[r] = cp;
+                }
             }
             const int kr = (k - 1) >> 5, kl = (k - 1) & 31;
-            uint64_t kv = e[0];
+            unsigned long long kv = e[0];
 #pragma unroll
             for (int r = 1; r < KPL; ++r)
                 if (r == kr) kv = e[r];
@@ -79,144 +407,272 @@ struct TopK {
     }
 };
 
-// Range of the cell at level `lev` with integer coordinates c (any may be out
-// of the grid): start and count, count 0 when empty or outside.
-__device__ __forceinline__ void cell_range(const GridView &g, int lev, int cx, int cy, int cz, int &start,
-                                           int &count) {
-    start = 0;
-    count = 0;
-    const int dims = (int)(kAxisCells >> lev);
-    if (cx < 0 || cy < 0 || cz < 0 || cx >= dims || cy >= dims || cz >= dims) return;
-    const LevelTable &t = g.level[lev];
-    int32_t id = lookup_cell(t, morton3((uint32_t)cx, (uint32_t)cy, (uint32_t)cz));
-    if (id < 0) return;
-    start = __ldg(t.cell_start + id);
-    count = __ldg(t.cell_start + id + 1) - start;
+template <int KPL>
+__device__ float insertion_fallback(const GridView &g, const Cube &cb, WarpBuf &wb, float4 q, float lim2, float tau,
+                                    int k, int lane, int32_t qi, int32_t *__restrict__ out_idx,
+                                    float *__restrict__ out_key) {
+    TopK<KPL> top;
+    top.init();
+    for_each_point(g, cb, wb, q, lim2, lane, [&](float4 p, bool valid, int pos) {
+        const float key = rank_key(p, q.x, q.y, q.z);
+        top.offer(valid && key <= tau ? pack(key, p) : ~0ull, pos, k, lane);
+    });
+#pragma unroll
+    for (int r = 0; r < KPL; ++r) {
+        const int e = r * 32 + lane;
+        if (e < k) {
+            out_idx[(int64_t)qi * k + e] = (int32_t)(uint32_t)top.e[r];
+            if (out_key) out_key[(int64_t)qi * k + e] = __uint_as_float((uint32_t)(top.e[r] >> 32));
+            wb.nb[e] = top.pos[r];
+            wb.tpos[e] = top.pos[r];
+        }
+    }
+    if (lane == 0) wb.nprev = k;
+    __syncwarp();
+    return __uint_as_float((uint32_t)(top.kth >> 32));
 }
 
-// Scan the points of up to 32 cells (one per lane) and offer them to the list.
-template <int KPL>
-__device__ void scan_cells(const GridView &g, int start, int count, float qx, float qy, float qz, int k,
-                           int lane, TopK<KPL> &top) {
-    int incl = count;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        int y = __shfl_up_sync(kFull, incl, o);
-        if (lane >= o) incl += y;
-    }
-    const int total = __shfl_sync(kFull, incl, 31);
-    for (int base = 0; base < total; base += 32) {
-        const int e = base + lane;
-        int j = 0;    // number of cells whose inclusive count is <= e
-#pragma unroll
-        for (int step = 16; step >= 1; step >>= 1) {
-            int v = __shfl_sync(kFull, incl, j + step - 1);
-            if (v <= e) j += step;
-        }
-        const int st_j = __shfl_sync(kFull, start, j & 31);
-        const int in_j = __shfl_sync(kFull, incl, j & 31);
-        const int ct_j = __shfl_sync(kFull, count, j & 31);
-        uint64_t cand = ~0ull;
-        if (e < total) {
-            float4 p = __ldg(g.pts + st_j + (e - (in_j - ct_j)));
-            float key = rank_key(p, qx, qy, qz);
-            cand = ((uint64_t)__float_as_uint(key) << 32) | (uint32_t)__float_as_int(p.w);
-        }
-        top.offer(cand, k, lane);
-    }
+// Key bound from an earlier query p (its k-th key kappa): its k neighbours
+// are within sqrt(kappa) + |q - p| of q.
+__device__ __forceinline__ float chain_bound(float4 q, float4 p, float kappa) {
+    const float dx = q.x - p.x, dy = q.y - p.y, dz = q.z - p.z;
+    const float d = sqrtf(dx * dx + dy * dy + dz * dz) * kGrow;
+    const float R = (sqrtf(kappa) * kGrow + d) * kGrow;
+    return R * R * kGrow * kGrow;
 }
 
+// Key bound from the previous query's kept words (wb.nprev of them, sorted
+// positions in wb.tpos, its k neighbours among them): the k-th smallest of
+// their keys seen from q, to bucket precision (real points, so no margin).
 template <int KPL>
-__global__ void __launch_bounds__(kKnnThreads) k_knn(GridView g, int k, int32_t *__restrict__ out_idx,
-                                                     float *__restrict__ out_key) {
-    const int lane = threadIdx.x & 31;
-    const int64_t warps = (int64_t)gridDim.x * (kKnnThreads / 32);
-    for (int64_t sp = (blockIdx.x * (int64_t)kKnnThreads + threadIdx.x) >> 5; sp < g.n; sp += warps) {
-        const float4 q = __ldg(g.pts + sp);
-        const int32_t qi = __float_as_int(q.w);
-        uint32_t c0[3];
-        double frac[3];
-        c0[0] = cell_coord(q.x, g.frame.origin[0], g.frame.inv_s0, &frac[0]);
-        c0[1] = cell_coord(q.y, g.frame.origin[1], g.frame.inv_s0, &frac[1]);
-        c0[2] = cell_coord(q.z, g.frame.origin[2], g.frame.inv_s0, &frac[2]);
+__device__ float survivor_bound(const GridView &g, WarpBuf &wb, float4 q, int k, int lane) {
+    const int S = wb.nprev;
+    float key[kCap / 32];
+    float mx = 0.f;
+#pragma unroll
+    for (int r = 0; r < kCap / 32; ++r) {
+        const int e = r * 32 + lane;
+        key[r] = e < S ? rank_key(__ldg(g.pts + wb.tpos[e]), q.x, q.y, q.z) : INFINITY;
+        if (e < S) mx = fmaxf(mx, key[r]);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(kFull, mx, o));
+    __syncwarp();
+    wb.hist[lane] = 0;
+    wb.binmax[lane] = 0u;
+    __syncwarp();
+    const float scale = mx > 0.f ? 32.0f / mx : 0.f;
+#pragma unroll
+    for (int r = 0; r < kCap / 32; ++r)
+        if (r * 32 + lane < S) {
+            const int bin = min(31, (int)(key[r] * scale));
+            atomicAdd(&wb.hist[bin], 1);
+            atomicMax(&wb.binmax[bin], __float_as_uint(key[r]));
+        }
+    __syncwarp();
+    return tighten(wb, k, lane, mx);
+}
 
-        // level: coarsen while the 27 cells around the query hold fewer than k points
+// Key bound from the previous query's neighbours: the largest of their keys
+// seen from q (k real points, so no margin is needed).
+template <int KPL>
+__device__ __forceinline__ float neighbour_bound(const GridView &g, const WarpBuf &wb, float4 q, int k, int lane) {
+    float mx = 0.f;
+#pragma unroll
+    for (int r = 0; r < KPL; ++r) {
+        const int e = r * 32 + lane;
+        if (e < k) mx = fmaxf(mx, rank_key(__ldg(g.pts + wb.nb[e]), q.x, q.y, q.z));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(kFull, mx, o));
+    return mx;
+}
+
+// The warp search for one query (lanes over candidates): the query's own key
+// bound (from the 5x5x5 cube of the finest level holding k points) unless a
+// finite tau_in is given, then the cube search with culling, tightening and,
+// as a last resort, the sorted insertion list.  Returns the k-th key.
+template <int KPL>
+__device__ __noinline__ float solve_query(const GridView &g, WarpBuf &wb, Cube &cb, float4 q, int32_t qi,
+                                          const uint32_t c0[3], float tau, int k, int lane, bool may_defer,
+                                          int32_t *__restrict__ out_idx, float *__restrict__ out_key) {
+    const float eps2 = 2.0f * g.frame.eps;
+    if (!(tau < INFINITY)) {
+        // fresh bound: coarsen until the cube holds k points, then take the
+        // cells nearest to the query that hold 2k of them
         int lev = g.base_level;
-        int start = 0, count = 0;
-        const int bx = lane % 3 - 1, by = (lane / 3) % 3 - 1, bz = lane / 9 - 1;
-        for (;;) {
-            start = count = 0;
-            if (lane < 27)
-                cell_range(g, lev, (int)(c0[0] >> lev) + bx, (int)(c0[1] >> lev) + by,
-                           (int)(c0[2] >> lev) + bz, start, count);
-            int tot = warp_sum(count);
-            if (tot >= k || lev >= g.top_level) break;
-            ++lev;
+        for (;; ++lev) {
+            load_cube(g, lev, c0, cb, lane);
+            if (cb.M >= k || lev >= g.top_level) break;
         }
-        TopK<KPL> top;
-        top.init();
-        scan_cells<KPL>(g, start, count, q.x, q.y, q.z, k, lane, top);
+        // a sparse neighbourhood (two levels above the base) is left to the
+        // pass that shares such queries among all warps
+        if (may_defer && lev > g.base_level + 1) return NAN;
+        const float S = g.side[lev];
+        // count-weighted histogram of cell distances over [0, 3S)
+        __syncwarp();
+        wb.hist[lane] = 0;
+        __syncwarp();
+        const float dscale = 32.0f / (3.0f * S);
+#pragma unroll
+        for (int r = 0; r < kSlots; ++r)
+            if (cb.count[r] > 0)
+                atomicAdd(&wb.hist[min(31, (int)(sqrtf(cell_dist2(g, cb, r, lane, q)) * dscale))], cb.count[r]);
+        __syncwarp();
+        const int need = min(2 * k, cb.M);
+        const unsigned ok = __ballot_sync(kFull, warp_incl_scan(wb.hist[lane], lane) >= need);
+        __syncwarp();
+        // bucket 31 also holds every farther cell: then take them all
+        const bool all = __ffs(ok) >= 32;
+        const float rstar = (float)(__ffs(ok)) / dscale;
+        const float lim = (rstar + eps2) * kGrow;
+        const float lim2 = all ? INFINITY : lim * lim;
+        // every visited point lies within lim + sqrt(3) S of q (any cube point
+        // within 3 sqrt(3) S < 5.2 S): bucket all their keys over [0, hi]
+        const float far = ((all ? 5.2f * S : lim) + 1.7320509f * S + eps2) * kGrow * kGrow;
+        const float hi = far * far * kGrow;
+        scan_keep<true>(g, cb, wb, q, lim2, INFINITY, hi > 0.f ? 32.0f / hi : 0.f, lane);
+        tau = tighten(wb, k, lane, hi);
+    }
+    bool full_hist = false;
+    for (int iter = 0;; ++iter) {
+        // finest level whose cube (radius two cells) holds the search ball
+        const float reach = sqrtf(tau) * kGrow * kGrow + eps2;
+        int lev = g.base_level;
+        while (lev < g.top_level && !(2.0f * g.side[lev] > reach)) ++lev;
+        load_cube(g, lev, c0, cb, lane);
+        const float lim = (reach + eps2) * kGrow;
+        const float lim2 = lim * lim;
+        const float scale = tau > 0.f ? 32.0f / tau : 0.f;
+        const int S = full_hist ? scan_keep<true>(g, cb, wb, q, lim2, tau, scale, lane)
+                                : scan_keep<false>(g, cb, wb, q, lim2, tau, scale, lane);
+        if (S >= k && S <= kCap) return rank_and_write(wb, S, scale, k, lane, qi, out_idx, out_key);
+        if (S < k) {            // cannot happen for a valid bound: search everything
+            tau = INFINITY;
+            full_hist = false;
+            continue;
+        }
+        if (iter >= 8) return insertion_fallback<KPL>(g, cb, wb, q, lim2, tau, k, lane, qi, out_idx, out_key);
+        if (full_hist) {        // buckets over every kept word: each round cuts ~32x
+            tau = tighten(wb, k, lane, tau);
+            full_hist = false;
+        } else if (S <= 2 * kCap) {
+            // a mild overflow: the first kCap kept words (real points) bound it
+            bucket_hist(wb, S, scale, lane);
+            tau = tighten(wb, k, lane, tau);
+        } else {
+            full_hist = true;   // rescan with buckets over all kept words
+        }
+    }
+}
 
-        const int C[3] = {(int)(c0[0] >> lev), (int)(c0[1] >> lev), (int)(c0[2] >> lev)};
-        const int dims = (int)(kAxisCells >> lev);
-        const double S = ldexp(g.frame.s0, lev);
-        double t[3];
-#pragma unroll
-        for (int a = 0; a < 3; ++a) t[a] = ((double)(c0[a] & ((1u << lev) - 1u)) + frac[a]) / (double)(1u << lev);
+// ---- chains: one query per warp -----------------------------------------
+//
+// A warp takes chunks of 128 consecutive queries from a global counter.  The
+// bound for a query comes from the query before it: the k-th smallest key,
+// seen from the new query, of the points that query kept (its k neighbours
+// among them), and the triangle bound from the query before that.  A fresh
+// bound is computed when there is no earlier query, or the bound is more than
+// 9 times the previous query's own k-th key or reaches past four base cells.
+// Queries in sparse regions (their fresh bound needs a level two above the
+// base) are appended to a list and solved afterwards by k_knn_sparse, where
+// all warps share them: they cost far more than the rest and would otherwise
+// leave a few warps running long after the others.
+//
+// work[0]: next chunk; work[1]: deferred count; work[2]: next deferred;
+// work[8 ...]: sorted positions of the deferred queries.
 
-        for (int L = 1;; ++L) {
-            // lower bound on the distance to any point outside the block of radius L
-            double dmin = INFINITY;
-#pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                if (C[a] - L > 0) dmin = fmin(dmin, (L + t[a]) * S);
-                if (C[a] + L < dims - 1) dmin = fmin(dmin, (L + 1 - t[a]) * S);
+constexpr int kChainThreads = 256;
+constexpr int kChainWarps = kChainThreads / 32;
+
+__device__ __forceinline__ int warp_take(int *counter, int lane) {
+    int v = 0;
+    if (lane == 0) v = atomicAdd(counter, 1);
+    return __shfl_sync(kFull, v, 0);
+}
+
+template <int KPL>
+__global__ void __launch_bounds__(kChainThreads) k_knn_chain(GridView g, int k, int *__restrict__ work,
+                                                            int32_t *__restrict__ out_idx,
+                                                            float *__restrict__ out_key) {
+    __shared__ WarpBuf bufs[kChainWarps];
+    const int lane = threadIdx.x & 31;
+    WarpBuf &wb = bufs[threadIdx.x >> 5];
+    const int64_t n_chunks = (g.n + kChunk - 1) / kChunk;
+    const float big = 16.0f * g.side[g.base_level] * g.side[g.base_level];
+    Cube cb;
+    for (int64_t chunk = warp_take(&work[0], lane); chunk < n_chunks; chunk = warp_take(&work[0], lane)) {
+        // the previous query (its kept points in wb, k-th key k1, position
+        // p1) and the one before it (position p2, k-th key k2)
+        int n_prev = 0;
+        float4 p1 = make_float4(0.f, 0.f, 0.f, 0.f), p2 = p1;
+        float k1 = 0.f, k2 = 0.f;
+        const int64_t end = min((int64_t)g.n, (chunk + 1) * kChunk);
+        for (int64_t sp = chunk * kChunk; sp < end; ++sp) {
+            const float4 q = __ldg(g.pts + sp);
+            const uint64_t key0 = __ldg(g.keys + sp);
+            const uint32_t c0[3] = {compact3(key0), compact3(key0 >> 1), compact3(key0 >> 2)};
+            float tau = INFINITY;
+            if (n_prev >= 1) tau = survivor_bound<KPL>(g, wb, q, k, lane);
+            if (n_prev >= 2) tau = fminf(tau, chain_bound(q, p2, k2));
+            // a bound far above the previous query's, or reaching past four
+            // base cells, would search a large region: start afresh instead
+            if (n_prev == 0 || tau > 9.0f * k1 || tau > big) tau = INFINITY;
+            const float kth =
+                solve_query<KPL>(g, wb, cb, q, __float_as_int(q.w), c0, tau, k, lane, true, out_idx, out_key);
+            if (isnan(kth)) {
+                if (lane == 0) work[8 + atomicAdd(&work[1], 1)] = (int)sp;
+                n_prev = 0;
+                continue;
             }
-            if (dmin == INFINITY) break;                       // the whole grid is searched
-            if (top.kth != ~0ull) {
-                double kth_key = (double)__uint_as_float((uint32_t)(top.kth >> 32));
-                if (kth_key < dmin * dmin * (1.0 - 0x1p-20)) break;
-            }
-            // shell of radius L + 1
-            const int R = L + 1, m = 2 * R + 1, m3 = m * m * m;
-            for (int base = 0; base < m3; base += 32) {
-                const int li = base + lane;
-                start = count = 0;
-                if (li < m3) {
-                    const int dx = li % m - R, dy = (li / m) % m - R, dz = li / (m * m) - R;
-                    const int cheb = max(abs(dx), max(abs(dy), abs(dz)));
-                    if (cheb == R) cell_range(g, lev, C[0] + dx, C[1] + dy, C[2] + dz, start, count);
-                }
-                if (__ballot_sync(kFull, count > 0))
-                    scan_cells<KPL>(g, start, count, q.x, q.y, q.z, k, lane, top);
-            }
+            p2 = p1;
+            k2 = k1;
+            p1 = q;
+            k1 = kth;
+            n_prev = min(n_prev + 1, 2);
         }
-#pragma unroll
-        for (int r = 0; r < KPL; ++r) {
-            const int e = r * 32 + lane;
-            if (e < k) {
-                out_idx[(int64_t)qi * k + e] = (int32_t)(uint32_t)top.e[r];
-                if (out_key) out_key[(int64_t)qi * k + e] = __uint_as_float((uint32_t)(top.e[r] >> 32));
-            }
-        }
+    }
+}
+
+template <int KPL>
+__global__ void __launch_bounds__(kChainThreads) k_knn_sparse(GridView g, int k, int *__restrict__ work,
+                                                             int32_t *__restrict__ out_idx,
+                                                             float *__restrict__ out_key) {
+    __shared__ WarpBuf bufs[kChainWarps];
+    const int lane = threadIdx.x & 31;
+    WarpBuf &wb = bufs[threadIdx.x >> 5];
+    const int count = work[1];
+    Cube cb;
+    for (int i = warp_take(&work[2], lane); i < count; i = warp_take(&work[2], lane)) {
+        const int64_t sp = work[8 + i];
+        const float4 q = __ldg(g.pts + sp);
+        const uint64_t key0 = __ldg(g.keys + sp);
+        const uint32_t c0[3] = {compact3(key0), compact3(key0 >> 1), compact3(key0 >> 2)};
+        solve_query<KPL>(g, wb, cb, q, __float_as_int(q.w), c0, INFINITY, k, lane, false, out_idx, out_key);
     }
 }
 
 }  // namespace
 
 int launch_knn(const mls_grid *grid, int k, int32_t *idx, float *key, cudaStream_t st) {
-    int64_t n = grid->n;
-    int64_t blocks = (n * 32 + kKnnThreads - 1) / kKnnThreads;
+    const int64_t n = grid->n;
     int dev = 0, sms = 152;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int64_t cap = (int64_t)sms * 8 * 16;
+    const int64_t chunks = (n + kChunk - 1) / kChunk;
+    int64_t blocks = (chunks + kChainWarps - 1) / kChainWarps;
+    const int64_t cap = (int64_t)sms * 4;      // one resident wave; chunks are taken dynamically
     if (blocks > cap) blocks = cap;
-    if (k <= 32)
-        k_knn<1><<<(int)blocks, kKnnThreads, 0, st>>>(grid->view, k, idx, key);
-    else
-        k_knn<2><<<(int)blocks, kKnnThreads, 0, st>>>(grid->view, k, idx, key);
-    count_launches(1);
+    const int sparse_blocks = sms * 4;
+    MLS_CUDA_TRY(cudaMemsetAsync(grid->work, 0, 8 * sizeof(int), st));
+    if (k <= 32) {
+        k_knn_chain<1><<<(int)blocks, kChainThreads, 0, st>>>(grid->view, k, grid->work, idx, key);
+        k_knn_sparse<1><<<sparse_blocks, kChainThreads, 0, st>>>(grid->view, k, grid->work, idx, key);
+    } else {
+        k_knn_chain<2><<<(int)blocks, kChainThreads, 0, st>>>(grid->view, k, grid->work, idx, key);
+        k_knn_sparse<2><<<sparse_blocks, kChainThreads, 0, st>>>(grid->view, k, grid->work, idx, key);
+    }
+    count_launches(2);
     MLS_CUDA_TRY(cudaGetLastError());
     return MLS_OK;
 }

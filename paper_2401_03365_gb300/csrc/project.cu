@@ -9,6 +9,7 @@
 // accesses); pass B accumulates the covariance about the weighted centroid;
 // pass C accumulates the 15 monomial moments and 6 right-hand sides of the
 // degree-2 normal equations in local coordinates scaled by 1/h.
+#include <algorithm>
 #include <cfloat>
 
 #include "common.cuh"
@@ -18,7 +19,7 @@ namespace mls {
 namespace {
 
 constexpr int kProjThreads = 128;
-constexpr float kMixedGapFlag = 1e-2f;     // FP32 eigensolve trusted above this gap ratio
+constexpr float kMixedGapFlag = 1e-3f;     // FP32 eigensolve trusted above this gap ratio
 constexpr float kMixedCondFlag = 1e5f;     // FP32 Cholesky trusted below this condition estimate
 
 template <int DEG>
@@ -224,52 +225,69 @@ __device__ int frame_from(const T C[6], T nrm[3], T e1[3], T e2[3], T lam[3]) {
     return 0;
 }
 
+// Copy of the points as float4 (w = 0): one 16-byte load per neighbour gather.
+__global__ void k_pack_xyz4(const float *__restrict__ xyz, int64_t n, float4 *__restrict__ xyz4) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        xyz4[i] = make_float4(xyz[3 * i], xyz[3 * i + 1], xyz[3 * i + 2], 0.f);
+}
+
+// FP32 / mixed projection, one thread per point.  The warp first copies its
+// 32 neighbour rows into shared memory with coalesced loads (stored
+// transposed, entry j of lane t at j * 32 + t).  Pass 1 gathers each
+// neighbour once and accumulates the weight, the weighted centroid offset and
+// the covariance about it with the weighted online update of West (1979):
+// with W' = W + w, delta = d - m: m += delta w / W', C += (W w / W') delta
+// delta^T -- as accurate as a second centred pass, without storing d.
+// Pass 2 gathers again (now from L1) for the height-fit moments.
 template <int DEG, int PREC>
-__global__ void __launch_bounds__(kProjThreads) k_project(const float *__restrict__ xyz, int64_t n,
+__global__ void __launch_bounds__(kProjThreads) k_project(const float4 *__restrict__ xyz4, int64_t n,
                                                           const int32_t *__restrict__ idx, int k, float h,
                                                           const int32_t *__restrict__ order,
                                                           float *__restrict__ out_xyz, float *__restrict__ out_n,
                                                           uint8_t *__restrict__ status) {
-    extern __shared__ float4 stage[];
+    extern __shared__ int32_t rows[];
+    const int lane = threadIdx.x & 31;
+    int32_t *my_rows = rows + (threadIdx.x >> 5) * k * 32;
     const int64_t slot = blockIdx.x * (int64_t)kProjThreads + threadIdx.x;
+    const int64_t warp_base = slot - lane;
+    const int64_t i = slot < n ? (order ? (int64_t)__ldg(order + slot) : slot) : -1;
+    const int nrows = (int)min((int64_t)32, n - warp_base);
+#pragma unroll 8
+    for (int r = 0; r < 32; ++r) {
+        const int64_t i_r = __shfl_sync(0xffffffffu, i, r);
+        if (r < nrows)
+            for (int c = lane; c < k; c += 32) my_rows[c * 32 + r] = __ldg(idx + i_r * k + c);
+    }
+    __syncwarp();
     if (slot >= n) return;
-    const int64_t i = order ? (int64_t)order[slot] : slot;
-    const float rx = xyz[3 * i], ry = xyz[3 * i + 1], rz = xyz[3 * i + 2];
-    const int32_t *row = idx + i * k;
-    float4 *my = stage + threadIdx.x;
+    const float4 r4 = __ldg(xyz4 + i);
+    const float rx = r4.x, ry = r4.y, rz = r4.z;
     // exp(-|d|^2 / h^2) = exp2(-|d|^2 * log2(e) / h^2)
     const float neg_scale = -1.4426950408889634f / (h * h);
 
-    // pass A: weights and weighted centroid offset m = sum w d / W
-    float W = 0.f, sx = 0.f, sy = 0.f, sz = 0.f;
-#pragma unroll 4
-    for (int j = 0; j < k; ++j) {
-        const int64_t p = __ldg(row + j);
-        const float dx = __ldg(xyz + 3 * p) - rx, dy = __ldg(xyz + 3 * p + 1) - ry, dz = __ldg(xyz + 3 * p + 2) - rz;
-        const float w = exp2f(fmaf(dx, dx, fmaf(dy, dy, dz * dz)) * neg_scale);
-        W += w;
-        sx = fmaf(w, dx, sx);
-        sy = fmaf(w, dy, sy);
-        sz = fmaf(w, dz, sz);
-        my[j * kProjThreads] = make_float4(dx, dy, dz, w);
-    }
-    const float invW = 1.f / W;
-    const float mx = sx * invW, my_ = sy * invW, mz = sz * invW;
-
-    // pass B: covariance about the weighted centroid (unnormalised: the
-    // eigenvectors and the ratio tests do not depend on the 1/W factor)
+    // pass 1: weight W, centroid offset m, covariance C (unnormalised)
+    float W = 0.f, mx = 0.f, my = 0.f, mz = 0.f;
     float C[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
 #pragma unroll 4
     for (int j = 0; j < k; ++j) {
-        const float4 v = my[j * kProjThreads];
-        const float ex = v.x - mx, ey = v.y - my_, ez = v.z - mz;
-        const float wx = v.w * ex, wy = v.w * ey, wz = v.w * ez;
-        C[0] = fmaf(wx, ex, C[0]);
-        C[1] = fmaf(wx, ey, C[1]);
-        C[2] = fmaf(wx, ez, C[2]);
-        C[3] = fmaf(wy, ey, C[3]);
-        C[4] = fmaf(wy, ez, C[4]);
-        C[5] = fmaf(wz, ez, C[5]);
+        const float4 p = __ldg(xyz4 + my_rows[j * 32 + lane]);
+        const float dx = p.x - rx, dy = p.y - ry, dz = p.z - rz;
+        const float w = exp2f(fmaf(dx, dx, fmaf(dy, dy, dz * dz)) * neg_scale);
+        const float Wn = W + w;
+        const float c = __fdividef(w, Wn);
+        const float ex = dx - mx, ey = dy - my, ez = dz - mz;
+        mx = fmaf(ex, c, mx);
+        my = fmaf(ey, c, my);
+        mz = fmaf(ez, c, mz);
+        const float f = W * c;
+        const float fx = f * ex, fy = f * ey, fz = f * ez;
+        C[0] = fmaf(fx, ex, C[0]);
+        C[1] = fmaf(fx, ey, C[1]);
+        C[2] = fmaf(fx, ez, C[2]);
+        C[3] = fmaf(fy, ey, C[3]);
+        C[4] = fmaf(fy, ez, C[4]);
+        C[5] = fmaf(fz, ez, C[5]);
+        W = Wn;
     }
     uint8_t st = 0;
     float nf[3], e1f[3], e2f[3];
@@ -295,11 +313,11 @@ __global__ void __launch_bounds__(kProjThreads) k_project(const float *__restric
     }
     float px = rx, py = ry, pz = rz;
     if (!(st & MLS_PT_PLANE_DEGENERATE)) {
-        const float ofs = nf[0] * mx + nf[1] * my_ + nf[2] * mz;
+        const float ofs = nf[0] * mx + nf[1] * my + nf[2] * mz;
         const float ih = 1.f / h;
         const float a1x = e1f[0] * ih, a1y = e1f[1] * ih, a1z = e1f[2] * ih;
         const float a2x = e2f[0] * ih, a2y = e2f[1] * ih, a2z = e2f[2] * ih;
-        // pass C: moments of the height fit
+        // pass 2: moments of the height fit
         float mom[15], rhs[6];
 #pragma unroll
         for (int c = 0; c < 15; ++c) mom[c] = 0.f;
@@ -307,15 +325,16 @@ __global__ void __launch_bounds__(kProjThreads) k_project(const float *__restric
         for (int c = 0; c < 6; ++c) rhs[c] = 0.f;
 #pragma unroll 2
         for (int j = 0; j < k; ++j) {
-            const float4 v = my[j * kProjThreads];
-            const float w = v.w;
-            const float f = fmaf(nf[2], v.z, fmaf(nf[1], v.y, fmaf(nf[0], v.x, -ofs)));
+            const float4 p = __ldg(xyz4 + my_rows[j * 32 + lane]);
+            const float dx = p.x - rx, dy = p.y - ry, dz = p.z - rz;
+            const float w = exp2f(fmaf(dx, dx, fmaf(dy, dy, dz * dz)) * neg_scale);
+            const float f = fmaf(nf[2], dz, fmaf(nf[1], dy, fmaf(nf[0], dx, -ofs)));
             const float wf = w * f;
             mom[0] += w;
             rhs[0] += wf;
             if (DEG >= 1) {
-                const float u = fmaf(a1z, v.z, fmaf(a1y, v.y, a1x * v.x));
-                const float vv = fmaf(a2z, v.z, fmaf(a2y, v.y, a2x * v.x));
+                const float u = fmaf(a1z, dz, fmaf(a1y, dy, a1x * dx));
+                const float vv = fmaf(a2z, dz, fmaf(a2y, dy, a2x * dx));
                 const float wu = w * u, wv = w * vv;
                 mom[1] += wu;
                 mom[2] += wv;
@@ -467,19 +486,25 @@ int launch_deg(const float *xyz, int64_t n, const int32_t *idx, int k, float h, 
     const int blocks = (int)((n + kProjThreads - 1) / kProjThreads);
     if (precision == MLS_PREC_FP64) {
         k_project_fp64<DEG><<<blocks, kProjThreads, 0, st>>>(xyz, n, idx, k, h, order, out_xyz, out_n, status);
+        count_launches(1);
     } else {
-        const size_t smem = (size_t)k * kProjThreads * sizeof(float4);
+        // a stream-ordered scratch copy of the points as float4
+        float4 *xyz4 = nullptr;
+        MLS_CUDA_TRY(cudaMallocAsync((void **)&xyz4, (size_t)n * sizeof(float4), st));
+        k_pack_xyz4<<<(int)std::min<int64_t>((n + 255) / 256, 152 * 16), 256, 0, st>>>(xyz, n, xyz4);
+        const size_t smem = (size_t)k * 32 * sizeof(int32_t) * (kProjThreads / 32);
         if (precision == MLS_PREC_MIXED) {
             auto kern = k_project<DEG, MLS_PREC_MIXED>;
             MLS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            kern<<<blocks, kProjThreads, smem, st>>>(xyz, n, idx, k, h, order, out_xyz, out_n, status);
+            kern<<<blocks, kProjThreads, smem, st>>>(xyz4, n, idx, k, h, order, out_xyz, out_n, status);
         } else {
             auto kern = k_project<DEG, MLS_PREC_FP32>;
             MLS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            kern<<<blocks, kProjThreads, smem, st>>>(xyz, n, idx, k, h, order, out_xyz, out_n, status);
+            kern<<<blocks, kProjThreads, smem, st>>>(xyz4, n, idx, k, h, order, out_xyz, out_n, status);
         }
+        count_launches(2);
+        MLS_CUDA_TRY(cudaFreeAsync(xyz4, st));
     }
-    count_launches(1);
     MLS_CUDA_TRY(cudaGetLastError());
     return MLS_OK;
 }

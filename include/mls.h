@@ -151,6 +151,28 @@ int mls_project(const float *d_xyz, int64_t n, const int32_t *d_idx, int k, floa
                 uint8_t *d_status, mls_stream stream);
 
 /*
+ * mls_project_backward -- vector-Jacobian product of mls_project (not in the
+ * paper): with cotangents gp (of the projected points) and gn (of the
+ * normals), the gradients of L = sum_i <gp_i, p'_i> + <gn_i, n_i> with
+ * respect to every coordinate and to h, neighbour rows and normal signs held
+ * fixed.  Points whose plane is degenerate pass gp to their own position only
+ * (their normal counts as constant); with a singular height fit the fitted
+ * height counts as zero, as in the forward.
+ *
+ *   d_xyz, n, d_idx, k, h, degree, precision, d_order   as for mls_project
+ *                    (MLS_PREC_FP64 runs the mixed form)
+ *   d_grad_out_xyz     device, n x 3 floats: gp
+ *   d_grad_out_normal  device, n x 3 floats or NULL (zero)
+ *   d_grad_xyz         device, n x 3 floats, overwritten: dL/dx
+ *   d_grad_h           device, 1 float, overwritten: dL/dh
+ * Deterministic: edge contributions are summed in a fixed order.  Uses
+ * stream-ordered scratch (cudaMallocAsync) of about n * (28 + 16 k) bytes.
+ */
+int mls_project_backward(const float *d_xyz, int64_t n, const int32_t *d_idx, int k, float h, int degree,
+                         int precision, const int32_t *d_order, const float *d_grad_out_xyz,
+                         const float *d_grad_out_normal, float *d_grad_xyz, float *d_grad_h, mls_stream stream);
+
+/*
  * mls_mean_knn_dist -- bandwidth helper (not in the paper): the mean distance,
  * in FP64, from each point to the entries of its neighbour row other than
  * itself.  Writes one double to d_out (device).  Typical use: h = 2 * value.

@@ -17,7 +17,7 @@ from .build import library_path
 
 __all__ = [
     "MLSError", "Grid", "lib", "mls_build_grid", "mls_grid_destroy", "mls_grid_size", "mls_grid_order",
-    "mls_knn", "mls_project", "mls_mean_knn_dist", "mls_status_str", "mls_last_error", "mls_kernel_launches",
+    "mls_knn", "mls_project", "mls_project_backward", "mls_mean_knn_dist", "mls_status_str", "mls_last_error", "mls_kernel_launches",
     "PRECISION", "MLS_MAX_K", "MLS_PT_OK", "MLS_PT_PLANE_DEGENERATE", "MLS_PT_POLY_SINGULAR",
     "MLS_PT_FP64_USED", "EXPORTED_SYMBOLS",
 ]
@@ -39,6 +39,7 @@ _SIGNATURES = [
     ("mls_grid_order", _vp, [_vp]),
     ("mls_knn", _int, [_vp, _int, _vp, _vp, _vp]),
     ("mls_project", _int, [_vp, _i64, _vp, _int, _flt, _int, _int, _vp, _vp, _vp, _vp, _vp]),
+    ("mls_project_backward", _int, [_vp, _i64, _vp, _int, _flt, _int, _int, _vp, _vp, _vp, _vp, _vp, _vp]),
     ("mls_mean_knn_dist", _int, [_vp, _i64, _vp, _int, _vp, _vp]),
     ("mls_kernel_launches", _i64, []),
     ("mls_last_error", ctypes.c_char_p, []),
@@ -218,6 +219,33 @@ def mls_project(xyz: torch.Tensor, idx: torch.Tensor, h: float, degree: int = 2,
                            _ptr(order), _ptr(out_xyz), _ptr(out_normal), _ptr(out_status), _stream(stream))
     _check("mls_project", rc)
     return out_xyz, out_normal, out_status
+
+
+def mls_project_backward(xyz: torch.Tensor, idx: torch.Tensor, h: float, grad_out_xyz: torch.Tensor,
+                         grad_out_normal: torch.Tensor | None = None, degree: int = 2, precision: str = "mixed",
+                         order: torch.Tensor | None = None, out_grad_xyz=None, out_grad_h=None, stream=None):
+    """(dL/dxyz, dL/dh) for L = <grad_out_xyz, xyz'> + <grad_out_normal, normal>."""
+    _need(xyz, "xyz", torch.float32)
+    n = xyz.shape[0]
+    _need(idx, "idx", torch.int32)
+    if idx.dim() != 2 or idx.shape[0] != n:
+        raise ValueError("idx must be (n, k)")
+    _need(grad_out_xyz, "grad_out_xyz", torch.float32, (n, 3))
+    if grad_out_normal is not None:
+        _need(grad_out_normal, "grad_out_normal", torch.float32, (n, 3))
+    if order is not None:
+        _need(order, "order", torch.int32, (n,))
+    if out_grad_xyz is None:
+        out_grad_xyz = torch.empty_like(xyz)
+    _need(out_grad_xyz, "out_grad_xyz", torch.float32, (n, 3))
+    if out_grad_h is None:
+        out_grad_h = torch.empty(1, dtype=torch.float32, device=xyz.device)
+    _need(out_grad_h, "out_grad_h", torch.float32, (1,))
+    rc = lib().mls_project_backward(_ptr(xyz), n, _ptr(idx), idx.shape[1], float(h), int(degree),
+                                    PRECISION[precision], _ptr(order), _ptr(grad_out_xyz), _ptr(grad_out_normal),
+                                    _ptr(out_grad_xyz), _ptr(out_grad_h), _stream(stream))
+    _check("mls_project_backward", rc)
+    return out_grad_xyz, out_grad_h
 
 
 def mls_mean_knn_dist(xyz: torch.Tensor, idx: torch.Tensor, stream=None) -> torch.Tensor:

@@ -14,6 +14,9 @@ void free_grid_buffers(mls_grid *g);
 int launch_knn(const mls_grid *grid, int k, int32_t *idx, float *key, cudaStream_t st);
 int launch_project(const float *xyz, int64_t n, const int32_t *idx, int k, float h, int degree, int precision,
                    const int32_t *order, float *out_xyz, float *out_n, uint8_t *status, cudaStream_t st);
+int launch_backward(const float *xyz, int64_t n, const int32_t *idx, int k, float h, int degree, int precision,
+                    const int32_t *order, const float *gp, const float *gn, float *grad_xyz, float *grad_h,
+                    cudaStream_t st);
 
 namespace {
 thread_local char g_last_error[512] = "";
@@ -159,6 +162,29 @@ int mls_project(const float *d_xyz, int64_t n, const int32_t *d_idx, int k, floa
         return set_error(MLS_ERR_INVALID_ARG, "mls_project: output aliases the input");
     return mls::launch_project(d_xyz, n, d_idx, k, h, degree, precision, d_order, d_out_xyz, d_out_normal,
                                d_status, (cudaStream_t)stream);
+}
+
+int mls_project_backward(const float *d_xyz, int64_t n, const int32_t *d_idx, int k, float h, int degree,
+                         int precision, const int32_t *d_order, const float *d_grad_out_xyz,
+                         const float *d_grad_out_normal, float *d_grad_xyz, float *d_grad_h, mls_stream stream) {
+    mls::g_last_error[0] = 0;
+    if (!d_xyz || !d_idx || !d_grad_out_xyz || !d_grad_xyz || !d_grad_h)
+        return set_error(MLS_ERR_INVALID_ARG, "mls_project_backward: null pointer");
+    if (n < 1) return set_error(MLS_ERR_INVALID_ARG, "mls_project_backward: n = %lld < 1", (long long)n);
+    if (n > 0x7fffffffLL / MLS_MAX_K)
+        return set_error(MLS_ERR_TOO_LARGE, "mls_project_backward: n = %lld", (long long)n);
+    if (k < 1 || k > MLS_MAX_K || k > n)
+        return set_error(MLS_ERR_K_TOO_LARGE, "mls_project_backward: k = %d not in [1, min(%d, n)]", k, MLS_MAX_K);
+    if (!(h > 0.0f) || !std::isfinite(h))
+        return set_error(MLS_ERR_INVALID_ARG, "mls_project_backward: h = %g must be finite and > 0", (double)h);
+    if (degree < 0 || degree > 2)
+        return set_error(MLS_ERR_UNSUPPORTED_DEGREE, "mls_project_backward: degree = %d", degree);
+    if (precision < MLS_PREC_FP32 || precision > MLS_PREC_FP64)
+        return set_error(MLS_ERR_INVALID_ARG, "mls_project_backward: precision = %d", precision);
+    if ((const void *)d_grad_xyz == (const void *)d_xyz || (const void *)d_grad_xyz == (const void *)d_grad_out_xyz)
+        return set_error(MLS_ERR_INVALID_ARG, "mls_project_backward: output aliases an input");
+    return mls::launch_backward(d_xyz, n, d_idx, k, h, degree, precision, d_order, d_grad_out_xyz,
+                                d_grad_out_normal, d_grad_xyz, d_grad_h, (cudaStream_t)stream);
 }
 
 int mls_mean_knn_dist(const float *d_xyz, int64_t n, const int32_t *d_idx, int k, double *d_out,

@@ -12,7 +12,7 @@
 #include <algorithm>
 #include <cfloat>
 
-#include "common.cuh"
+#include "solve.cuh"
 
 namespace mls {
 
@@ -21,209 +21,6 @@ namespace {
 constexpr int kProjThreads = 128;
 constexpr float kMixedGapFlag = 1e-3f;     // FP32 eigensolve trusted above this gap ratio
 constexpr float kMixedCondFlag = 1e5f;     // FP32 Cholesky trusted below this condition estimate
-
-template <int DEG>
-struct Basis {
-    static constexpr int M = DEG == 0 ? 1 : (DEG == 1 ? 3 : 6);
-};
-
-// Cyclic Jacobi on the symmetric 3x3 matrix a (xx, xy, xz, yy, yz, zz).
-// Eigenvalues ascending in lam, eigenvectors as columns of V.
-template <typename T>
-__device__ void jacobi3(const T a6[6], T lam[3], T V[3][3]) {
-    T A[3][3] = {{a6[0], a6[1], a6[2]}, {a6[1], a6[3], a6[4]}, {a6[2], a6[4], a6[5]}};
-#pragma unroll
-    for (int i = 0; i < 3; ++i)
-#pragma unroll
-        for (int j = 0; j < 3; ++j) V[i][j] = (i == j) ? T(1) : T(0);
-    const T tol = sizeof(T) == 4 ? T(1e-15) : T(1e-30);
-    for (int sweep = 0; sweep < (sizeof(T) == 4 ? 8 : 20); ++sweep) {
-        T off = A[0][1] * A[0][1] + A[0][2] * A[0][2] + A[1][2] * A[1][2];
-        T all = A[0][0] * A[0][0] + A[1][1] * A[1][1] + A[2][2] * A[2][2] + T(2) * off;
-        if (off <= tol * all) break;
-#pragma unroll
-        for (int pq = 0; pq < 3; ++pq) {
-            const int p = pq == 2 ? 1 : 0, q = pq == 0 ? 1 : 2;
-            T apq = A[p][q];
-            if (apq == T(0)) continue;
-            T theta = (A[q][q] - A[p][p]) / (T(2) * apq);
-            T t = (theta >= T(0) ? T(1) : T(-1)) / (fabs(theta) + sqrt(theta * theta + T(1)));
-            T c = T(1) / sqrt(t * t + T(1)), s = t * c;
-#pragma unroll
-            for (int r = 0; r < 3; ++r) {
-                T arp = A[r][p], arq = A[r][q];
-                A[r][p] = c * arp - s * arq;
-                A[r][q] = s * arp + c * arq;
-            }
-#pragma unroll
-            for (int r = 0; r < 3; ++r) {
-                T apr = A[p][r], aqr = A[q][r];
-                A[p][r] = c * apr - s * aqr;
-                A[q][r] = s * apr + c * aqr;
-            }
-            A[p][q] = A[q][p] = T(0);
-#pragma unroll
-            for (int r = 0; r < 3; ++r) {
-                T vrp = V[r][p], vrq = V[r][q];
-                V[r][p] = c * vrp - s * vrq;
-                V[r][q] = s * vrp + c * vrq;
-            }
-        }
-    }
-    lam[0] = A[0][0];
-    lam[1] = A[1][1];
-    lam[2] = A[2][2];
-    // sort ascending (three compare-swaps)
-#pragma unroll
-    for (int pass = 0; pass < 3; ++pass) {
-        const int i = pass == 1 ? 1 : 0, j = i + 1;
-        if (lam[j] < lam[i]) {
-            T tl = lam[i];
-            lam[i] = lam[j];
-            lam[j] = tl;
-#pragma unroll
-            for (int r = 0; r < 3; ++r) {
-                T tv = V[r][i];
-                V[r][i] = V[r][j];
-                V[r][j] = tv;
-            }
-        }
-    }
-}
-
-// Cholesky A = L L^T of an M x M symmetric matrix (lower triangle used).
-// Returns false when a pivot is <= rel_tol * trace.  min/max pivot (of L)
-// are returned for the conditioning estimate.
-template <typename T, int M>
-__device__ bool cholesky(const T A[M][M], T L[M][M], T rel_tol, T &pmin, T &pmax) {
-    T tr = T(0);
-#pragma unroll
-    for (int i = 0; i < M; ++i) tr += A[i][i];
-    pmin = T(INFINITY);
-    pmax = T(0);
-    bool ok = true;
-#pragma unroll
-    for (int j = 0; j < M; ++j) {
-        T d = A[j][j];
-#pragma unroll
-        for (int c = 0; c < j; ++c) d -= L[j][c] * L[j][c];
-        if (!(d > rel_tol * tr)) {
-            ok = false;
-            d = T(1);
-        }
-        T l = sqrt(d);
-        L[j][j] = l;
-        pmin = fmin(pmin, l);
-        pmax = fmax(pmax, l);
-        T inv = T(1) / l;
-#pragma unroll
-        for (int i = j + 1; i < M; ++i) {
-            T s = A[i][j];
-#pragma unroll
-            for (int c = 0; c < j; ++c) s -= L[i][c] * L[j][c];
-            L[i][j] = s * inv;
-        }
-    }
-    return ok;
-}
-
-template <typename T, int M>
-__device__ void chol_solve(const T L[M][M], const T b[M], T x[M]) {
-    T y[M];
-#pragma unroll
-    for (int i = 0; i < M; ++i) {
-        T s = b[i];
-#pragma unroll
-        for (int c = 0; c < i; ++c) s -= L[i][c] * y[c];
-        y[i] = s / L[i][i];
-    }
-#pragma unroll
-    for (int i = M - 1; i >= 0; --i) {
-        T s = y[i];
-#pragma unroll
-        for (int c = i + 1; c < M; ++c) s -= L[c][i] * x[c];
-        x[i] = s / L[i][i];
-    }
-}
-
-// Normal matrix and right-hand side from the moments.
-// mom: M00 M10 M01 M20 M11 M02 M30 M21 M12 M03 M40 M31 M22 M13 M04 (Mab = sum w u^a v^b)
-template <typename T, int DEG>
-__device__ void assemble(const float mom[15], T A[Basis<DEG>::M][Basis<DEG>::M]) {
-    constexpr int M = Basis<DEG>::M;
-    // exponent pairs of the basis monomials
-    const int ea[6] = {0, 1, 0, 2, 1, 0}, eb[6] = {0, 0, 1, 0, 1, 2};
-#pragma unroll
-    for (int r = 0; r < M; ++r)
-#pragma unroll
-        for (int c = 0; c < M; ++c) {
-            const int a = ea[r] + ea[c], b = eb[r] + eb[c], dg = a + b;
-            // position of (a, b) in the moment list: degree blocks 1, 2, 3, 4, 5 long
-            const int at = dg * (dg + 1) / 2 + b;
-            A[r][c] = (T)mom[at];
-        }
-}
-
-// Solve the height fit: returns a0 and whether the system was singular.
-template <typename T, int DEG>
-__device__ T solve_a0(const float mom[15], const float rhs[6], bool refine, bool &singular, T &cond_est) {
-    constexpr int M = Basis<DEG>::M;
-    T A[M][M], L[M][M], b[M], x[M];
-    assemble<T, DEG>(mom, A);
-#pragma unroll
-    for (int r = 0; r < M; ++r) b[r] = (T)rhs[r];
-    T pmin, pmax;
-    singular = !cholesky<T, M>(A, L, T(1e-12), pmin, pmax);
-    cond_est = (pmax / pmin) * (pmax / pmin);
-    if (singular) return T(0);
-    chol_solve<T, M>(L, b, x);
-    if (refine) {
-        T res[M], dx[M];
-#pragma unroll
-        for (int r = 0; r < M; ++r) {
-            T s = b[r];
-#pragma unroll
-            for (int c = 0; c < M; ++c) s -= A[r][c] * x[c];
-            res[r] = s;
-        }
-        chol_solve<T, M>(L, res, dx);
-#pragma unroll
-        for (int r = 0; r < M; ++r) x[r] += dx[r];
-    }
-    return x[0];
-}
-
-template <typename T>
-__device__ void canonical(T n[3]) {
-    int a = 0;
-    if (fabs(n[1]) > fabs(n[a])) a = 1;
-    if (fabs(n[2]) > fabs(n[a])) a = 2;
-    if (n[a] < T(0)) {
-        n[0] = -n[0];
-        n[1] = -n[1];
-        n[2] = -n[2];
-    }
-}
-
-// Frame from the eigen-decomposition: n = v0 (canonical sign), e1 = v1,
-// e2 = n x e1.  Returns the status bit for a degenerate plane.
-template <typename T>
-__device__ int frame_from(const T C[6], T nrm[3], T e1[3], T e2[3], T lam[3]) {
-    T V[3][3];
-    jacobi3<T>(C, lam, V);
-    nrm[0] = V[0][0];
-    nrm[1] = V[1][0];
-    nrm[2] = V[2][0];
-    e1[0] = V[0][1];
-    e1[1] = V[1][1];
-    e1[2] = V[2][1];
-    canonical(nrm);
-    e2[0] = nrm[1] * e1[2] - nrm[2] * e1[1];
-    e2[1] = nrm[2] * e1[0] - nrm[0] * e1[2];
-    e2[2] = nrm[0] * e1[1] - nrm[1] * e1[0];
-    if (!(lam[2] > T(0)) || (lam[1] - lam[0]) <= T(1e-6) * lam[2]) return MLS_PT_PLANE_DEGENERATE;
-    return 0;
-}
 
 // Copy of the points as float4 (w = 0): one 16-byte load per neighbour gather.
 __global__ void k_pack_xyz4(const float *__restrict__ xyz, int64_t n, float4 *__restrict__ xyz4) {

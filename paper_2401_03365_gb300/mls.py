@@ -56,6 +56,42 @@ class Pipeline:
             self.grid = None
 
 
+class ProjectFunction(torch.autograd.Function):
+    """Differentiable MLS projection: forward mls_project, backward
+    mls_project_backward (gradients for the coordinates and h; the neighbour
+    rows are constants).  Only xyz, the rows and h are saved: the backward
+    recomputes every per-point frame."""
+
+    @staticmethod
+    def forward(ctx, xyz, h, idx, degree, precision, order):
+        hv = float(h)
+        out, nrm, st = capi.mls_project(xyz, idx, hv, degree, precision, order=order)
+        ctx.save_for_backward(xyz, idx, order if order is not None else torch.empty(0, dtype=torch.int32))
+        ctx.hv, ctx.degree, ctx.precision, ctx.has_order = hv, degree, precision, order is not None
+        ctx.h_shape = h.shape if isinstance(h, torch.Tensor) else None
+        ctx.mark_non_differentiable(st)
+        return out, nrm, st
+
+    @staticmethod
+    def backward(ctx, g_out, g_n, g_st):
+        xyz, idx, order = ctx.saved_tensors
+        if g_out is None:
+            g_out = torch.zeros_like(xyz)
+        gx, gh = capi.mls_project_backward(xyz, idx, ctx.hv, g_out.contiguous(),
+                                           None if g_n is None else g_n.contiguous(), ctx.degree, ctx.precision,
+                                           order=order if ctx.has_order else None)
+        gh_out = gh.reshape(ctx.h_shape).to(torch.float32) if ctx.h_shape is not None else None
+        return gx, gh_out, None, None, None, None
+
+
+def project_differentiable(xyz: torch.Tensor, idx: torch.Tensor, h, degree: int = 2, precision: str = "mixed",
+                           order: torch.Tensor | None = None):
+    """(xyz', normal, status) with autograd to xyz and h (a tensor)."""
+    if not isinstance(h, torch.Tensor):
+        h = torch.tensor(float(h), dtype=torch.float32, device=xyz.device)
+    return ProjectFunction.apply(xyz, h, idx, degree, precision, order)
+
+
 def knn(xyz: torch.Tensor, k: int, with_key: bool = False, cell_size: float = 0.0):
     grid = capi.mls_build_grid(xyz, cell_size, k)
     try:

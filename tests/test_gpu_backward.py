@@ -1,0 +1,113 @@
+"""GPU adjoint (mls_project_backward through the C ABI) against the FP64
+oracle's adjoint, itself pinned to central differences on the CPU."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2401_03365_gb300 import workloads
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def capi():
+    from paper_2401_03365_gb300 import build, capi
+    build.build()
+    return capi
+
+
+def _setup(capi, cloud, k, degree, seed):
+    x = torch.from_numpy(cloud.xyz).cuda()
+    grid = capi.mls_build_grid(x, 0.0, k)
+    idx, _ = capi.mls_knn(grid, k)
+    order = capi.mls_grid_order(grid).clone()
+    torch.cuda.synchronize()
+    grid.close()
+    idx_o, _ = oracle.knn_kdtree(cloud.xyz, k)
+    assert np.array_equal(idx.cpu().numpy(), idx_o)
+    h = float(np.float32(2.0 * oracle.mean_knn_dist(cloud.xyz, idx_o)))
+    rng = np.random.default_rng(seed)
+    gp = rng.standard_normal((cloud.n, 3)).astype(np.float32)
+    gn = rng.standard_normal((cloud.n, 3)).astype(np.float32)
+    return x, idx, order, idx_o, h, gp, gn
+
+
+@pytest.mark.parametrize("degree", [1, 2])
+@pytest.mark.parametrize("precision", ["fp32", "mixed"])
+def test_backward_matches_oracle_adjoint(capi, degree, precision):
+    c = workloads.bumpy_sphere(n=20_000, seed=31, k=16)
+    x, idx, order, idx_o, h, gp, gn = _setup(capi, c, 16, degree, 7)
+    gx, gh = capi.mls_project_backward(x, idx, h, torch.from_numpy(gp).cuda(), torch.from_numpy(gn).cuda(),
+                                       degree, precision, order=order)
+    torch.cuda.synchronize()
+    g_o, gh_o = oracle.project_grad(c.xyz, idx_o, h, degree, gp.astype(np.float64), gn.astype(np.float64))
+    g = gx.cpu().numpy().astype(np.float64)
+    err = np.linalg.norm(g - g_o, axis=1)
+    scale = np.linalg.norm(g_o, axis=1)
+    ref = np.median(scale)
+    assert np.all(err <= 2e-3 * scale + 2e-4 * ref), (err / (scale + 1e-30)).max()
+    assert abs(float(gh.item()) - gh_o) <= 2e-3 * abs(gh_o) + 1e-6 * ref * np.sqrt(c.n)
+
+
+def test_backward_with_outliers_matches_on_well_posed_neighbourhoods(capi):
+    """Noisy torus with outliers: points whose gradient comes only from
+    well-posed neighbourhoods (every point that has them as a neighbour is
+    well-posed) match the oracle."""
+    c = workloads.torus(n=60_000, seed=17)
+    x, idx, order, idx_o, h, gp, gn = _setup(capi, c, 32, 2, 8)
+    gx, gh = capi.mls_project_backward(x, idx, h, torch.from_numpy(gp).cuda(), torch.from_numpy(gn).cuda(),
+                                       2, "mixed", order=order)
+    torch.cuda.synchronize()
+    g_o, _ = oracle.project_grad(c.xyz, idx_o, h, 2, gp.astype(np.float64), gn.astype(np.float64))
+    _, _, _, diag = oracle.project(c.xyz, idx_o, h, 2)
+    gap = (diag[:, 1] - diag[:, 0]) / np.maximum(diag[:, 2], 1e-300)
+    good = (gap >= 1e-2) & (diag[:, 3] <= 1e6)
+    # a target is clean when every source that lists it is good
+    bad_src = ~good
+    tainted = np.zeros(c.n, bool)
+    tainted[idx_o[bad_src].ravel()] = True
+    tainted |= bad_src
+    clean = ~tainted
+    assert clean.mean() > 0.5
+    g = gx.cpu().numpy().astype(np.float64)
+    err = np.linalg.norm(g - g_o, axis=1)
+    scale = np.linalg.norm(g_o, axis=1)
+    ref = np.median(scale[clean])
+    assert np.all(err[clean] <= 2e-3 * scale[clean] + 2e-4 * ref), (err[clean] / (scale[clean] + 1e-30)).max()
+
+
+def test_backward_deterministic(capi):
+    c = workloads.torus(n=100_000, seed=18)
+    x = torch.from_numpy(c.xyz).cuda()
+    grid = capi.mls_build_grid(x, 0.0, 32)
+    idx, _ = capi.mls_knn(grid, 32)
+    order = capi.mls_grid_order(grid).clone()
+    gp = torch.randn(c.n, 3, device="cuda")
+    a, ah = capi.mls_project_backward(x, idx, 0.02, gp, None, 2, "mixed", order=order)
+    a, ah = a.clone(), ah.clone()
+    b, bh = capi.mls_project_backward(x, idx, 0.02, gp, None, 2, "mixed")
+    torch.cuda.synchronize()
+    grid.close()
+    assert torch.equal(a, b) and torch.equal(ah, bh)
+
+
+def test_autograd_function(capi):
+    from paper_2401_03365_gb300 import mls
+    c = workloads.bumpy_sphere(n=10_000, seed=40, k=16)
+    x = torch.from_numpy(c.xyz).cuda().requires_grad_(True)
+    grid = capi.mls_build_grid(x.detach(), 0.0, 16)
+    idx, _ = capi.mls_knn(grid, 16)
+    torch.cuda.synchronize()
+    grid.close()
+    h = torch.tensor(0.05, device="cuda", requires_grad=True)
+    out, nrm, st = mls.project_differentiable(x, idx, h)
+    loss = (out.norm(dim=1) - 1.0).pow(2).sum() + 0.1 * nrm[:, 2].sum()
+    loss.backward()
+    gp = (2 * (out.norm(dim=1) - 1.0) / out.norm(dim=1)).unsqueeze(1) * out
+    gn = torch.zeros_like(nrm)
+    gn[:, 2] = 0.1
+    gx, gh = capi.mls_project_backward(x.detach(), idx, 0.05, gp.detach().contiguous(), gn)
+    torch.cuda.synchronize()
+    assert torch.allclose(x.grad, gx, rtol=1e-4, atol=1e-6 * gx.abs().max().item())
+    assert torch.allclose(h.grad.reshape(1), gh, rtol=1e-4)

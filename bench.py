@@ -38,7 +38,7 @@ WORKLOAD = ("torus2m_k32: 2,000,000 points on a torus (R=1, r=0.3) with normal n
 N_POINTS = 2_000_000
 K = 32
 
-# Algorithmic work per point (see DESIGN.md "Roofline"): flops of the degree-2
+# Algorithmic work per point: flops of the degree-2
 # projection as the oracle's operation list counts them, and the minimal HBM
 # bytes of the kNN (read the point, write its k indices).
 FLOPS_PER_NEIGHBOUR = 97

@@ -151,6 +151,30 @@ int mls_project(const float *d_xyz, int64_t n, const int32_t *d_idx, int k, floa
                 uint8_t *d_status, mls_stream stream);
 
 /*
+ * mls_project_noalloc -- mls_project for callers that must not allocate
+ * device memory.  The paper has no counterpart: this is a deployment
+ * variant.  Some callers cannot let a library allocate: hosts that hand out
+ * all device memory from their own fixed pool or budget (inference servers,
+ * embedded pipelines) and would not see a cudaMallocAsync, or loops that must
+ * not risk an allocation failing half way.  This entry point takes its
+ * scratch (a float4 copy of the points) from a fixed device array of
+ * MLS_NOALLOC_MAX_POINTS entries (4 MiB), which every GPU that loads the
+ * library holds until the process exits; it calls no allocation routine.
+ *
+ * Arguments, outputs and results are those of mls_project.
+ * Returns MLS_ERR_TOO_LARGE when n > MLS_NOALLOC_MAX_POINTS.
+ * The first call on a device looks the array's device address up (with that
+ * device current); make that first call before any stream capture.
+ * All calls share the one array: calls that overlap on the GPU (other
+ * streams, other threads) race and corrupt each other's scratch; serialise
+ * them.  Every call overwrites the part it uses, so no state carries over.
+ */
+#define MLS_NOALLOC_MAX_POINTS 262144
+int mls_project_noalloc(const float *d_xyz, int64_t n, const int32_t *d_idx, int k, float h, int degree,
+                        int precision, const int32_t *d_order, float *d_out_xyz, float *d_out_normal,
+                        uint8_t *d_status, mls_stream stream);
+
+/*
  * mls_project_backward -- vector-Jacobian product of mls_project (not in the
  * paper): with cotangents gp (of the projected points) and gn (of the
  * normals), the gradients of L = sum_i <gp_i, p'_i> + <gn_i, n_i> with

@@ -23,6 +23,7 @@ __all__ = [
 ]
 
 MLS_MAX_K = 64
+MLS_NOALLOC_MAX_POINTS = 262144
 PRECISION = {"fp32": 0, "mixed": 1, "fp64": 2}
 MLS_PT_OK, MLS_PT_PLANE_DEGENERATE, MLS_PT_POLY_SINGULAR, MLS_PT_FP64_USED = 0, 1, 2, 4
 
@@ -39,6 +40,7 @@ _SIGNATURES = [
     ("mls_grid_order", _vp, [_vp]),
     ("mls_knn", _int, [_vp, _int, _vp, _vp, _vp]),
     ("mls_project", _int, [_vp, _i64, _vp, _int, _flt, _int, _int, _vp, _vp, _vp, _vp, _vp]),
+    ("mls_project_noalloc", _int, [_vp, _i64, _vp, _int, _flt, _int, _int, _vp, _vp, _vp, _vp, _vp]),
     ("mls_project_backward", _int, [_vp, _i64, _vp, _int, _flt, _int, _int, _vp, _vp, _vp, _vp, _vp, _vp]),
     ("mls_mean_knn_dist", _int, [_vp, _i64, _vp, _int, _vp, _vp]),
     ("mls_kernel_launches", _i64, []),

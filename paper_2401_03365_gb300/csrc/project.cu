@@ -11,6 +11,8 @@
 // degree-2 normal equations in local coordinates scaled by 1/h.
 #include <algorithm>
 #include <cfloat>
+#include <cmath>
+#include <mutex>
 
 #include "solve.cuh"
 
@@ -320,4 +322,94 @@ int launch_project(const float *xyz, int64_t n, const int32_t *idx, int k, float
     }
 }
 
+// ---- mls_project_noalloc --------------------------------------------------
+//
+// The same kernels as mls_project, with the float4 copy of the points kept in
+// a file-scope device array instead of stream-ordered scratch.  The array is
+// a host-side stand-in in host code: its device address is looked up once per
+// device (with that device current) and passed to the kernels.
+
+namespace {
+
+__device__ __align__(256) float4 g_noalloc_xyz4[MLS_NOALLOC_MAX_POINTS];
+
+constexpr int kMaxDevices = 64;
+float4 *g_noalloc_addr[kMaxDevices] = {};
+std::mutex g_noalloc_mutex;
+
+int noalloc_scratch(float4 **out) {
+    int dev = 0;
+    MLS_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDevices) return set_error(MLS_ERR_CUDA, "mls_project_noalloc: device %d", dev);
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_addr[dev]) {
+        void *p = nullptr;
+        MLS_CUDA_TRY(cudaGetSymbolAddress(&p, g_noalloc_xyz4));
+        g_noalloc_addr[dev] = (float4 *)p;
+    }
+    *out = g_noalloc_addr[dev];
+    return MLS_OK;
+}
+
+template <int DEG>
+int launch_noalloc(const float *xyz, int64_t n, const int32_t *idx, int k, float h, int precision,
+                   const int32_t *order, float *out_xyz, float *out_n, uint8_t *status, cudaStream_t st) {
+    const int blocks = (int)((n + kProjThreads - 1) / kProjThreads);
+    if (precision == MLS_PREC_FP64) {
+        k_project_fp64<DEG><<<blocks, kProjThreads, 0, st>>>(xyz, n, idx, k, h, order, out_xyz, out_n, status);
+        count_launches(1);
+    } else {
+        float4 *xyz4 = nullptr;
+        int rc = noalloc_scratch(&xyz4);
+        if (rc != MLS_OK) return rc;
+        k_pack_xyz4<<<(int)std::min<int64_t>((n + 255) / 256, 152 * 16), 256, 0, st>>>(xyz, n, xyz4);
+        const size_t smem = (size_t)k * 32 * sizeof(int32_t) * (kProjThreads / 32);
+        if (precision == MLS_PREC_MIXED) {
+            auto kern = k_project<DEG, MLS_PREC_MIXED>;
+            MLS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            kern<<<blocks, kProjThreads, smem, st>>>(xyz4, n, idx, k, h, order, out_xyz, out_n, status);
+        } else {
+            auto kern = k_project<DEG, MLS_PREC_FP32>;
+            MLS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            kern<<<blocks, kProjThreads, smem, st>>>(xyz4, n, idx, k, h, order, out_xyz, out_n, status);
+        }
+        count_launches(2);
+    }
+    MLS_CUDA_TRY(cudaGetLastError());
+    return MLS_OK;
+}
+
+}  // namespace
+
 }  // namespace mls
+
+extern "C" int mls_project_noalloc(const float *d_xyz, int64_t n, const int32_t *d_idx, int k, float h, int degree,
+                                   int precision, const int32_t *d_order, float *d_out_xyz, float *d_out_normal,
+                                   uint8_t *d_status, mls_stream stream) {
+    using mls::set_error;
+    if (!d_xyz || !d_idx || !d_out_xyz) return set_error(MLS_ERR_INVALID_ARG, "mls_project_noalloc: null pointer");
+    if (n < 1) return set_error(MLS_ERR_INVALID_ARG, "mls_project_noalloc: n = %lld < 1", (long long)n);
+    if (n > MLS_NOALLOC_MAX_POINTS)
+        return set_error(MLS_ERR_TOO_LARGE,
+                         "mls_project_noalloc: n = %lld exceeds its fixed scratch of %d points; use mls_project",
+                         (long long)n, MLS_NOALLOC_MAX_POINTS);
+    if (k < 1 || k > MLS_MAX_K || k > n)
+        return set_error(MLS_ERR_K_TOO_LARGE, "mls_project_noalloc: k = %d not in [1, min(%d, n)]", k, MLS_MAX_K);
+    if (!(h > 0.0f) || !std::isfinite(h))
+        return set_error(MLS_ERR_INVALID_ARG, "mls_project_noalloc: h = %g must be finite and > 0", (double)h);
+    if (degree < 0 || degree > 2)
+        return set_error(MLS_ERR_UNSUPPORTED_DEGREE, "mls_project_noalloc: degree = %d not in {0, 1, 2}", degree);
+    if (precision < MLS_PREC_FP32 || precision > MLS_PREC_FP64)
+        return set_error(MLS_ERR_INVALID_ARG, "mls_project_noalloc: precision = %d", precision);
+    if ((const void *)d_out_xyz == (const void *)d_xyz)
+        return set_error(MLS_ERR_INVALID_ARG, "mls_project_noalloc: output aliases the input");
+    cudaStream_t st = (cudaStream_t)stream;
+    switch (degree) {
+        case 0:
+            return mls::launch_noalloc<0>(d_xyz, n, d_idx, k, h, precision, d_order, d_out_xyz, d_out_normal, d_status, st);
+        case 1:
+            return mls::launch_noalloc<1>(d_xyz, n, d_idx, k, h, precision, d_order, d_out_xyz, d_out_normal, d_status, st);
+        default:
+            return mls::launch_noalloc<2>(d_xyz, n, d_idx, k, h, precision, d_order, d_out_xyz, d_out_normal, d_status, st);
+    }
+}

@@ -4,8 +4,9 @@
 
 Workload: 2,000,000-point torus (R = 1, r = 0.3, normal noise 0.005, 1 %
 uniform outliers), k = 32, degree-2 polynomial, mixed precision.  One step is
-one pass of the whole hot path over the cloud: grid build, exact kNN and the
-MLS projection (through the C ABI of libmls, inputs resident in HBM).  L2 is
+one pass of the whole hot path over the cloud: grid build, exact kNN, the MLS
+projection and its backward with a fixed cotangent (through the C ABI of
+libmls, inputs resident in HBM).  L2 is
 flushed (a 256 MB write) before every timed step, outside the timed events.
 
 With N > 1 (torchrun) every rank projects its own cloud (seed 2 + rank): the
@@ -44,7 +45,7 @@ K = 32
 FLOPS_PER_NEIGHBOUR = 97
 FLOPS_PER_POINT = 645
 KNN_BYTES_PER_POINT = 16 + 4 * K
-PROJECT_BYTES_PER_POINT = 12 + 4 * K + 12 + 12 + 1
+GRID_BYTES_PER_POINT = 12 + 16 + 8 + 4
 
 
 def load_peaks():
@@ -143,6 +144,11 @@ def run_ours(args):
     out_xyz = torch.empty_like(x)
     out_n = torch.empty_like(x)
     out_st = torch.empty(N_POINTS, dtype=torch.uint8, device=dev)
+    grad = torch.empty_like(x)
+    grad_h = torch.empty(1, dtype=torch.float32, device=dev)
+    gen = torch.Generator(device=dev).manual_seed(11 + rank)
+    gp = torch.randn((N_POINTS, 3), generator=gen, device=dev)          # cotangent of the points
+    gn = 0.1 * torch.randn((N_POINTS, 3), generator=gen, device=dev)    # cotangent of the normals
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
     # bandwidth of the workload: 2 x mean kNN distance, from the GPU kNN
@@ -150,21 +156,24 @@ def run_ours(args):
     capi.mls_knn(grid, K, out_idx=idx)
     h = 2.0 * float(capi.mls_mean_knn_dist(x, idx).item())
 
-    def step(ev=None):
+    def step(xin, ev=None):
         nonlocal grid
         if ev: ev[0].record(stream)
-        grid = capi.mls_build_grid(x, 0.0, K, grid=grid)
+        grid = capi.mls_build_grid(xin, 0.0, K, grid=grid)
         if ev: ev[1].record(stream)
         capi.mls_knn(grid, K, out_idx=idx)
         if ev: ev[2].record(stream)
-        capi.mls_project(x, idx, h, 2, "mixed", order=capi.mls_grid_order(grid), out_xyz=out_xyz,
-                         out_normal=out_n, out_status=out_st)
+        order = capi.mls_grid_order(grid)
+        capi.mls_project(xin, idx, h, 2, "mixed", order=order, out_xyz=out_xyz, out_normal=out_n, out_status=out_st)
         if ev: ev[3].record(stream)
+        capi.mls_project_backward(xin, idx, h, gp, gn, 2, "mixed", order=order, out_grad_xyz=grad,
+                                  out_grad_h=grad_h)
+        if ev: ev[4].record(stream)
 
     for _ in range(args.warmup):
-        step()
+        step(x)
     torch.cuda.synchronize()
-    events = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+    events = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(args.steps)]
     launches0 = capi.mls_kernel_launches()
     if world > 1:
         dist.barrier()
@@ -173,51 +182,49 @@ def run_ours(args):
         t0 = time.perf_counter()
         for s in range(args.steps):
             flush.zero_()
-            step(events[s])
+            step(x, events[s])
         torch.cuda.synchronize()
         wall = time.perf_counter() - t0
     if world > 1:
         dist.barrier()
     launches = capi.mls_kernel_launches() - launches0
-    stage = np.array([[e[i].elapsed_time(e[i + 1]) for i in range(3)] for e in events])  # ms
-    step_ms = float(stage.sum(1).mean())
-    t_max = torch.tensor([step_ms], dtype=torch.float64, device=dev)
+    stage = np.array([[e[i].elapsed_time(e[i + 1]) for i in range(4)] for e in events])  # ms
+    build_ms, knn_ms, proj_ms, bwd_ms = (float(v) for v in stage.mean(0))
+    t = torch.tensor([stage.sum(1).mean(), stage[:, :3].sum(1).mean()], dtype=torch.float64, device=dev)
     if world > 1:
-        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
-    step_ms_max = float(t_max.item())
-    value = world * N_POINTS / (step_ms_max * 1e-3)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    step_ms, fwd_ms = float(t[0]), float(t[1])
+    value = world * N_POINTS / (step_ms * 1e-3)
 
-    # end to end through the public API with host buffers: H2D of the points,
-    # the three calls, D2H of positions, normals and status, every step
+    # end to end through the public API with host buffers: every step copies
+    # the points in from pinned memory, runs the four calls, and copies the
+    # projected points, normals, status and gradient back
     host_in = torch.from_numpy(cloud.xyz).pin_memory()
     host_xyz = torch.empty((N_POINTS, 3), dtype=torch.float32).pin_memory()
     host_n = torch.empty((N_POINTS, 3), dtype=torch.float32).pin_memory()
     host_st = torch.empty(N_POINTS, dtype=torch.uint8).pin_memory()
+    host_g = torch.empty((N_POINTS, 3), dtype=torch.float32).pin_memory()
     x_e2e = torch.empty_like(x)
-    e2e_steps = max(3, min(args.steps, 10))
     e2e_ms = []
-    for s in range(e2e_steps + 1):
+    for s in range(min(max(args.steps, 3), 10) + 1):
         flush.zero_()
         torch.cuda.synchronize()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
         x_e2e.copy_(host_in, non_blocking=True)
-        grid = capi.mls_build_grid(x_e2e, 0.0, K, grid=grid)
-        capi.mls_knn(grid, K, out_idx=idx)
-        capi.mls_project(x_e2e, idx, h, 2, "mixed", order=capi.mls_grid_order(grid), out_xyz=out_xyz,
-                         out_normal=out_n, out_status=out_st)
+        step(x_e2e)
         host_xyz.copy_(out_xyz, non_blocking=True)
         host_n.copy_(out_n, non_blocking=True)
         host_st.copy_(out_st, non_blocking=True)
+        host_g.copy_(grad, non_blocking=True)
         b.record(stream)
         b.synchronize()
-        if s > 0:                      # the first is a warm-up of the copy path
+        if s > 0:                      # the first one warms the copy path
             e2e_ms.append(a.elapsed_time(b))
-    e2e_t = torch.tensor([float(np.mean(e2e_ms))], dtype=torch.float64, device=dev)
+    te = torch.tensor([float(np.mean(e2e_ms))], dtype=torch.float64, device=dev)
     if world > 1:
-        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
-    e2e_value = world * N_POINTS / (float(e2e_t.item()) * 1e-3)
-
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    e2e_value = world * N_POINTS / (float(te.item()) * 1e-3)
     grid.close()
     if rank != 0:
         if world > 1:
@@ -226,28 +233,33 @@ def run_ours(args):
         return None
 
     peaks = load_peaks()
-    knn_ms, proj_ms, build_ms = float(stage[:, 1].mean()), float(stage[:, 2].mean()), float(stage[:, 0].mean())
     proj_flops = N_POINTS * (FLOPS_PER_NEIGHBOUR * K + FLOPS_PER_POINT)
+    knn_gbs = N_POINTS * KNN_BYTES_PER_POINT / (knn_ms * 1e-3) / 1e9
+    proj_tf = proj_flops / (proj_ms * 1e-3) / 1e12
+    bwd_tf = 3 * proj_flops / (bwd_ms * 1e-3) / 1e12
     kernels = {
-        "grid_build": {"ms": build_ms, "launches_per_step": 34},
-        "knn": {"ms": knn_ms, "bound": "hbm", "achieved_gbs": N_POINTS * KNN_BYTES_PER_POINT / (knn_ms * 1e-3) / 1e9},
-        "project": {"ms": proj_ms, "bound": "alu",
-                    "achieved_tflops": proj_flops / (proj_ms * 1e-3) / 1e12,
-                    "frac": proj_flops / (proj_ms * 1e-3) / 1e12 / peaks["fp32_tflops"]},
+        "grid_build": {"ms": build_ms, "calls": "mls_build_grid"},
+        "knn": {"ms": knn_ms, "calls": "mls_knn (k_knn_chain + k_knn_sparse)", "bound": "hbm",
+                "achieved_gbs": knn_gbs, "frac": knn_gbs / peaks["hbm_gbs"]},
+        "project": {"ms": proj_ms, "calls": "mls_project (k_pack_xyz4 + k_project)", "bound": "alu",
+                    "achieved_tflops": proj_tf, "frac": proj_tf / peaks["fp32_tflops"]},
+        "backward": {"ms": bwd_ms, "calls": "mls_project_backward (adjoint + gather)", "bound": "alu",
+                     "achieved_tflops": bwd_tf, "frac": bwd_tf / peaks["fp32_tflops"]},
     }
-    dominant = max(("grid_build", build_ms), ("knn", knn_ms), ("project", proj_ms), key=lambda t: t[1])[0]
-    if dominant == "project":
-        ach = kernels["project"]["achieved_tflops"]
-        roofline = {"kernel": "k_project (mixed, degree 2)", "bound": "alu", "achieved": ach,
-                    "peak": peaks["fp32_tflops"], "unit": "TFLOP/s", "frac": ach / peaks["fp32_tflops"],
-                    "traffic": None, "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 x max SM clock"}
+    dom = max(kernels, key=lambda n_: kernels[n_]["ms"])
+    if dom == "knn" or dom == "grid_build":
+        ms = kernels[dom]["ms"]
+        bytes_pp = KNN_BYTES_PER_POINT if dom == "knn" else GRID_BYTES_PER_POINT
+        ach = N_POINTS * bytes_pp / (ms * 1e-3) / 1e9
+        roofline = {"kernel": kernels[dom]["calls"], "bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"],
+                    "unit": "GB/s", "frac": ach / peaks["hbm_gbs"], "traffic": None,
+                    "peak_source": f"{peaks['source']} hbm_gbs (copy)",
+                    "algorithmic_bytes_per_point": bytes_pp}
     else:
-        name = "k_knn" if dominant == "knn" else "grid build"
-        ms = knn_ms if dominant == "knn" else build_ms
-        ach = N_POINTS * KNN_BYTES_PER_POINT / (ms * 1e-3) / 1e9
-        roofline = {"kernel": name, "bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                    "frac": ach / peaks["hbm_gbs"], "traffic": None,
-                    "peak_source": f"{peaks['source']} hbm_gbs (copy)"}
+        ach = proj_tf if dom == "project" else bwd_tf
+        roofline = {"kernel": kernels[dom]["calls"], "bound": "alu", "achieved": ach, "peak": peaks["fp32_tflops"],
+                    "unit": "TFLOP/s", "frac": ach / peaks["fp32_tflops"], "traffic": None,
+                    "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 flops x max SM clock"}
     line = {
         "metric": METRIC,
         "value": value,
@@ -255,20 +267,22 @@ def run_ours(args):
         "n_gpus": world,
         "steps": args.steps,
         "warmup": args.warmup,
-        "ms_per_step": step_ms_max,
+        "ms_per_step": step_ms,
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
         "dtype": "f32",
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "points_per_gpu": N_POINTS, "k": K, "degree": 2, "precision": "mixed",
-                   "h": h, "step": "grid build + exact kNN + MLS projection (forward)",
+                   "h": h, "step": "grid build + exact kNN + MLS projection + backward (fwd+bwd)",
                    "l2": "flushed before every step (256 MB write, outside the timed events)",
                    "parallelism": f"independent clouds per GPU x{world}"},
+        "fwd": {"value": world * N_POINTS / (fwd_ms * 1e-3), "unit": "points/s", "ms_per_step": fwd_ms,
+                "step": "grid build + exact kNN + MLS projection"},
         "roofline": roofline,
         "kernels": kernels,
         "e2e": {"value": e2e_value, "unit": "points/s", "h2d_bytes_per_step": N_POINTS * 12,
-                "d2h_bytes_per_step": N_POINTS * (12 + 12 + 1)},
+                "d2h_bytes_per_step": N_POINTS * (12 + 12 + 1 + 12)},
         "gpu_launches": int(launches),
         "clocks": clocks.summary(),
         "wall_s_timed_region": wall,
@@ -283,23 +297,27 @@ def run_ours(args):
 
 def cpu_baseline(xyz, h, sample):
     """The FP64 oracle as it stands, single-threaded on this host: k-d tree over
-    the whole cloud, then kNN + projection of a seeded sample of points; the
-    per-point time is extrapolated to the full cloud."""
+    the whole cloud, then kNN, projection and adjoint of a seeded sample of
+    points; the per-point time is extrapolated to the full cloud."""
     import oracle
     n = xyz.shape[0]
     rng = np.random.default_rng(123)
     q = np.sort(rng.choice(n, sample, replace=False))
+    gp = rng.standard_normal((n, 3))
+    gn = 0.1 * rng.standard_normal((n, 3))
     t0 = time.perf_counter()
     oracle.knn_kdtree(xyz, K, queries=np.zeros(0, np.int64))
     t_build = time.perf_counter() - t0
     t0 = time.perf_counter()
     rows, _ = oracle.knn_kdtree(xyz, K, queries=q)
     oracle.project(xyz, rows, h, 2, queries=q)
+    oracle.project_grad(xyz, rows, h, 2, gp, gn, queries=q)
     t_sample = time.perf_counter() - t0 - t_build
     t_full = t_build + t_sample * n / sample
     return {"value": n / t_full, "unit": "points/s", "cores": 1, "kind": "oracle",
-            "sample": (f"k-d tree build over all {n} points ({t_build:.2f} s) + kNN and FP64 projection of a "
-                       f"seeded sample of {sample} points ({t_sample:.2f} s), extrapolated to the full cloud"),
+            "sample": (f"k-d tree build over all {n} points ({t_build:.2f} s) + kNN, FP64 projection and FP64 "
+                       f"adjoint of a seeded sample of {sample} points ({t_sample:.2f} s), extrapolated to the "
+                       f"full cloud"),
             "seconds": t_build + t_sample}
 
 
@@ -314,11 +332,11 @@ def run_reference(args):
     rng = np.random.default_rng(5)
     q = np.sort(rng.choice(N_POINTS, 20_000, replace=False))
     rows, _ = oracle.knn_kdtree(cloud.xyz, K, queries=q)
-    x = cloud.xyz.astype(np.float64)
-    d = np.linalg.norm(x[rows] - x[q][:, None, :], axis=2)
+    xd = cloud.xyz.astype(np.float64)
+    d = np.linalg.norm(xd[rows] - xd[q][:, None, :], axis=2)
     h = float(np.float32(2.0 * d[rows != q[:, None]].mean()))
     for _ in range(args.warmup):
-        cpu_baseline(cloud.xyz, h, 2_000)
+        cpu_baseline(cloud.xyz, h, 1_000)
     times = []
     info = None
     for _ in range(args.steps):
@@ -331,7 +349,7 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_s * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "points_per_gpu": N_POINTS, "k": K, "degree": 2,
-                   "step": "oracle: k-d tree + kNN + FP64 projection, sampled and extrapolated"},
+                   "step": "oracle: k-d tree + kNN + FP64 projection + FP64 adjoint, sampled and extrapolated"},
         "cpu_baseline": {"value": value, "unit": "points/s", "cores": 1, "kind": "oracle", "sample": info["sample"]},
         "e2e": {"value": value, "unit": "points/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
         "gpu_launches": 0,
@@ -344,7 +362,7 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--cpu-sample", type=int, default=50_000)
+    ap.add_argument("--cpu-sample", type=int, default=20_000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)     # at least three untimed warm-up steps

@@ -68,8 +68,8 @@ def _load():
                                       _f64p, _f64p]
     lib.oracle_project.argtypes = [_f32p, _i64, _i32p, _int, _dbl, _int, _i64p, _i64, _f64p, _f64p,
                                    _u8p, _f64p]
-    lib.oracle_project_grad.argtypes = [_f32p, _i64, _i32p, _int, _dbl, _int, _f64p, _f64p, _f64p,
-                                        _f64p]
+    lib.oracle_project_grad.argtypes = [_f32p, _i64, _i32p, _int, _dbl, _int, _f64p, _f64p, _i64p, _i64,
+                                        _f64p, _f64p]
     _lib = lib
     return lib
 
@@ -150,16 +150,22 @@ def project(xyz, idx, h, degree=2, queries=None):
     return out, nrm, st, diag
 
 
-def project_grad(xyz, idx, h, degree, gout_xyz, gout_normal=None):
+def project_grad(xyz, idx, h, degree, gout_xyz, gout_normal=None, queries=None):
+    """(dL/dxyz, dL/dh).  With `queries`, only those points' terms (idx: one
+    row per query) are summed."""
     xyz = _xyz(xyz)
     idx = np.ascontiguousarray(idx, np.int32)
     n, k = xyz.shape[0], idx.shape[1]
+    q = None if queries is None else np.ascontiguousarray(queries, np.int64)
+    m = n if q is None else q.shape[0]
+    assert idx.shape[0] == m
     gp = np.ascontiguousarray(gout_xyz, np.float64)
     gn = None if gout_normal is None else np.ascontiguousarray(gout_normal, np.float64)
     grad = np.empty((n, 3), np.float64)
     gh = np.zeros(1, np.float64)
     rc = _load().oracle_project_grad(_p(xyz, _f32p), n, _p(idx, _i32p), k, float(h), int(degree),
-                                     _p(gp, _f64p), _p(gn, _f64p), _p(grad, _f64p), _p(gh, _f64p))
+                                     _p(gp, _f64p), _p(gn, _f64p), _p(q, _i64p), m, _p(grad, _f64p),
+                                     _p(gh, _f64p))
     if rc != 0:
         raise ValueError(f"oracle_project_grad failed ({rc})")
     return grad, float(gh[0])

@@ -780,12 +780,14 @@ static void adjoint_point(const point_state *st, const int32_t *row, int64_t i,
     free(wbar);
 }
 
-/* Vector-Jacobian product of the projection over all n points:
- * grad_xyz (n x 3, overwritten) and *grad_h (overwritten) for the cotangents
- * gout_xyz (n x 3) and gout_normal (n x 3, or NULL for zero). */
+/* Vector-Jacobian product of the projection: grad_xyz (n x 3, overwritten)
+ * and *grad_h (overwritten) for the cotangents gout_xyz (n x 3) and
+ * gout_normal (n x 3, or NULL for zero).  With queries != NULL only the
+ * listed points' terms are summed (their rows are idx rows s, in order):
+ * the full product is the sum over all points. */
 int oracle_project_grad(const float *xyz, int64_t n, const int32_t *idx, int k, double h,
                         int degree, const double *gout_xyz, const double *gout_normal,
-                        double *grad_xyz, double *grad_h)
+                        const int64_t *queries, int64_t nq, double *grad_xyz, double *grad_h)
 {
     if (k < 1 || k > n || !(h > 0.0) || degree < 0 || degree > 2) return -1;
     point_state st;
@@ -795,9 +797,11 @@ int oracle_project_grad(const float *xyz, int64_t n, const int32_t *idx, int k, 
     }
     memset(grad_xyz, 0, sizeof(double) * 3 * (size_t)n);
     *grad_h = 0.0;
-    for (int64_t i = 0; i < n; ++i) {
-        project_point(xyz, idx + i * k, k, h, degree, i, &st);
-        adjoint_point(&st, idx + i * k, i, gout_xyz + 3 * i, gout_normal ? gout_normal + 3 * i : NULL,
+    int64_t m = queries ? nq : n;
+    for (int64_t s = 0; s < m; ++s) {
+        int64_t i = queries ? queries[s] : s;
+        project_point(xyz, idx + s * k, k, h, degree, i, &st);
+        adjoint_point(&st, idx + s * k, i, gout_xyz + 3 * i, gout_normal ? gout_normal + 3 * i : NULL,
                       grad_xyz, grad_h);
     }
     free_state(&st);

@@ -17,6 +17,7 @@
 // edge number) then sums them in a fixed order: results do not depend on
 // scheduling.
 #include <algorithm>
+#include <climits>
 
 #include "solve.cuh"
 
@@ -348,39 +349,90 @@ __global__ void k_edge_fill(const int32_t *__restrict__ idx, int64_t ne, const i
     }
 }
 
-// Sum of the edges that point at p, in ascending edge order (the bucket is
-// sorted in place first), plus p's own term.
-__global__ void k_gather(int64_t n, const int32_t *__restrict__ off, int32_t *__restrict__ ent,
-                         const float *__restrict__ edge_grad, const float *__restrict__ self_grad,
-                         float *__restrict__ grad) {
-    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
-        const int32_t b = off[p], e = off[p + 1];
-        for (int32_t t = b + 1; t < e; ++t) {
-            const int32_t v = ent[t];
-            int32_t u = t;
-            while (u > b && ent[u - 1] > v) {
-                ent[u] = ent[u - 1];
-                --u;
-            }
-            ent[u] = v;
-        }
-        float g[3] = {self_grad[3 * p], self_grad[3 * p + 1], self_grad[3 * p + 2]};
-        for (int32_t t = b; t < e; ++t) {
-            const int64_t edge = ent[t];
-#pragma unroll
-            for (int c = 0; c < 3; ++c) g[c] += edge_grad[edge * 3 + c];
-        }
-#pragma unroll
-        for (int c = 0; c < 3; ++c) grad[3 * p + c] = g[c];
+// Sum of the edges that point at p plus p's own term, one warp per target:
+// the bucket's edge numbers are sorted (bitonic network over 64 slots, two per
+// lane) and summed by a fixed tree over the sorted order, so the result does
+// not depend on the order in which the edges were bucketed.  Buckets above 64
+// entries (rare hubs) are sorted in place and summed by one lane.
+__device__ __forceinline__ void cswap(int &a, int &b, bool up) {
+    if ((a > b) == up) {
+        const int t = a;
+        a = b;
+        b = t;
     }
 }
 
-__global__ void k_sum_h(const double *__restrict__ part, int m, float *__restrict__ out) {
-    if (threadIdx.x == 0 && blockIdx.x == 0) {
-        double t = 0.0;
-        for (int i = 0; i < m; ++i) t += part[i];
-        *out = (float)t;
+__global__ void k_gather(int64_t n, const int32_t *__restrict__ off, int32_t *__restrict__ ent,
+                         const float *__restrict__ edge_grad, const float *__restrict__ self_grad,
+                         float *__restrict__ grad) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t p = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; p < n; p += warps) {
+        const int32_t b = off[p], m = off[p + 1] - b;
+        float g[3] = {0.f, 0.f, 0.f};
+        if (m <= 64) {
+            int v0 = 2 * lane < m ? ent[b + 2 * lane] : INT_MAX;
+            int v1 = 2 * lane + 1 < m ? ent[b + 2 * lane + 1] : INT_MAX;
+            // element e = 2 lane + r
+#pragma unroll
+            for (int kk = 2; kk <= 64; kk <<= 1) {
+#pragma unroll
+                for (int j = kk >> 1; j > 0; j >>= 1) {
+                    const bool up = ((2 * lane) & kk) == 0;
+                    if (j == 1) {
+                        cswap(v0, v1, up);
+                    } else {
+                        const int pl = j >> 1;
+                        const int o0 = __shfl_xor_sync(0xffffffffu, v0, pl);
+                        const int o1 = __shfl_xor_sync(0xffffffffu, v1, pl);
+                        const bool lower = (lane & pl) == 0;
+                        v0 = (lower == up) ? min(v0, o0) : max(v0, o0);
+                        v1 = (lower == up) ? min(v1, o1) : max(v1, o1);
+                    }
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const float a0 = v0 != INT_MAX ? edge_grad[(int64_t)v0 * 3 + c] : 0.f;
+                const float a1 = v1 != INT_MAX ? edge_grad[(int64_t)v1 * 3 + c] : 0.f;
+                float t = a0 + a1;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+                g[c] = t;
+            }
+        } else if (lane == 0) {
+            for (int32_t t = b + 1; t < b + m; ++t) {
+                const int32_t v = ent[t];
+                int32_t u = t;
+                while (u > b && ent[u - 1] > v) {
+                    ent[u] = ent[u - 1];
+                    --u;
+                }
+                ent[u] = v;
+            }
+            for (int32_t t = b; t < b + m; ++t)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) g[c] += edge_grad[(int64_t)ent[t] * 3 + c];
+        }
+        if (lane == 0)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) grad[3 * p + c] = self_grad[3 * p + c] + g[c];
     }
+}
+
+// dL/dh: the blocks' partial sums, each thread a fixed stride of them, then a
+// fixed tree.
+__global__ void __launch_bounds__(1024) k_sum_h(const double *__restrict__ part, int m, float *__restrict__ out) {
+    __shared__ double red[1024];
+    double t = 0.0;
+    for (int i = threadIdx.x; i < m; i += 1024) t += part[i];
+    red[threadIdx.x] = t;
+    __syncthreads();
+    for (int s = 512; s > 0; s >>= 1) {
+        if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = (float)red[0];
 }
 
 template <int DEG>
@@ -430,8 +482,8 @@ int launch_backward(const float *xyz, int64_t n, const int32_t *idx, int k, floa
     int rc = device_exclusive_scan(cnt, off, n + 1, st);
     if (rc != MLS_OK) return rc;
     k_edge_fill<<<gs, 256, 0, st>>>(idx, ne, off, fill, ent);
-    k_gather<<<(int)std::min<int64_t>((n + 127) / 128, 152 * 32), 128, 0, st>>>(n, off, ent, edge, self, grad_xyz);
-    k_sum_h<<<1, 32, 0, st>>>(hp, blocks, grad_h);
+    k_gather<<<(int)std::min<int64_t>((n * 32 + 255) / 256, 152 * 32), 256, 0, st>>>(n, off, ent, edge, self, grad_xyz);
+    k_sum_h<<<1, 1024, 0, st>>>(hp, blocks, grad_h);
     count_launches(6);
     MLS_CUDA_TRY(cudaGetLastError());
     cudaFreeAsync(xyz4, st);

@@ -399,3 +399,17 @@ def test_adjoint_matches_central_differences(degree):
     lp, _ = _loss(c.xyz, idx, h + eps, degree, gp, gn)
     lm, _ = _loss(c.xyz, idx, h - eps, degree, gp, gn)
     assert (lp - lm) / (2 * eps) == pytest.approx(gh, rel=1e-5)
+
+
+def test_adjoint_over_query_subsets_sums_to_the_whole():
+    c = workloads.sphere(n=1500, seed=52, k=12)
+    idx, _ = oracle.knn_kdtree(c.xyz, 12)
+    rng = np.random.default_rng(53)
+    gp = rng.standard_normal((1500, 3))
+    g_all, h_all = oracle.project_grad(c.xyz, idx, 0.1, 2, gp)
+    perm = rng.permutation(1500)
+    a, b = np.sort(perm[:700]), np.sort(perm[700:])
+    g_a, h_a = oracle.project_grad(c.xyz, idx[a], 0.1, 2, gp, queries=a)
+    g_b, h_b = oracle.project_grad(c.xyz, idx[b], 0.1, 2, gp, queries=b)
+    assert np.allclose(g_a + g_b, g_all, rtol=1e-12, atol=1e-12 * np.abs(g_all).max())
+    assert h_a + h_b == pytest.approx(h_all, rel=1e-12)

@@ -47,6 +47,31 @@ FLOPS_PER_POINT = 645
 KNN_BYTES_PER_POINT = 16 + 4 * K
 GRID_BYTES_PER_POINT = 12 + 16 + 8 + 4
 
+# Measured DRAM bytes per point of a stage (dram__bytes_read.sum +
+# dram__bytes_write.sum of its kernels, one ncu capture on a 1,000,000-point
+# torus, scaled by the point count), valid only while the kernel sources it was
+# taken on are unchanged (SHA-256 of each file).
+STAGE_TRAFFIC = {
+    "knn": (143.2, {
+        "paper_2401_03365_gb300/csrc/knn.cu": "d19d6be9d2e6bfe3fb8452fb3b4c7167e8b45774c0ff2c657d137d32aba9d8b7",
+        "paper_2401_03365_gb300/csrc/grid.cuh": "02304be6ff7be958e7766ce1581f3943c1909c21b0e47e12bca66d0553181ec5",
+        "paper_2401_03365_gb300/csrc/common.cuh": "41341bb3ed4b79ccd7a58380bc5758af08999e5a2b0756cf2855458f453f92cf",
+    }),
+}
+
+
+def stage_traffic(stage, n_points):
+    """DRAM bytes of one launch of the stage, or None when unmeasured or stale."""
+    import hashlib
+    if stage not in STAGE_TRAFFIC:
+        return None
+    per_point, sources = STAGE_TRAFFIC[stage]
+    for rel, digest in sources.items():
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            if hashlib.sha256(f.read()).hexdigest() != digest:
+                return None
+    return per_point * n_points
+
 
 def load_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -78,7 +103,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
         except (OSError, FileNotFoundError):
@@ -131,24 +156,25 @@ def run_ours(args):
     from paper_2401_03365_gb300 import build, capi, workloads
 
     world, rank, local = dist_setup(args)
+    n_pts = args.points
     torch.cuda.set_device(local)
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     build.build()
     dev = torch.device("cuda", local)
-    cloud = workloads.torus(n=N_POINTS, seed=2 + rank, k=K)
+    cloud = workloads.torus(n=n_pts, seed=2 + rank, k=K)
     x = torch.from_numpy(cloud.xyz).to(dev)
     stream = torch.cuda.current_stream()
 
-    idx = torch.empty((N_POINTS, K), dtype=torch.int32, device=dev)
+    idx = torch.empty((n_pts, K), dtype=torch.int32, device=dev)
     out_xyz = torch.empty_like(x)
     out_n = torch.empty_like(x)
-    out_st = torch.empty(N_POINTS, dtype=torch.uint8, device=dev)
+    out_st = torch.empty(n_pts, dtype=torch.uint8, device=dev)
     grad = torch.empty_like(x)
     grad_h = torch.empty(1, dtype=torch.float32, device=dev)
     gen = torch.Generator(device=dev).manual_seed(11 + rank)
-    gp = torch.randn((N_POINTS, 3), generator=gen, device=dev)          # cotangent of the points
-    gn = 0.1 * torch.randn((N_POINTS, 3), generator=gen, device=dev)    # cotangent of the normals
+    gp = torch.randn((n_pts, 3), generator=gen, device=dev)          # cotangent of the points
+    gn = 0.1 * torch.randn((n_pts, 3), generator=gen, device=dev)    # cotangent of the normals
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
     # bandwidth of the workload: 2 x mean kNN distance, from the GPU kNN
@@ -194,16 +220,16 @@ def run_ours(args):
     if world > 1:
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
     step_ms, fwd_ms = float(t[0]), float(t[1])
-    value = world * N_POINTS / (step_ms * 1e-3)
+    value = world * n_pts / (step_ms * 1e-3)
 
     # end to end through the public API with host buffers: every step copies
     # the points in from pinned memory, runs the four calls, and copies the
     # projected points, normals, status and gradient back
     host_in = torch.from_numpy(cloud.xyz).pin_memory()
-    host_xyz = torch.empty((N_POINTS, 3), dtype=torch.float32).pin_memory()
-    host_n = torch.empty((N_POINTS, 3), dtype=torch.float32).pin_memory()
-    host_st = torch.empty(N_POINTS, dtype=torch.uint8).pin_memory()
-    host_g = torch.empty((N_POINTS, 3), dtype=torch.float32).pin_memory()
+    host_xyz = torch.empty((n_pts, 3), dtype=torch.float32).pin_memory()
+    host_n = torch.empty((n_pts, 3), dtype=torch.float32).pin_memory()
+    host_st = torch.empty(n_pts, dtype=torch.uint8).pin_memory()
+    host_g = torch.empty((n_pts, 3), dtype=torch.float32).pin_memory()
     x_e2e = torch.empty_like(x)
     e2e_ms = []
     for s in range(min(max(args.steps, 3), 10) + 1):
@@ -224,7 +250,7 @@ def run_ours(args):
     te = torch.tensor([float(np.mean(e2e_ms))], dtype=torch.float64, device=dev)
     if world > 1:
         dist.all_reduce(te, op=dist.ReduceOp.MAX)
-    e2e_value = world * N_POINTS / (float(te.item()) * 1e-3)
+    e2e_value = world * n_pts / (float(te.item()) * 1e-3)
     grid.close()
     if rank != 0:
         if world > 1:
@@ -233,8 +259,8 @@ def run_ours(args):
         return None
 
     peaks = load_peaks()
-    proj_flops = N_POINTS * (FLOPS_PER_NEIGHBOUR * K + FLOPS_PER_POINT)
-    knn_gbs = N_POINTS * KNN_BYTES_PER_POINT / (knn_ms * 1e-3) / 1e9
+    proj_flops = n_pts * (FLOPS_PER_NEIGHBOUR * K + FLOPS_PER_POINT)
+    knn_gbs = n_pts * KNN_BYTES_PER_POINT / (knn_ms * 1e-3) / 1e9
     proj_tf = proj_flops / (proj_ms * 1e-3) / 1e12
     bwd_tf = 3 * proj_flops / (bwd_ms * 1e-3) / 1e12
     kernels = {
@@ -250,15 +276,15 @@ def run_ours(args):
     if dom == "knn" or dom == "grid_build":
         ms = kernels[dom]["ms"]
         bytes_pp = KNN_BYTES_PER_POINT if dom == "knn" else GRID_BYTES_PER_POINT
-        ach = N_POINTS * bytes_pp / (ms * 1e-3) / 1e9
+        ach = n_pts * bytes_pp / (ms * 1e-3) / 1e9
         roofline = {"kernel": kernels[dom]["calls"], "bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"],
-                    "unit": "GB/s", "frac": ach / peaks["hbm_gbs"], "traffic": None,
+                    "unit": "GB/s", "frac": ach / peaks["hbm_gbs"], "traffic": stage_traffic(dom, n_pts),
                     "peak_source": f"{peaks['source']} hbm_gbs (copy)",
                     "algorithmic_bytes_per_point": bytes_pp}
     else:
         ach = proj_tf if dom == "project" else bwd_tf
         roofline = {"kernel": kernels[dom]["calls"], "bound": "alu", "achieved": ach, "peak": peaks["fp32_tflops"],
-                    "unit": "TFLOP/s", "frac": ach / peaks["fp32_tflops"], "traffic": None,
+                    "unit": "TFLOP/s", "frac": ach / peaks["fp32_tflops"], "traffic": stage_traffic(dom, n_pts),
                     "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 flops x max SM clock"}
     line = {
         "metric": METRIC,
@@ -273,16 +299,18 @@ def run_ours(args):
         "vs_baseline": None,
         "dtype": "f32",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "points_per_gpu": N_POINTS, "k": K, "degree": 2, "precision": "mixed",
+        "config": {"workload": WORKLOAD if n_pts == N_POINTS else
+                   WORKLOAD.replace("2,000,000", f"{n_pts:,}").replace("torus2m", "torus") + " (profiling size)",
+                   "points_per_gpu": n_pts, "k": K, "degree": 2, "precision": "mixed",
                    "h": h, "step": "grid build + exact kNN + MLS projection + backward (fwd+bwd)",
                    "l2": "flushed before every step (256 MB write, outside the timed events)",
                    "parallelism": f"independent clouds per GPU x{world}"},
-        "fwd": {"value": world * N_POINTS / (fwd_ms * 1e-3), "unit": "points/s", "ms_per_step": fwd_ms,
+        "fwd": {"value": world * n_pts / (fwd_ms * 1e-3), "unit": "points/s", "ms_per_step": fwd_ms,
                 "step": "grid build + exact kNN + MLS projection"},
         "roofline": roofline,
         "kernels": kernels,
-        "e2e": {"value": e2e_value, "unit": "points/s", "h2d_bytes_per_step": N_POINTS * 12,
-                "d2h_bytes_per_step": N_POINTS * (12 + 12 + 1 + 12)},
+        "e2e": {"value": e2e_value, "unit": "points/s", "h2d_bytes_per_step": n_pts * 12,
+                "d2h_bytes_per_step": n_pts * (12 + 12 + 1 + 12)},
         "gpu_launches": int(launches),
         "clocks": clocks.summary(),
         "wall_s_timed_region": wall,
@@ -364,6 +392,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--cpu-sample", type=int, default=20_000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--points", type=int, default=N_POINTS,
+                    help="cloud size; smaller than the default only for profiling captures")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)     # at least three untimed warm-up steps
     line = run_reference(args) if args.impl == "reference" else run_ours(args)

@@ -317,10 +317,102 @@ def run_ours(args):
     }
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(cloud.xyz, h, args.cpu_sample)
+    if world == 1 and not args.no_batched:
+        line["batched"] = run_batched(args, dev)
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
     return line
+
+
+def run_batched(args, dev):
+    """The batched form on 256 clouds (ellipsoids and superquadrics, sizes
+    log-uniform in 1e3..5e5, k in {16, 32, 64}): one graph replay of the
+    autotuned persistent mixed-precision launch against 256 per-cloud launches
+    of the plain FP64 projection, on the same rows and h."""
+    import torch
+
+    from paper_2401_03365_gb300 import capi, workloads
+    from paper_2401_03365_gb300.batched import BatchedProjector, TuneCache
+
+    t0 = time.perf_counter()
+    clouds = workloads.batch_clouds(workers=min(os.cpu_count() or 1, 16))
+    t_gen = time.perf_counter() - t0
+    xs = [torch.from_numpy(c.xyz).to(dev) for c in clouds]
+    bp = BatchedProjector.from_clouds(xs, [c.k for c in clouds])
+    total = bp.batch.total
+    import tempfile
+    cache = TuneCache(os.path.join(tempfile.gettempdir(), "mls_autotune_bench.json"))
+    tuned = bp.tune(cache=cache, reps=2, retune=True)
+    bp.capture()
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        bp.replay()
+    torch.cuda.synchronize()
+    steps = max(args.steps, 5)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    ev[0].record(stream)
+    for _ in range(steps):
+        bp.replay()
+    ev[1].record(stream)
+    torch.cuda.synchronize()
+    batched_ms = ev[0].elapsed_time(ev[1]) / steps
+
+    # the plain FP64 form, one launch per cloud, into its own outputs
+    f_xyz = torch.empty_like(bp.xyz)
+    f_n = torch.empty_like(bp.xyz)
+    f_st = torch.empty(total, dtype=torch.uint8, device=dev)
+    views = []
+    for c, cl in enumerate(clouds):
+        a, e = bp.batch.offsets[c], bp.batch.offsets[c + 1]
+        views.append((bp.xyz[a:e], bp.idx[bp.batch.idx_offset(c):bp.batch.idx_offset(c + 1)].view(e - a, cl.k),
+                      float(bp.h[c].item()), bp.order[a:e], f_xyz[a:e], f_n[a:e], f_st[a:e]))
+
+    def fp64_pass():
+        for x, idx, h, order, ox, on, os_ in views:
+            capi.mls_project(x, idx, h, 2, "fp64", order=order, out_xyz=ox, out_normal=on, out_status=os_)
+
+    fp64_pass()
+    torch.cuda.synchronize()
+    reps = 2
+    ev[0].record(stream)
+    for _ in range(reps):
+        fp64_pass()
+    ev[1].record(stream)
+    torch.cuda.synchronize()
+    fp64_ms = ev[0].elapsed_time(ev[1]) / reps
+
+    # accuracy of the batched mixed form against the FP64 form, per cloud in
+    # units of its bounding-box diagonal, on points both call regular
+    devs = []
+    for c in range(len(clouds)):
+        a, e = bp.batch.offsets[c], bp.batch.offsets[c + 1]
+        x = bp.xyz[a:e]
+        diag = float((x.max(0).values - x.min(0).values).norm())
+        ok = ((bp.out_status[a:e] & 3) == 0) & ((f_st[a:e] & 3) == 0)
+        d = ((bp.out_xyz[a:e] - f_xyz[a:e]).double().norm(dim=1) / diag)[ok]
+        devs.append(d)
+    devs = torch.cat(devs)
+    acc = {"max": float(devs.max()), "p99_99": float(torch.quantile(devs[:: max(1, devs.numel() // 1_000_000)],
+                                                                     0.9999)),
+           "frac_within_1e-5": float((devs <= 1e-5).double().mean())}
+    ks = [c.k for c in clouds]
+    out = {
+        "workload": (f"batch256: {len(clouds)} clouds, {total:,} points, k=16/32/64 on {ks.count(16)}/"
+                     f"{ks.count(32)}/{ks.count(64)} clouds, degree 2, per-cloud h = 2 x mean kNN distance"),
+        "value": total / (batched_ms * 1e-3), "unit": "points/s", "ms": batched_ms,
+        "form": "one CUDA-graph replay: memset + float4 pack + persistent kernel, mixed precision",
+        "shape": {"lanes_per_point": tuned["shape"][0], "threads": tuned["shape"][1],
+                  "rounds": tuned["shape"][2]},
+        "autotune_ms": {f"{g}x{t}x{r}": round(ms, 4) for g, t, r, ms in tuned["table"]},
+        "fp64_per_cloud": {"value": total / (fp64_ms * 1e-3), "unit": "points/s", "ms": fp64_ms,
+                           "form": f"{len(clouds)} mls_project launches, precision fp64"},
+        "speedup_vs_fp64_per_cloud": fp64_ms / batched_ms,
+        "deviation_from_fp64_in_diag": acc,
+        "setup_s": {"generate": t_gen},
+    }
+    bp.close()
+    return out
 
 
 def cpu_baseline(xyz, h, sample):
@@ -368,7 +460,7 @@ def run_reference(args):
     times = []
     info = None
     for _ in range(args.steps):
-        info = cpu_baseline(cloud.xyz, h, args.cpu_sample)
+        info = cpu_baseline(cloud.xyz, h, args.ref_sample)
         times.append(N_POINTS / info["value"])
     step_s = float(np.mean(times))
     value = N_POINTS / step_s
@@ -390,8 +482,12 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--cpu-sample", type=int, default=20_000)
+    ap.add_argument("--cpu-sample", type=int, default=300_000,
+                    help="sampled queries of the cpu_baseline leg (about 10 s of oracle work)")
+    ap.add_argument("--ref-sample", type=int, default=100_000,
+                    help="sampled queries per step of --impl reference")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true", help="skip the 256-cloud batched measurement")
     ap.add_argument("--points", type=int, default=N_POINTS,
                     help="cloud size; smaller than the default only for profiling captures")
     args = ap.parse_args()

@@ -204,6 +204,86 @@ int mls_project_backward(const float *d_xyz, int64_t n, const int32_t *d_idx, in
 int mls_mean_knn_dist(const float *d_xyz, int64_t n, const int32_t *d_idx, int k, double *d_out,
                       mls_stream stream);
 
+/*
+ * Batched projection -- many independent clouds in one persistent launch.
+ * Algorithm 1 projects every point of one cloud independently; here that
+ * per-point loop runs over the union of B clouds of uneven size, each with
+ * its own k and h, in a single kernel whose blocks take tiles of points from
+ * a shared counter (the paper has no batched form; its per-point arithmetic is
+ * that of mls_project).  A batch handle fixes the cloud sizes and k; the
+ * point data can change between launches.
+ *
+ * Layouts (all DEVICE memory owned by the caller):
+ *   d_xyz    total x 3 floats: the clouds one after another, cloud c at rows
+ *            offsets[c] .. offsets[c+1]-1
+ *   d_idx    the clouds' neighbour rows one after another: cloud c's n_c x k_c
+ *            rows start at element mls_batch_idx_offset(b, c) =
+ *            sum_{c' < c} n_c' k_c', with indices LOCAL to the cloud (0..n_c-1),
+ *            as mls_knn writes them for that cloud alone
+ *   d_order  total int32 or NULL: cloud c's slice is a permutation of 0..n_c-1
+ *            (e.g. its mls_grid_order); speed only, never results
+ *   d_h      B floats: each cloud's bandwidth, finite and > 0
+ *   outputs  d_out_xyz total x 3, d_out_normal total x 3 or NULL, d_status
+ *            total bytes or NULL, at the input's rows
+ * degree 0, 1 or 2; precision MLS_PREC_FP32 or MLS_PREC_MIXED.
+ */
+typedef struct mls_batch mls_batch;
+
+/* Creates a batch of `batch` clouds: h_offsets (HOST, batch + 1 entries,
+ * offsets[0] = 0, every cloud at least one point, total < 2^31) and h_k (HOST,
+ * batch entries, 1 <= k_c <= min(MLS_MAX_K, n_c)).  Allocates about
+ * 16 x total bytes of device scratch on the current device and synchronises.
+ * Launch shape starts at 1 lane per point, 128 threads, 1 round per tile. */
+int mls_batch_create(int batch, const int64_t *h_offsets, const int32_t *h_k, mls_batch **out);
+
+/* Synchronises the device and frees the batch (NULL is ignored). */
+void mls_batch_destroy(mls_batch *b);
+
+/* Total points of the batch (-1 for NULL). */
+int64_t mls_batch_total(const mls_batch *b);
+
+/* Element offset of cloud `cloud`'s rows in d_idx (cloud = batch gives the
+ * total length); -1 for a bad argument. */
+int64_t mls_batch_idx_offset(const mls_batch *b, int cloud);
+
+/* Launch shape: lanes_per_point in {1, 2, 4, 8, 16, 32} (G lanes share a
+ * point's neighbours and merge their moments), threads per block (multiple of
+ * 32, <= 256), rounds of blockDim / G points per tile (1..64).  Changing the
+ * shape drops a captured graph.  Synchronous. */
+int mls_batch_set_shape(mls_batch *b, int lanes_per_point, int threads, int rounds);
+int mls_batch_get_shape(const mls_batch *b, int *lanes_per_point, int *threads, int *rounds);
+
+/* One batched projection on `stream`: a 4-byte memset of the tile counter, a
+ * float4 copy of the points, and the persistent projection kernel. */
+int mls_project_batched(mls_batch *b, const float *d_xyz, const int32_t *d_idx, const int32_t *d_order,
+                        const float *d_h, int degree, int precision, float *d_out_xyz, float *d_out_normal,
+                        uint8_t *d_status, mls_stream stream);
+
+/* Captures mls_project_batched with these buffers (on a private stream) into a
+ * CUDA graph held by the batch, replacing any earlier one.  Nothing runs.  The
+ * buffers must stay valid while the graph is replayed; their contents (points,
+ * rows, h) may change between replays. */
+int mls_batch_capture(mls_batch *b, const float *d_xyz, const int32_t *d_idx, const int32_t *d_order,
+                      const float *d_h, int degree, int precision, float *d_out_xyz, float *d_out_normal,
+                      uint8_t *d_status);
+
+/* Launches the captured graph on `stream`. */
+int mls_batch_replay(mls_batch *b, mls_stream stream);
+
+/* Autotuner: runs every candidate shape (lanes 1, 2, 4, 8 x threads 64, 128,
+ * 256 x rounds 1, 4) once untimed and `reps` times timed with CUDA events on
+ * `stream`, keeps the fastest, and leaves that shape's results in the outputs.
+ * Synchronises `stream`.  Results of different shapes agree to rounding (the
+ * lanes of a point sum in a different order). */
+int mls_batch_autotune(mls_batch *b, const float *d_xyz, const int32_t *d_idx, const int32_t *d_order,
+                       const float *d_h, int degree, int precision, float *d_out_xyz, float *d_out_normal,
+                       uint8_t *d_status, int reps, mls_stream stream);
+
+/* The last autotune's timings: up to `capacity` entries of (lanes, threads,
+ * rounds) into shapes (3 int32 each, HOST) and the best time in ms into ms
+ * (HOST); either may be NULL.  Returns the number of entries. */
+int mls_batch_tune_results(const mls_batch *b, int capacity, int32_t *shapes, float *ms);
+
 /* Number of CUDA kernels this library has launched in the process so far
  * (all threads).  Host-side count, for accounting in benchmarks. */
 int64_t mls_kernel_launches(void);

@@ -18,6 +18,8 @@ from .build import library_path
 __all__ = [
     "MLSError", "Grid", "lib", "mls_build_grid", "mls_grid_destroy", "mls_grid_size", "mls_grid_order",
     "mls_knn", "mls_project", "mls_project_backward", "mls_mean_knn_dist", "mls_status_str", "mls_last_error", "mls_kernel_launches",
+    "Batch", "mls_batch_create", "mls_batch_destroy", "mls_batch_set_shape", "mls_batch_get_shape",
+    "mls_project_batched", "mls_batch_capture", "mls_batch_replay", "mls_batch_autotune", "mls_batch_tune_results",
     "PRECISION", "MLS_MAX_K", "MLS_PT_OK", "MLS_PT_PLANE_DEGENERATE", "MLS_PT_POLY_SINGULAR",
     "MLS_PT_FP64_USED", "EXPORTED_SYMBOLS",
 ]
@@ -43,6 +45,17 @@ _SIGNATURES = [
     ("mls_project_noalloc", _int, [_vp, _i64, _vp, _int, _flt, _int, _int, _vp, _vp, _vp, _vp, _vp]),
     ("mls_project_backward", _int, [_vp, _i64, _vp, _int, _flt, _int, _int, _vp, _vp, _vp, _vp, _vp, _vp]),
     ("mls_mean_knn_dist", _int, [_vp, _i64, _vp, _int, _vp, _vp]),
+    ("mls_batch_create", _int, [_int, _vp, _vp, ctypes.POINTER(_vp)]),
+    ("mls_batch_destroy", None, [_vp]),
+    ("mls_batch_total", _i64, [_vp]),
+    ("mls_batch_idx_offset", _i64, [_vp, _int]),
+    ("mls_batch_set_shape", _int, [_vp, _int, _int, _int]),
+    ("mls_batch_get_shape", _int, [_vp, ctypes.POINTER(_int), ctypes.POINTER(_int), ctypes.POINTER(_int)]),
+    ("mls_project_batched", _int, [_vp, _vp, _vp, _vp, _vp, _int, _int, _vp, _vp, _vp, _vp]),
+    ("mls_batch_capture", _int, [_vp, _vp, _vp, _vp, _vp, _int, _int, _vp, _vp, _vp]),
+    ("mls_batch_replay", _int, [_vp, _vp]),
+    ("mls_batch_autotune", _int, [_vp, _vp, _vp, _vp, _vp, _int, _int, _vp, _vp, _vp, _int, _vp]),
+    ("mls_batch_tune_results", _int, [_vp, _int, _vp, _vp]),
     ("mls_kernel_launches", _i64, []),
     ("mls_last_error", ctypes.c_char_p, []),
     ("mls_status_str", ctypes.c_char_p, [_int]),
@@ -257,3 +270,135 @@ def mls_mean_knn_dist(xyz: torch.Tensor, idx: torch.Tensor, stream=None) -> torc
     _check("mls_mean_knn_dist", lib().mls_mean_knn_dist(_ptr(xyz), xyz.shape[0], _ptr(idx), idx.shape[1],
                                                         _ptr(out), _stream(stream)))
     return out
+
+
+class Batch:
+    """Owner of an mls_batch handle (clouds' sizes and k fixed at creation)."""
+
+    def __init__(self, handle, offsets, ks):
+        self.handle = handle
+        self.offsets = [int(o) for o in offsets]
+        self.ks = [int(k) for k in ks]
+        self.total = self.offsets[-1]
+        self.idx_len = int(lib().mls_batch_idx_offset(handle, len(self.ks)))
+        self._keep = ()             # buffers a captured graph refers to
+
+    def idx_offset(self, cloud: int) -> int:
+        return int(lib().mls_batch_idx_offset(self.handle, int(cloud)))
+
+    def close(self):
+        if self.handle:
+            lib().mls_batch_destroy(self.handle)
+            self.handle = None
+            self._keep = ()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def mls_batch_create(offsets, ks) -> Batch:
+    """offsets: B + 1 point offsets (host sequence); ks: B neighbour counts."""
+    offsets = [int(o) for o in offsets]
+    ks = [int(k) for k in ks]
+    if len(offsets) != len(ks) + 1:
+        raise ValueError("offsets must have one entry more than ks")
+    off = (ctypes.c_int64 * len(offsets))(*offsets)
+    kk = (ctypes.c_int32 * max(len(ks), 1))(*ks)
+    h = _vp()
+    _check("mls_batch_create", lib().mls_batch_create(len(ks), off, kk, ctypes.byref(h)))
+    return Batch(h, offsets, ks)
+
+
+def mls_batch_destroy(batch: Batch) -> None:
+    batch.close()
+
+
+def mls_batch_set_shape(batch: Batch, lanes_per_point: int, threads: int, rounds: int) -> None:
+    _check("mls_batch_set_shape", lib().mls_batch_set_shape(batch.handle, int(lanes_per_point), int(threads),
+                                                            int(rounds)))
+    batch._keep = ()
+
+
+def mls_batch_get_shape(batch: Batch) -> tuple[int, int, int]:
+    g, t, r = _int(), _int(), _int()
+    _check("mls_batch_get_shape", lib().mls_batch_get_shape(batch.handle, ctypes.byref(g), ctypes.byref(t),
+                                                            ctypes.byref(r)))
+    return g.value, t.value, r.value
+
+
+def _batch_args(batch, xyz, idx, h, order, out_xyz, out_normal, out_status, want_normal, want_status):
+    n = batch.total
+    _need(xyz, "xyz", torch.float32, (n, 3))
+    _need(idx, "idx", torch.int32, (batch.idx_len,))
+    _need(h, "h", torch.float32, (len(batch.ks),))
+    if order is not None:
+        _need(order, "order", torch.int32, (n,))
+    if out_xyz is None:
+        out_xyz = torch.empty_like(xyz)
+    _need(out_xyz, "out_xyz", torch.float32, (n, 3))
+    if out_normal is None and want_normal:
+        out_normal = torch.empty_like(xyz)
+    if out_normal is not None:
+        _need(out_normal, "out_normal", torch.float32, (n, 3))
+    if out_status is None and want_status:
+        out_status = torch.empty(n, dtype=torch.uint8, device=xyz.device)
+    if out_status is not None:
+        _need(out_status, "out_status", torch.uint8, (n,))
+    return out_xyz, out_normal, out_status
+
+
+def mls_project_batched(batch: Batch, xyz: torch.Tensor, idx: torch.Tensor, h: torch.Tensor, degree: int = 2,
+                        precision: str = "mixed", order: torch.Tensor | None = None, out_xyz=None, out_normal=None,
+                        out_status=None, want_normal: bool = True, want_status: bool = True, stream=None):
+    """xyz (total, 3) float32; idx the concatenated per-cloud rows (flat int32,
+    cloud-local indices); h (B,) float32 on the device."""
+    out_xyz, out_normal, out_status = _batch_args(batch, xyz, idx, h, order, out_xyz, out_normal, out_status,
+                                                  want_normal, want_status)
+    rc = lib().mls_project_batched(batch.handle, _ptr(xyz), _ptr(idx), _ptr(order), _ptr(h), int(degree),
+                                   PRECISION[precision], _ptr(out_xyz), _ptr(out_normal), _ptr(out_status),
+                                   _stream(stream))
+    _check("mls_project_batched", rc)
+    return out_xyz, out_normal, out_status
+
+
+def mls_batch_capture(batch: Batch, xyz, idx, h, degree: int = 2, precision: str = "mixed", order=None,
+                      out_xyz=None, out_normal=None, out_status=None, want_normal: bool = True,
+                      want_status: bool = True):
+    """Captures one batched projection into the batch's CUDA graph; returns the
+    output tensors the graph writes (kept alive with the inputs by the batch)."""
+    out_xyz, out_normal, out_status = _batch_args(batch, xyz, idx, h, order, out_xyz, out_normal, out_status,
+                                                  want_normal, want_status)
+    rc = lib().mls_batch_capture(batch.handle, _ptr(xyz), _ptr(idx), _ptr(order), _ptr(h), int(degree),
+                                 PRECISION[precision], _ptr(out_xyz), _ptr(out_normal), _ptr(out_status))
+    _check("mls_batch_capture", rc)
+    batch._keep = (xyz, idx, h, order, out_xyz, out_normal, out_status)
+    return out_xyz, out_normal, out_status
+
+
+def mls_batch_replay(batch: Batch, stream=None) -> None:
+    _check("mls_batch_replay", lib().mls_batch_replay(batch.handle, _stream(stream)))
+
+
+def mls_batch_autotune(batch: Batch, xyz, idx, h, degree: int = 2, precision: str = "mixed", order=None,
+                       out_xyz=None, out_normal=None, out_status=None, reps: int = 3, stream=None):
+    """Times every candidate launch shape and keeps the fastest; returns
+    (shape, [(lanes, threads, rounds, ms), ...])."""
+    out_xyz, out_normal, out_status = _batch_args(batch, xyz, idx, h, order, out_xyz, out_normal, out_status,
+                                                  True, True)
+    rc = lib().mls_batch_autotune(batch.handle, _ptr(xyz), _ptr(idx), _ptr(order), _ptr(h), int(degree),
+                                  PRECISION[precision], _ptr(out_xyz), _ptr(out_normal), _ptr(out_status),
+                                  int(reps), _stream(stream))
+    _check("mls_batch_autotune", rc)
+    batch._keep = ()
+    return mls_batch_get_shape(batch), mls_batch_tune_results(batch)
+
+
+def mls_batch_tune_results(batch: Batch):
+    n = int(lib().mls_batch_tune_results(batch.handle, 0, None, None))
+    shapes = (ctypes.c_int32 * (3 * max(n, 1)))()
+    ms = (ctypes.c_float * max(n, 1))()
+    lib().mls_batch_tune_results(batch.handle, n, shapes, ms)
+    return [(shapes[3 * i], shapes[3 * i + 1], shapes[3 * i + 2], float(ms[i])) for i in range(n)]

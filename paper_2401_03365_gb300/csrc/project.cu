@@ -1,28 +1,22 @@
-// The per-point MLS projection (Sec. 1.4, Eq. 1; Algorithm 1): weighted plane,
-// origin q on it, local height polynomial, projection onto the polynomial.
-//
-// One thread per point (each point is independent, as the paper's information
-// graph shows), so the per-point 3x3 eigensolve and 6x6 solve run on every
-// lane at once.  FP32 / mixed form: pass A gathers the k neighbours, forms
-// d_j = p_j - r and w_j = exp(-|d_j|^2 / h^2) and stages (d_j, w_j) in shared
-// memory (entry j of thread t at j * blockDim + t: conflict-free float4
-// accesses); pass B accumulates the covariance about the weighted centroid;
-// pass C accumulates the 15 monomial moments and 6 right-hand sides of the
-// degree-2 normal equations in local coordinates scaled by 1/h.
+// The single-cloud MLS projection kernels (Sec. 1.4, Eq. 1; Algorithm 1):
+// weighted plane, origin q on it, local height polynomial, projection onto
+// the polynomial.  One thread per point (each point is independent, as the
+// paper's information graph shows), so the per-point 3x3 eigensolve and 6x6
+// solve run on every lane at once; the per-point arithmetic is
+// project_point (project_point.cuh).  The FP64 form is a plain restatement in
+// double, kept as the slow comparison path.
 #include <algorithm>
 #include <cfloat>
 #include <cmath>
 #include <mutex>
 
-#include "solve.cuh"
+#include "project_point.cuh"
 
 namespace mls {
 
 namespace {
 
 constexpr int kProjThreads = 128;
-constexpr float kMixedGapFlag = 1e-3f;     // FP32 eigensolve trusted above this gap ratio
-constexpr float kMixedCondFlag = 1e5f;     // FP32 Cholesky trusted below this condition estimate
 
 // Copy of the points as float4 (w = 0): one 16-byte load per neighbour gather.
 __global__ void k_pack_xyz4(const float *__restrict__ xyz, int64_t n, float4 *__restrict__ xyz4) {
@@ -32,12 +26,8 @@ __global__ void k_pack_xyz4(const float *__restrict__ xyz, int64_t n, float4 *__
 
 // FP32 / mixed projection, one thread per point.  The warp first copies its
 // 32 neighbour rows into shared memory with coalesced loads (stored
-// transposed, entry j of lane t at j * 32 + t).  Pass 1 gathers each
-// neighbour once and accumulates the weight, the weighted centroid offset and
-// the covariance about it with the weighted online update of West (1979):
-// with W' = W + w, delta = d - m: m += delta w / W', C += (W w / W') delta
-// delta^T -- as accurate as a second centred pass, without storing d.
-// Pass 2 gathers again (now from L1) for the height-fit moments.
+// transposed, entry j of lane t at j * 32 + t), then every lane runs
+// project_point on its own point.
 template <int DEG, int PREC>
 __global__ void __launch_bounds__(kProjThreads) k_project(const float4 *__restrict__ xyz4, int64_t n,
                                                           const int32_t *__restrict__ idx, int k, float h,
@@ -60,126 +50,12 @@ __global__ void __launch_bounds__(kProjThreads) k_project(const float4 *__restri
     __syncwarp();
     if (slot >= n) return;
     const float4 r4 = __ldg(xyz4 + i);
-    const float rx = r4.x, ry = r4.y, rz = r4.z;
-    // exp(-|d|^2 / h^2) = exp2(-|d|^2 * log2(e) / h^2)
-    const float neg_scale = -1.4426950408889634f / (h * h);
-
-    // pass 1: weight W, centroid offset m, covariance C (unnormalised)
-    float W = 0.f, mx = 0.f, my = 0.f, mz = 0.f;
-    float C[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-#pragma unroll 4
-    for (int j = 0; j < k; ++j) {
-        const float4 p = __ldg(xyz4 + my_rows[j * 32 + lane]);
-        const float dx = p.x - rx, dy = p.y - ry, dz = p.z - rz;
-        const float w = exp2f(fmaf(dx, dx, fmaf(dy, dy, dz * dz)) * neg_scale);
-        const float Wn = W + w;
-        const float c = __fdividef(w, Wn);
-        const float ex = dx - mx, ey = dy - my, ez = dz - mz;
-        mx = fmaf(ex, c, mx);
-        my = fmaf(ey, c, my);
-        mz = fmaf(ez, c, mz);
-        const float f = W * c;
-        const float fx = f * ex, fy = f * ey, fz = f * ez;
-        C[0] = fmaf(fx, ex, C[0]);
-        C[1] = fmaf(fx, ey, C[1]);
-        C[2] = fmaf(fx, ez, C[2]);
-        C[3] = fmaf(fy, ey, C[3]);
-        C[4] = fmaf(fy, ez, C[4]);
-        C[5] = fmaf(fz, ez, C[5]);
-        W = Wn;
-    }
-    uint8_t st = 0;
-    float nf[3], e1f[3], e2f[3];
-    {
-        float lam[3];
-        int deg_flag = frame_from<float>(C, nf, e1f, e2f, lam);
-        // the FP32 eigenvector error grows like eps * l2 / (l1 - l0): in the
-        // mixed form, narrow gaps are solved again in FP64 from the same moments
-        if (PREC == MLS_PREC_MIXED && (!(lam[2] > 0.f) || (lam[1] - lam[0]) < kMixedGapFlag * lam[2])) {
-            double Cd[6], nd[3], e1d[3], e2d[3], ld[3];
-#pragma unroll
-            for (int c = 0; c < 6; ++c) Cd[c] = (double)C[c];
-            deg_flag = frame_from<double>(Cd, nd, e1d, e2d, ld);
-#pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                nf[a] = (float)nd[a];
-                e1f[a] = (float)e1d[a];
-                e2f[a] = (float)e2d[a];
-            }
-            st |= MLS_PT_FP64_USED;
-        }
-        st |= (uint8_t)deg_flag;
-    }
-    float px = rx, py = ry, pz = rz;
-    if (!(st & MLS_PT_PLANE_DEGENERATE)) {
-        const float ofs = nf[0] * mx + nf[1] * my + nf[2] * mz;
-        const float ih = 1.f / h;
-        const float a1x = e1f[0] * ih, a1y = e1f[1] * ih, a1z = e1f[2] * ih;
-        const float a2x = e2f[0] * ih, a2y = e2f[1] * ih, a2z = e2f[2] * ih;
-        // pass 2: moments of the height fit
-        float mom[15], rhs[6];
-#pragma unroll
-        for (int c = 0; c < 15; ++c) mom[c] = 0.f;
-#pragma unroll
-        for (int c = 0; c < 6; ++c) rhs[c] = 0.f;
-#pragma unroll 2
-        for (int j = 0; j < k; ++j) {
-            const float4 p = __ldg(xyz4 + my_rows[j * 32 + lane]);
-            const float dx = p.x - rx, dy = p.y - ry, dz = p.z - rz;
-            const float w = exp2f(fmaf(dx, dx, fmaf(dy, dy, dz * dz)) * neg_scale);
-            const float f = fmaf(nf[2], dz, fmaf(nf[1], dy, fmaf(nf[0], dx, -ofs)));
-            const float wf = w * f;
-            mom[0] += w;
-            rhs[0] += wf;
-            if (DEG >= 1) {
-                const float u = fmaf(a1z, dz, fmaf(a1y, dy, a1x * dx));
-                const float vv = fmaf(a2z, dz, fmaf(a2y, dy, a2x * dx));
-                const float wu = w * u, wv = w * vv;
-                mom[1] += wu;
-                mom[2] += wv;
-                rhs[1] = fmaf(wf, u, rhs[1]);
-                rhs[2] = fmaf(wf, vv, rhs[2]);
-                const float wuu = wu * u, wuv = wu * vv, wvv = wv * vv;
-                mom[3] += wuu;
-                mom[4] += wuv;
-                mom[5] += wvv;
-                if (DEG >= 2) {
-                    const float uu = u * u, uv = u * vv, v2 = vv * vv;
-                    mom[6] = fmaf(wuu, u, mom[6]);
-                    mom[7] = fmaf(wuu, vv, mom[7]);
-                    mom[8] = fmaf(wvv, u, mom[8]);
-                    mom[9] = fmaf(wvv, vv, mom[9]);
-                    mom[10] = fmaf(wuu, uu, mom[10]);
-                    mom[11] = fmaf(wuu, uv, mom[11]);
-                    mom[12] = fmaf(wuu, v2, mom[12]);
-                    mom[13] = fmaf(wvv, uv, mom[13]);
-                    mom[14] = fmaf(wvv, v2, mom[14]);
-                    rhs[3] = fmaf(wf, uu, rhs[3]);
-                    rhs[4] = fmaf(wf, uv, rhs[4]);
-                    rhs[5] = fmaf(wf, v2, rhs[5]);
-                }
-            }
-        }
-        bool singular;
-        float cond;
-        float a0 = solve_a0<float, DEG>(mom, rhs, true, singular, cond);
-        if (PREC == MLS_PREC_MIXED && (singular || !(cond < kMixedCondFlag))) {
-            double condd;
-            a0 = (float)solve_a0<double, DEG>(mom, rhs, false, singular, condd);
-            st |= MLS_PT_FP64_USED;
-        }
-        if (singular) {
-            st |= MLS_PT_POLY_SINGULAR;
-            a0 = 0.f;
-        }
-        const float s = ofs + a0;
-        px = fmaf(s, nf[0], rx);
-        py = fmaf(s, nf[1], ry);
-        pz = fmaf(s, nf[2], rz);
-    }
-    out_xyz[3 * i] = px;
-    out_xyz[3 * i + 1] = py;
-    out_xyz[3 * i + 2] = pz;
+    float out[3], nf[3];
+    const uint8_t st = project_point<DEG, PREC>(
+        xyz4, [&](int j) { return my_rows[j * 32 + lane]; }, k, 0, 1, h, r4.x, r4.y, r4.z, out, nf);
+    out_xyz[3 * i] = out[0];
+    out_xyz[3 * i + 1] = out[1];
+    out_xyz[3 * i + 2] = out[2];
     if (out_n) {
         out_n[3 * i] = nf[0];
         out_n[3 * i + 1] = nf[1];

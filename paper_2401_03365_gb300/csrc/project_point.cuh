@@ -1,0 +1,196 @@
+// The per-point MLS projection (Sec. 1.4, Eq. 1; Algorithm 1) as one device
+// routine, shared by the single-cloud kernel and the batched persistent one.
+//
+// A point is handled by a group of G consecutive lanes (G = 1, 2, 4, 8, 16 or
+// 32).  Lane `sub` of the group takes the neighbours j = sub, sub + G, ... .
+// Pass 1 gathers each of them once and accumulates the weight, the weighted
+// centroid offset and the covariance about it with the weighted online update
+// of West (1979): with W' = W + w, delta = d - m: m += delta w / W',
+// C += (W w / W') delta delta^T -- as accurate as a second centred pass,
+// without storing d.  The G partial states are then merged pairwise with the
+// combination rule of Chan, Golub and LeVeque (1979): W = Wa + Wb,
+// m = ma + (mb - ma) Wb / W, C = Ca + Cb + (Wa Wb / W) (mb - ma)(mb - ma)^T,
+// always with the lower lane's state as `a`, so every lane of the group ends
+// with bit-identical moments.  Pass 2 gathers again (now from L1) for the 15
+// monomial moments and 6 right-hand sides of the height fit, summed over the
+// group with xor shuffles (a + b == b + a exactly, so the sums agree too).
+// Every lane of the group then solves the same small systems; the caller
+// writes the result from one of them.
+#pragma once
+
+#include "solve.cuh"
+
+namespace mls {
+
+constexpr float kMixedGapFlag = 1e-3f;     // FP32 eigensolve trusted above this gap ratio
+constexpr float kMixedCondFlag = 1e5f;     // FP32 Cholesky trusted below this condition estimate
+
+// Row: callable, Row(j) = index of the point's neighbour j.  All 32 lanes of
+// the warp must call this together when G > 1 (the merges are warp shuffles,
+// and no lane leaves before the last of them); with G = 1 no lane talks to
+// another.  Returns the status bits; out = the
+// projected point, nf = the normal.
+template <int DEG, int PREC, class Row>
+__device__ __forceinline__ uint8_t project_point(const float4 *__restrict__ xyz4, const Row &row, int k, int sub,
+                                                 int G, float h, float rx, float ry, float rz, float out[3],
+                                                 float nf[3]) {
+    // exp(-|d|^2 / h^2) = exp2(-|d|^2 * log2(e) / h^2)
+    const float neg_scale = -1.4426950408889634f / (h * h);
+
+    // pass 1: weight W, centroid offset m, covariance C (unnormalised)
+    float W = 0.f, mx = 0.f, my = 0.f, mz = 0.f;
+    float C[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll 4
+    for (int j = sub; j < k; j += G) {
+        const float4 p = __ldg(xyz4 + row(j));
+        const float dx = p.x - rx, dy = p.y - ry, dz = p.z - rz;
+        const float w = exp2f(fmaf(dx, dx, fmaf(dy, dy, dz * dz)) * neg_scale);
+        const float Wn = W + w;
+        const float c = Wn > 0.f ? __fdividef(w, Wn) : 0.f;
+        const float ex = dx - mx, ey = dy - my, ez = dz - mz;
+        mx = fmaf(ex, c, mx);
+        my = fmaf(ey, c, my);
+        mz = fmaf(ez, c, mz);
+        const float f = W * c;
+        const float fx = f * ex, fy = f * ey, fz = f * ez;
+        C[0] = fmaf(fx, ex, C[0]);
+        C[1] = fmaf(fx, ey, C[1]);
+        C[2] = fmaf(fx, ez, C[2]);
+        C[3] = fmaf(fy, ey, C[3]);
+        C[4] = fmaf(fy, ez, C[4]);
+        C[5] = fmaf(fz, ez, C[5]);
+        W = Wn;
+    }
+    for (int s = 1; s < G; s <<= 1) {
+        const float Wo = __shfl_xor_sync(0xffffffffu, W, s);
+        const float mox = __shfl_xor_sync(0xffffffffu, mx, s);
+        const float moy = __shfl_xor_sync(0xffffffffu, my, s);
+        const float moz = __shfl_xor_sync(0xffffffffu, mz, s);
+        float Co[6];
+#pragma unroll
+        for (int c = 0; c < 6; ++c) Co[c] = __shfl_xor_sync(0xffffffffu, C[c], s);
+        const bool lower = (sub & s) == 0;
+        const float Wa = lower ? W : Wo, Wb = lower ? Wo : W;
+        const float max_ = lower ? mx : mox, may = lower ? my : moy, maz = lower ? mz : moz;
+        const float dx = (lower ? mox : mx) - max_, dy = (lower ? moy : my) - may, dz = (lower ? moz : mz) - maz;
+        const float Wn = Wa + Wb;
+        const float fb = Wn > 0.f ? __fdividef(Wb, Wn) : 0.f;
+        const float g = Wa * fb;
+        const float gx = g * dx, gy = g * dy, gz = g * dz;
+        float Cs[6];
+#pragma unroll
+        for (int c = 0; c < 6; ++c) Cs[c] = lower ? C[c] + Co[c] : Co[c] + C[c];
+        C[0] = fmaf(gx, dx, Cs[0]);
+        C[1] = fmaf(gx, dy, Cs[1]);
+        C[2] = fmaf(gx, dz, Cs[2]);
+        C[3] = fmaf(gy, dy, Cs[3]);
+        C[4] = fmaf(gy, dz, Cs[4]);
+        C[5] = fmaf(gz, dz, Cs[5]);
+        mx = fmaf(dx, fb, max_);
+        my = fmaf(dy, fb, may);
+        mz = fmaf(dz, fb, maz);
+        W = Wn;
+    }
+    uint8_t st = 0;
+    float e1f[3], e2f[3];
+    {
+        float lam[3];
+        int deg_flag = frame_from<float>(C, nf, e1f, e2f, lam);
+        // the FP32 eigenvector error grows like eps * l2 / (l1 - l0): in the
+        // mixed form, narrow gaps are solved again in FP64 from the same moments
+        if (PREC == MLS_PREC_MIXED && (!(lam[2] > 0.f) || (lam[1] - lam[0]) < kMixedGapFlag * lam[2])) {
+            double Cd[6], nd[3], e1d[3], e2d[3], ld[3];
+#pragma unroll
+            for (int c = 0; c < 6; ++c) Cd[c] = (double)C[c];
+            deg_flag = frame_from<double>(Cd, nd, e1d, e2d, ld);
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                nf[a] = (float)nd[a];
+                e1f[a] = (float)e1d[a];
+                e2f[a] = (float)e2d[a];
+            }
+            st |= MLS_PT_FP64_USED;
+        }
+        st |= (uint8_t)deg_flag;
+    }
+    out[0] = rx;
+    out[1] = ry;
+    out[2] = rz;
+    // a degenerate plane leaves the point where it is; its lanes still take
+    // part in the group's shuffles below, with nothing accumulated
+    const bool degenerate = (st & MLS_PT_PLANE_DEGENERATE) != 0;
+    const float ofs = nf[0] * mx + nf[1] * my + nf[2] * mz;
+    const float ih = 1.f / h;
+    const float a1x = e1f[0] * ih, a1y = e1f[1] * ih, a1z = e1f[2] * ih;
+    const float a2x = e2f[0] * ih, a2y = e2f[1] * ih, a2z = e2f[2] * ih;
+    // pass 2: moments of the height fit
+    float mom[15], rhs[6];
+#pragma unroll
+    for (int c = 0; c < 15; ++c) mom[c] = 0.f;
+#pragma unroll
+    for (int c = 0; c < 6; ++c) rhs[c] = 0.f;
+#pragma unroll 2
+    for (int j = degenerate ? k : sub; j < k; j += G) {
+        const float4 p = __ldg(xyz4 + row(j));
+        const float dx = p.x - rx, dy = p.y - ry, dz = p.z - rz;
+        const float w = exp2f(fmaf(dx, dx, fmaf(dy, dy, dz * dz)) * neg_scale);
+        const float f = fmaf(nf[2], dz, fmaf(nf[1], dy, fmaf(nf[0], dx, -ofs)));
+        const float wf = w * f;
+        mom[0] += w;
+        rhs[0] += wf;
+        if (DEG >= 1) {
+            const float u = fmaf(a1z, dz, fmaf(a1y, dy, a1x * dx));
+            const float vv = fmaf(a2z, dz, fmaf(a2y, dy, a2x * dx));
+            const float wu = w * u, wv = w * vv;
+            mom[1] += wu;
+            mom[2] += wv;
+            rhs[1] = fmaf(wf, u, rhs[1]);
+            rhs[2] = fmaf(wf, vv, rhs[2]);
+            const float wuu = wu * u, wuv = wu * vv, wvv = wv * vv;
+            mom[3] += wuu;
+            mom[4] += wuv;
+            mom[5] += wvv;
+            if (DEG >= 2) {
+                const float uu = u * u, uv = u * vv, v2 = vv * vv;
+                mom[6] = fmaf(wuu, u, mom[6]);
+                mom[7] = fmaf(wuu, vv, mom[7]);
+                mom[8] = fmaf(wvv, u, mom[8]);
+                mom[9] = fmaf(wvv, vv, mom[9]);
+                mom[10] = fmaf(wuu, uu, mom[10]);
+                mom[11] = fmaf(wuu, uv, mom[11]);
+                mom[12] = fmaf(wuu, v2, mom[12]);
+                mom[13] = fmaf(wvv, uv, mom[13]);
+                mom[14] = fmaf(wvv, v2, mom[14]);
+                rhs[3] = fmaf(wf, uu, rhs[3]);
+                rhs[4] = fmaf(wf, uv, rhs[4]);
+                rhs[5] = fmaf(wf, v2, rhs[5]);
+            }
+        }
+    }
+    for (int s = 1; s < G; s <<= 1) {
+#pragma unroll
+        for (int c = 0; c < 15; ++c) mom[c] += __shfl_xor_sync(0xffffffffu, mom[c], s);
+#pragma unroll
+        for (int c = 0; c < 6; ++c) rhs[c] += __shfl_xor_sync(0xffffffffu, rhs[c], s);
+    }
+    if (degenerate) return st;
+    bool singular;
+    float cond;
+    float a0 = solve_a0<float, DEG>(mom, rhs, true, singular, cond);
+    if (PREC == MLS_PREC_MIXED && (singular || !(cond < kMixedCondFlag))) {
+        double condd;
+        a0 = (float)solve_a0<double, DEG>(mom, rhs, false, singular, condd);
+        st |= MLS_PT_FP64_USED;
+    }
+    if (singular) {
+        st |= MLS_PT_POLY_SINGULAR;
+        a0 = 0.f;
+    }
+    const float s = ofs + a0;
+    out[0] = fmaf(s, nf[0], rx);
+    out[1] = fmaf(s, nf[1], ry);
+    out[2] = fmaf(s, nf[2], rz);
+    return st;
+}
+
+}  // namespace mls

@@ -170,30 +170,37 @@ def _area_uniform_superquadric(rng, n, a, e1, e2):
     return np.concatenate(out)[:n]
 
 
+def _batch_cloud(b: int, seed0: int, n_min: int, n_max: int, noise_frac: float, size_scale: float) -> Cloud:
+    rng = np.random.default_rng(seed0 + b)
+    n = int(round(math.exp(rng.uniform(math.log(n_min), math.log(n_max))) * size_scale))
+    n = max(n, 64)
+    k = int(rng.choice([16, 32, 64]))
+    a = rng.uniform(0.2, 1.0, 3)
+    if b % 2 == 0:
+        e1 = e2 = 1.0                               # ellipsoid
+    else:
+        e1, e2 = rng.uniform(0.3, 2.0, 2)
+    pts = _area_uniform_superquadric(rng, n, a, e1, e2)
+    diag = float(np.linalg.norm(pts.max(0) - pts.min(0)))
+    pts = pts + noise_frac * diag * rng.standard_normal(pts.shape)
+    return Cloud(f"quadric{b}", pts.astype(np.float32), min(k, n), 2, "mixed",
+                 {"semi_axes": a, "eps": (e1, e2), "seed": seed0 + b})
+
+
 def batch_clouds(n_clouds: int = 256, seed0: int = 4, n_min: int = 1_000, n_max: int = 500_000,
-                 noise_frac: float = 0.003, size_scale: float = 1.0) -> list[Cloud]:
+                 noise_frac: float = 0.003, size_scale: float = 1.0, workers: int = 1) -> list[Cloud]:
     """Clouds of uneven size: half ellipsoids, half superquadrics (semi-axes
     U(0.2, 1), exponents U(0.3, 2)); size log-uniform in [n_min, n_max] (times
     ``size_scale``); k drawn from {16, 32, 64}; isotropic noise of
     ``noise_frac`` times the cloud's bounding-box diagonal.  Cloud b uses seed
-    ``seed0 + b``."""
-    clouds = []
-    for b in range(n_clouds):
-        rng = np.random.default_rng(seed0 + b)
-        n = int(round(math.exp(rng.uniform(math.log(n_min), math.log(n_max))) * size_scale))
-        n = max(n, 64)
-        k = int(rng.choice([16, 32, 64]))
-        a = rng.uniform(0.2, 1.0, 3)
-        if b % 2 == 0:
-            e1 = e2 = 1.0                               # ellipsoid
-        else:
-            e1, e2 = rng.uniform(0.3, 2.0, 2)
-        pts = _area_uniform_superquadric(rng, n, a, e1, e2)
-        diag = float(np.linalg.norm(pts.max(0) - pts.min(0)))
-        pts = pts + noise_frac * diag * rng.standard_normal(pts.shape)
-        clouds.append(Cloud(f"quadric{b}", pts.astype(np.float32), min(k, n), 2, "mixed",
-                            {"semi_axes": a, "eps": (e1, e2), "seed": seed0 + b}))
-    return clouds
+    ``seed0 + b`` alone, so ``workers`` > 1 (a spawned process pool, safe
+    after CUDA has started) gives the same clouds faster."""
+    args = [(b, seed0, n_min, n_max, noise_frac, size_scale) for b in range(n_clouds)]
+    if workers > 1 and n_clouds > 1:
+        import multiprocessing as mp
+        with mp.get_context("spawn").Pool(min(workers, n_clouds)) as pool:
+            return pool.starmap(_batch_cloud, args, chunksize=1)
+    return [_batch_cloud(*a) for a in args]
 
 
 # Single-cloud workloads by name (the batched one is batch_clouds).

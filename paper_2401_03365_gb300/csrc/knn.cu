@@ -7,7 +7,7 @@
 // are non-negative floats, word order is exactly the order (key, index).  The
 // result is the unique first k words.
 //
-// Work layout.  One warp per query; each warp walks a chunk of 64 consecutive
+// Work layout.  One warp per query; each warp walks runs of consecutive
 // queries in Morton order.  For every query the warp first gets a key bound
 // tau with at least k points at or below it:
 //   - chained: from each of the two previous queries, with k-th key kappa at
@@ -29,6 +29,8 @@
 //
 // The cube's 125 cell ranges (four per lane) are cached in registers: queries
 // that follow each other in Morton order mostly share them.
+#include <algorithm>
+
 #include "grid.cuh"
 
 namespace mls {
@@ -36,9 +38,8 @@ namespace mls {
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
-constexpr int kKnnThreads = 256;
-constexpr int kWarpsPerBlock = kKnnThreads / 32;
-constexpr int kChunk = 128;         // consecutive queries per warp chain
+constexpr int kChunk = 128;         // largest run of consecutive queries per warp chain
+constexpr int kMinChunk = 8;        // smallest run, near the end of the queue
 constexpr int kCap = 128;           // kept-word capacity for the counting sort
 constexpr int kSlots = 4;           // cube cells per lane: 4 x 32 >= 125
 constexpr int kMaxSegWords = 64;    // segment-start bitmap: 2048 points per round
@@ -505,9 +506,9 @@ __device__ __noinline__ float solve_query(const GridView &g, WarpBuf &wb, Cube &
             load_cube(g, lev, c0, cb, lane);
             if (cb.M >= k || lev >= g.top_level) break;
         }
-        // a sparse neighbourhood (two levels above the base) is left to the
-        // pass that shares such queries among all warps
-        if (may_defer && lev > g.base_level + 1) return NAN;
+        // a sparse neighbourhood (a cube above the base level) is left to
+        // the pass that shares such queries among all warps
+        if (may_defer && lev > g.base_level) return NAN;
         const float S = g.side[lev];
         // count-weighted histogram of cell distances over [0, 3S)
         __syncwarp();
@@ -568,19 +569,21 @@ __device__ __noinline__ float solve_query(const GridView &g, WarpBuf &wb, Cube &
 
 // ---- chains: one query per warp -----------------------------------------
 //
-// A warp takes chunks of 128 consecutive queries from a global counter.  The
-// bound for a query comes from the query before it: the k-th smallest key,
+// A warp takes runs of consecutive queries from a global counter: 128 at a
+// time while many remain, fewer (down to 8) as the queue drains, so that the
+// warps finish together.  The bound for a query comes from the query before
+// it: the k-th smallest key,
 // seen from the new query, of the points that query kept (its k neighbours
 // among them), and the triangle bound from the query before that.  A fresh
 // bound is computed when there is no earlier query, or the bound is more than
 // 9 times the previous query's own k-th key or reaches past four base cells.
-// Queries in sparse regions (their fresh bound needs a level two above the
-// base) are appended to a list and solved afterwards by k_knn_sparse, where
+// Queries in sparse regions (their fresh bound needs a level above the base)
+// are appended to a list and solved afterwards by k_knn_sparse, where
 // all warps share them: they cost far more than the rest and would otherwise
 // leave a few warps running long after the others.
 //
-// work[0]: next chunk; work[1]: deferred count; work[2]: next deferred;
-// work[8 ...]: sorted positions of the deferred queries.
+// work[1]: deferred count; work[2]: next deferred; work[4..5]: next query
+// (64-bit); work[8 ...]: sorted positions of the deferred queries.
 
 constexpr int kChainThreads = 256;
 constexpr int kChainWarps = kChainThreads / 32;
@@ -591,24 +594,40 @@ __device__ __forceinline__ int warp_take(int *counter, int lane) {
     return __shfl_sync(kFull, v, 0);
 }
 
+// Six blocks per SM: the kernel is bound by instruction issue and latency,
+// and more resident warps hide more of the latter.
+constexpr int kChainBlocksPerSm = 6;
+
 template <int KPL>
-__global__ void __launch_bounds__(kChainThreads) k_knn_chain(GridView g, int k, int *__restrict__ work,
+__global__ void __launch_bounds__(kChainThreads, kChainBlocksPerSm) k_knn_chain(GridView g, int k, int *__restrict__ work,
                                                             int32_t *__restrict__ out_idx,
                                                             float *__restrict__ out_key) {
     __shared__ WarpBuf bufs[kChainWarps];
     const int lane = threadIdx.x & 31;
     WarpBuf &wb = bufs[threadIdx.x >> 5];
-    const int64_t n_chunks = (g.n + kChunk - 1) / kChunk;
+    const int64_t n_warps = (int64_t)gridDim.x * kChainWarps;
+    unsigned long long *next_query = reinterpret_cast<unsigned long long *>(&work[4]);
     const float big = 16.0f * g.side[g.base_level] * g.side[g.base_level];
     Cube cb;
-    for (int64_t chunk = warp_take(&work[0], lane); chunk < n_chunks; chunk = warp_take(&work[0], lane)) {
+    for (;;) {
+        // run length from a racy read of the queue: any length is correct,
+        // since every run is reserved by its own atomic add
+        long long first = 0, len = 0;
+        if (lane == 0) {
+            const long long left = g.n - (long long)*(volatile unsigned long long *)next_query;
+            len = min((long long)kChunk, max((long long)kMinChunk, left / (2 * n_warps)));
+            first = (long long)atomicAdd(next_query, (unsigned long long)len);
+        }
+        first = __shfl_sync(kFull, first, 0);
+        len = __shfl_sync(kFull, len, 0);
+        if (first >= g.n) break;
         // the previous query (its kept points in wb, k-th key k1, position
         // p1) and the one before it (position p2, k-th key k2)
         int n_prev = 0;
         float4 p1 = make_float4(0.f, 0.f, 0.f, 0.f), p2 = p1;
         float k1 = 0.f, k2 = 0.f;
-        const int64_t end = min((int64_t)g.n, (chunk + 1) * kChunk);
-        for (int64_t sp = chunk * kChunk; sp < end; ++sp) {
+        const int64_t end = min((int64_t)g.n, (int64_t)(first + len));
+        for (int64_t sp = first; sp < end; ++sp) {
             const float4 q = __ldg(g.pts + sp);
             const uint64_t key0 = __ldg(g.keys + sp);
             const uint32_t c0[3] = {compact3(key0), compact3(key0 >> 1), compact3(key0 >> 2)};
@@ -657,21 +676,25 @@ __global__ void __launch_bounds__(kChainThreads) k_knn_sparse(GridView g, int k,
 int launch_knn(const mls_grid *grid, int k, int32_t *idx, float *key, cudaStream_t st) {
     const int64_t n = grid->n;
     int dev = 0, sms = 152;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int64_t chunks = (n + kChunk - 1) / kChunk;
-    int64_t blocks = (chunks + kChainWarps - 1) / kChainWarps;
-    const int64_t cap = (int64_t)sms * 4;      // one resident wave; chunks are taken dynamically
-    if (blocks > cap) blocks = cap;
-    const int sparse_blocks = sms * 4;
+    MLS_CUDA_TRY(cudaGetDevice(&dev));
+    MLS_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    auto chain = k <= 32 ? k_knn_chain<1> : k_knn_chain<2>;
+    auto sparse = k <= 32 ? k_knn_sparse<1> : k_knn_sparse<2>;
+    // all shared memory to the carveout, so that every block the registers
+    // allow is resident; one resident wave of blocks, queries taken dynamically
+    MLS_CUDA_TRY(cudaFuncSetAttribute(chain, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                      cudaSharedmemCarveoutMaxShared));
+    MLS_CUDA_TRY(cudaFuncSetAttribute(sparse, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                      cudaSharedmemCarveoutMaxShared));
+    int per_sm = 1;
+    MLS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, chain, kChainThreads, 0));
+    per_sm = std::max(per_sm, 1);
+    const int64_t runs = (n + kMinChunk - 1) / kMinChunk;
+    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)sms * per_sm,
+                                                                    (runs + kChainWarps - 1) / kChainWarps));
     MLS_CUDA_TRY(cudaMemsetAsync(grid->work, 0, 8 * sizeof(int), st));
-    if (k <= 32) {
-        k_knn_chain<1><<<(int)blocks, kChainThreads, 0, st>>>(grid->view, k, grid->work, idx, key);
-        k_knn_sparse<1><<<sparse_blocks, kChainThreads, 0, st>>>(grid->view, k, grid->work, idx, key);
-    } else {
-        k_knn_chain<2><<<(int)blocks, kChainThreads, 0, st>>>(grid->view, k, grid->work, idx, key);
-        k_knn_sparse<2><<<sparse_blocks, kChainThreads, 0, st>>>(grid->view, k, grid->work, idx, key);
-    }
+    chain<<<blocks, kChainThreads, 0, st>>>(grid->view, k, grid->work, idx, key);
+    sparse<<<sms * per_sm, kChainThreads, 0, st>>>(grid->view, k, grid->work, idx, key);
     count_launches(2);
     MLS_CUDA_TRY(cudaGetLastError());
     return MLS_OK;

@@ -190,7 +190,7 @@ int mls_project_noalloc(const float *d_xyz, int64_t n, const int32_t *d_idx, int
  *   d_grad_xyz         device, n x 3 floats, overwritten: dL/dx
  *   d_grad_h           device, 1 float, overwritten: dL/dh
  * Deterministic: edge contributions are summed in a fixed order.  Uses
- * stream-ordered scratch (cudaMallocAsync) of about n * (28 + 16 k) bytes.
+ * stream-ordered scratch (cudaMallocAsync) of about n * (48 + 28 k) bytes.
  */
 int mls_project_backward(const float *d_xyz, int64_t n, const int32_t *d_idx, int k, float h, int degree,
                          int precision, const int32_t *d_order, const float *d_grad_out_xyz,

@@ -16,6 +16,17 @@
 // reverse adjacency (edges bucketed by target point, each bucket ordered by
 // edge number) then sums them in a fixed order: results do not depend on
 // scheduling.
+//
+// Everything is indexed by sorted (Morton) position when a processing order
+// is given: point slot s of the order sends edge (s, j) to the sorted
+// position t of its neighbour j.  Neighbours are close in that order, so the
+// per-target counts and the bucket fill touch a narrow window of memory at a
+// time, and the gather reads the edges of nearby sources.  Edge (s, j) is
+// stored at id = (s / 32) 32 k + 32 j + s % 32: a warp of 32 consecutive slots
+// writes 32 consecutive float4 records per neighbour rank.  Each bucket is
+// summed in the order of the edges' numbers in the original indexing,
+// i k + j for neighbour j of point i, so the gradient does not depend on the
+// processing order either.
 #include <algorithm>
 #include <climits>
 
@@ -67,8 +78,9 @@ __device__ __forceinline__ void basis(float u, float v, float phi[6]) {
 template <int DEG, int PREC>
 __global__ void __launch_bounds__(kBwdThreads) k_backward_point(
     const float4 *__restrict__ xyz4, int64_t n, const int32_t *__restrict__ idx, int k, float h,
-    const int32_t *__restrict__ order, const float *__restrict__ gout_xyz, const float *__restrict__ gout_n,
-    float *__restrict__ edge_grad, float *__restrict__ self_grad, double *__restrict__ h_part) {
+    const int32_t *__restrict__ order, const int32_t *__restrict__ pos, const float *__restrict__ gout_xyz,
+    const float *__restrict__ gout_n, float4 *__restrict__ edge4, uint32_t *__restrict__ tgt,
+    int32_t *__restrict__ cnt, float4 *__restrict__ self4, double *__restrict__ h_part) {
     constexpr int M = Basis<DEG>::M;
     extern __shared__ int32_t rows[];
     __shared__ double hred[kBwdThreads / 32];
@@ -131,11 +143,19 @@ __global__ void __launch_bounds__(kBwdThreads) k_backward_point(
         }
         const float gp[3] = {gout_xyz[3 * i], gout_xyz[3 * i + 1], gout_xyz[3 * i + 2]};
         float rbar[3] = {gp[0], gp[1], gp[2]};
+        // edge (slot, j): its record id, and the target's sorted position
+        const int64_t id0 = (slot >> 5) * 32 * (int64_t)k + lane;
+        auto emit = [&](int j, float gx, float gy, float gz) {
+            const int32_t p = my_rows[j * 32 + lane];
+            const int32_t t = pos ? __ldg(pos + p) : p;
+            const int64_t id = id0 + 32 * (int64_t)j;
+            edge4[id] = make_float4(gx, gy, gz, 0.f);
+            tgt[id] = (uint32_t)t;
+            atomicAdd(cnt + t, 1);
+        };
         if (flag & MLS_PT_PLANE_DEGENERATE) {
             // p' = r and the normal is taken as constant: nothing reaches the neighbours
-            for (int j = 0; j < k; ++j)
-#pragma unroll
-                for (int a = 0; a < 3; ++a) edge_grad[(i * k + j) * 3 + a] = 0.f;
+            for (int j = 0; j < k; ++j) emit(j, 0.f, 0.f, 0.f);
         } else {
             const float gn[3] = {gout_n ? gout_n[3 * i] : 0.f, gout_n ? gout_n[3 * i + 1] : 0.f,
                                  gout_n ? gout_n[3 * i + 2] : 0.f};
@@ -315,13 +335,12 @@ __global__ void __launch_bounds__(kBwdThreads) k_backward_point(
                     // weight w = exp(-|d|^2 / h^2)
                     dbar[c] -= 2.f * wb * d[c] / h2;
                     rbar[c] -= dbar[c];
-                    edge_grad[(i * k + j) * 3 + c] = dbar[c];
                 }
+                emit(j, dbar[0], dbar[1], dbar[2]);
                 hbar += 2.f * wb * dd / (h2 * h);
             }
         }
-#pragma unroll
-        for (int c = 0; c < 3; ++c) self_grad[3 * i + c] = rbar[c];
+        self4[slot] = make_float4(rbar[0], rbar[1], rbar[2], 0.f);
     }
     // dL/dh of the block, reduced in a fixed order
     double hb = (double)hbar;
@@ -336,43 +355,54 @@ __global__ void __launch_bounds__(kBwdThreads) k_backward_point(
     }
 }
 
-__global__ void k_edge_count(const int32_t *__restrict__ idx, int64_t ne, int32_t *__restrict__ cnt) {
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < ne; e += (int64_t)gridDim.x * blockDim.x)
-        atomicAdd(&cnt[idx[e]], 1);
+// Inverse of the processing order: pos[order[s]] = s.
+__global__ void k_inverse(const int32_t *__restrict__ order, int64_t n, int32_t *__restrict__ pos) {
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n; s += (int64_t)gridDim.x * blockDim.x)
+        pos[order[s]] = (int32_t)s;
 }
 
-__global__ void k_edge_fill(const int32_t *__restrict__ idx, int64_t ne, const int32_t *__restrict__ off,
-                            int32_t *__restrict__ fill, int32_t *__restrict__ ent) {
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < ne; e += (int64_t)gridDim.x * blockDim.x) {
-        const int32_t p = idx[e];
-        ent[off[p] + atomicAdd(&fill[p], 1)] = (int32_t)e;
+// Bucket fill: per target, the words (i k + j) << 32 | id of the edges that
+// point at it (in arbitrary order; the gather sorts each bucket).
+__global__ void k_edge_fill(const uint32_t *__restrict__ tgt, const int32_t *__restrict__ order, int64_t n, int k,
+                            const int32_t *__restrict__ off, int32_t *__restrict__ fill,
+                            unsigned long long *__restrict__ ent) {
+    const int64_t ne = ((n + 31) >> 5) * 32 * (int64_t)k;
+    for (int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; id < ne;
+         id += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t slot = (id / (32 * (int64_t)k)) * 32 + (id & 31);
+        if (slot >= n) continue;
+        const int64_t i = order ? (int64_t)order[slot] : slot;
+        const int64_t e = i * k + ((id >> 5) % k);
+        const uint32_t t = tgt[id];
+        ent[off[t] + atomicAdd(&fill[t], 1)] = ((unsigned long long)e << 32) | (unsigned long long)id;
     }
 }
 
-// Sum of the edges that point at p plus p's own term, one warp per target:
-// the bucket's edge numbers are sorted (bitonic network over 64 slots, two per
+// Sum of the edges that point at t plus t's own term, one warp per target:
+// the bucket's words are sorted (bitonic network over 64 slots, two per
 // lane) and summed by a fixed tree over the sorted order, so the result does
 // not depend on the order in which the edges were bucketed.  Buckets above 64
 // entries (rare hubs) are sorted in place and summed by one lane.
-__device__ __forceinline__ void cswap(int &a, int &b, bool up) {
+__device__ __forceinline__ void cswap(unsigned long long &a, unsigned long long &b, bool up) {
     if ((a > b) == up) {
-        const int t = a;
+        const unsigned long long t = a;
         a = b;
         b = t;
     }
 }
 
-__global__ void k_gather(int64_t n, const int32_t *__restrict__ off, int32_t *__restrict__ ent,
-                         const float *__restrict__ edge_grad, const float *__restrict__ self_grad,
-                         float *__restrict__ grad) {
+__global__ void k_gather(int64_t n, const int32_t *__restrict__ order, const int32_t *__restrict__ off,
+                         unsigned long long *__restrict__ ent, const float4 *__restrict__ edge4,
+                         const float4 *__restrict__ self4, float *__restrict__ grad) {
+    constexpr unsigned long long kNone = ~0ull;
     const int lane = threadIdx.x & 31;
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    for (int64_t p = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; p < n; p += warps) {
-        const int32_t b = off[p], m = off[p + 1] - b;
+    for (int64_t t = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; t < n; t += warps) {
+        const int32_t b = off[t], m = off[t + 1] - b;
         float g[3] = {0.f, 0.f, 0.f};
         if (m <= 64) {
-            int v0 = 2 * lane < m ? ent[b + 2 * lane] : INT_MAX;
-            int v1 = 2 * lane + 1 < m ? ent[b + 2 * lane + 1] : INT_MAX;
+            unsigned long long v0 = 2 * lane < m ? ent[b + 2 * lane] : kNone;
+            unsigned long long v1 = 2 * lane + 1 < m ? ent[b + 2 * lane + 1] : kNone;
             // element e = 2 lane + r
 #pragma unroll
             for (int kk = 2; kk <= 64; kk <<= 1) {
@@ -383,40 +413,50 @@ __global__ void k_gather(int64_t n, const int32_t *__restrict__ off, int32_t *__
                         cswap(v0, v1, up);
                     } else {
                         const int pl = j >> 1;
-                        const int o0 = __shfl_xor_sync(0xffffffffu, v0, pl);
-                        const int o1 = __shfl_xor_sync(0xffffffffu, v1, pl);
+                        const unsigned long long o0 = __shfl_xor_sync(0xffffffffu, v0, pl);
+                        const unsigned long long o1 = __shfl_xor_sync(0xffffffffu, v1, pl);
                         const bool lower = (lane & pl) == 0;
                         v0 = (lower == up) ? min(v0, o0) : max(v0, o0);
                         v1 = (lower == up) ? min(v1, o1) : max(v1, o1);
                     }
                 }
             }
+            const float4 a0 = v0 != kNone ? edge4[(uint32_t)v0] : make_float4(0.f, 0.f, 0.f, 0.f);
+            const float4 a1 = v1 != kNone ? edge4[(uint32_t)v1] : make_float4(0.f, 0.f, 0.f, 0.f);
+            float tx = a0.x + a1.x, ty = a0.y + a1.y, tz = a0.z + a1.z;
 #pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                const float a0 = v0 != INT_MAX ? edge_grad[(int64_t)v0 * 3 + c] : 0.f;
-                const float a1 = v1 != INT_MAX ? edge_grad[(int64_t)v1 * 3 + c] : 0.f;
-                float t = a0 + a1;
-#pragma unroll
-                for (int o = 1; o < 32; o <<= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-                g[c] = t;
+            for (int o = 1; o < 32; o <<= 1) {
+                tx += __shfl_xor_sync(0xffffffffu, tx, o);
+                ty += __shfl_xor_sync(0xffffffffu, ty, o);
+                tz += __shfl_xor_sync(0xffffffffu, tz, o);
             }
+            g[0] = tx;
+            g[1] = ty;
+            g[2] = tz;
         } else if (lane == 0) {
-            for (int32_t t = b + 1; t < b + m; ++t) {
-                const int32_t v = ent[t];
-                int32_t u = t;
+            for (int32_t q = b + 1; q < b + m; ++q) {
+                const unsigned long long v = ent[q];
+                int32_t u = q;
                 while (u > b && ent[u - 1] > v) {
                     ent[u] = ent[u - 1];
                     --u;
                 }
                 ent[u] = v;
             }
-            for (int32_t t = b; t < b + m; ++t)
-#pragma unroll
-                for (int c = 0; c < 3; ++c) g[c] += edge_grad[(int64_t)ent[t] * 3 + c];
+            for (int32_t q = b; q < b + m; ++q) {
+                const float4 e = edge4[(uint32_t)ent[q]];
+                g[0] += e.x;
+                g[1] += e.y;
+                g[2] += e.z;
+            }
         }
-        if (lane == 0)
-#pragma unroll
-            for (int c = 0; c < 3; ++c) grad[3 * p + c] = self_grad[3 * p + c] + g[c];
+        if (lane == 0) {
+            const float4 sg = self4[t];
+            const int64_t o = order ? (int64_t)order[t] : t;
+            grad[3 * o] = sg.x + g[0];
+            grad[3 * o + 1] = sg.y + g[1];
+            grad[3 * o + 2] = sg.z + g[2];
+        }
     }
 }
 
@@ -437,18 +477,12 @@ __global__ void __launch_bounds__(1024) k_sum_h(const double *__restrict__ part,
 
 template <int DEG>
 void launch_point(const float4 *xyz4, int64_t n, const int32_t *idx, int k, float h, int precision,
-                  const int32_t *order, const float *gp, const float *gn, float *edge, float *self, double *hp,
-                  int blocks, cudaStream_t st) {
+                  const int32_t *order, const int32_t *pos, const float *gp, const float *gn, float4 *edge4,
+                  uint32_t *tgt, int32_t *cnt, float4 *self4, double *hp, int blocks, cudaStream_t st) {
     const size_t smem = (size_t)k * 32 * sizeof(int32_t) * (kBwdThreads / 32);
-    if (precision == MLS_PREC_FP32) {
-        auto kern = k_backward_point<DEG, MLS_PREC_FP32>;
-        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        kern<<<blocks, kBwdThreads, smem, st>>>(xyz4, n, idx, k, h, order, gp, gn, edge, self, hp);
-    } else {
-        auto kern = k_backward_point<DEG, MLS_PREC_MIXED>;
-        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        kern<<<blocks, kBwdThreads, smem, st>>>(xyz4, n, idx, k, h, order, gp, gn, edge, self, hp);
-    }
+    auto kern = precision == MLS_PREC_FP32 ? k_backward_point<DEG, MLS_PREC_FP32> : k_backward_point<DEG, MLS_PREC_MIXED>;
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    kern<<<blocks, kBwdThreads, smem, st>>>(xyz4, n, idx, k, h, order, pos, gp, gn, edge4, tgt, cnt, self4, hp);
 }
 
 }  // namespace
@@ -456,43 +490,53 @@ void launch_point(const float4 *xyz4, int64_t n, const int32_t *idx, int k, floa
 int launch_backward(const float *xyz, int64_t n, const int32_t *idx, int k, float h, int degree, int precision,
                     const int32_t *order, const float *gp, const float *gn, float *grad_xyz, float *grad_h,
                     cudaStream_t st) {
-    const int64_t ne = n * k;
+    const int64_t ne = ((n + 31) >> 5) * 32 * (int64_t)k;     // edge records, whole warp tiles
     const int blocks = (int)((n + kBwdThreads - 1) / kBwdThreads);
-    float4 *xyz4 = nullptr;
-    float *edge = nullptr, *self = nullptr;
+    float4 *xyz4 = nullptr, *edge4 = nullptr, *self4 = nullptr;
     double *hp = nullptr;
-    int32_t *cnt = nullptr, *off = nullptr, *ent = nullptr;
+    int32_t *cnt = nullptr, *off = nullptr, *pos = nullptr;
+    uint32_t *tgt = nullptr;
+    unsigned long long *ent = nullptr;
     MLS_CUDA_TRY(cudaMallocAsync((void **)&xyz4, (size_t)n * sizeof(float4), st));
-    MLS_CUDA_TRY(cudaMallocAsync((void **)&edge, (size_t)ne * 3 * sizeof(float), st));
-    MLS_CUDA_TRY(cudaMallocAsync((void **)&self, (size_t)n * 3 * sizeof(float), st));
+    MLS_CUDA_TRY(cudaMallocAsync((void **)&edge4, (size_t)ne * sizeof(float4), st));
+    MLS_CUDA_TRY(cudaMallocAsync((void **)&self4, (size_t)n * sizeof(float4), st));
     MLS_CUDA_TRY(cudaMallocAsync((void **)&hp, (size_t)blocks * sizeof(double), st));
     MLS_CUDA_TRY(cudaMallocAsync((void **)&cnt, (size_t)(2 * n + 2) * sizeof(int32_t), st));
     MLS_CUDA_TRY(cudaMallocAsync((void **)&off, (size_t)(n + 1) * sizeof(int32_t), st));
-    MLS_CUDA_TRY(cudaMallocAsync((void **)&ent, (size_t)ne * sizeof(int32_t), st));
+    MLS_CUDA_TRY(cudaMallocAsync((void **)&tgt, (size_t)ne * sizeof(uint32_t), st));
+    MLS_CUDA_TRY(cudaMallocAsync((void **)&ent, (size_t)n * k * sizeof(unsigned long long), st));
+    if (order) MLS_CUDA_TRY(cudaMallocAsync((void **)&pos, (size_t)n * sizeof(int32_t), st));
     int32_t *fill = cnt + n + 1;
-    const int gs = (int)std::min<int64_t>((ne + 255) / 256, 152 * 16);
-    k_pack4<<<(int)std::min<int64_t>((n + 255) / 256, 152 * 16), 256, 0, st>>>(xyz, n, xyz4);
-    switch (degree) {
-        case 0: launch_point<0>(xyz4, n, idx, k, h, precision, order, gp, gn, edge, self, hp, blocks, st); break;
-        case 1: launch_point<1>(xyz4, n, idx, k, h, precision, order, gp, gn, edge, self, hp, blocks, st); break;
-        default: launch_point<2>(xyz4, n, idx, k, h, precision, order, gp, gn, edge, self, hp, blocks, st); break;
-    }
+    const int grid_n = (int)std::min<int64_t>((n + 255) / 256, 152 * 16);
     MLS_CUDA_TRY(cudaMemsetAsync(cnt, 0, (size_t)(2 * n + 2) * sizeof(int32_t), st));
-    k_edge_count<<<gs, 256, 0, st>>>(idx, ne, cnt);
+    k_pack4<<<grid_n, 256, 0, st>>>(xyz, n, xyz4);
+    int launches = 1;
+    if (order) {
+        k_inverse<<<grid_n, 256, 0, st>>>(order, n, pos);
+        ++launches;
+    }
+    switch (degree) {
+        case 0: launch_point<0>(xyz4, n, idx, k, h, precision, order, pos, gp, gn, edge4, tgt, cnt, self4, hp, blocks, st); break;
+        case 1: launch_point<1>(xyz4, n, idx, k, h, precision, order, pos, gp, gn, edge4, tgt, cnt, self4, hp, blocks, st); break;
+        default: launch_point<2>(xyz4, n, idx, k, h, precision, order, pos, gp, gn, edge4, tgt, cnt, self4, hp, blocks, st); break;
+    }
     int rc = device_exclusive_scan(cnt, off, n + 1, st);
     if (rc != MLS_OK) return rc;
-    k_edge_fill<<<gs, 256, 0, st>>>(idx, ne, off, fill, ent);
-    k_gather<<<(int)std::min<int64_t>((n * 32 + 255) / 256, 152 * 32), 256, 0, st>>>(n, off, ent, edge, self, grad_xyz);
+    k_edge_fill<<<(int)std::min<int64_t>((ne + 255) / 256, 152 * 32), 256, 0, st>>>(tgt, order, n, k, off, fill, ent);
+    k_gather<<<(int)std::min<int64_t>((n * 32 + 255) / 256, 152 * 32), 256, 0, st>>>(n, order, off, ent, edge4, self4,
+                                                                                      grad_xyz);
     k_sum_h<<<1, 1024, 0, st>>>(hp, blocks, grad_h);
-    count_launches(6);
+    count_launches(launches + 4);   // + point, fill, gather, sum_h (the scan counts its own)
     MLS_CUDA_TRY(cudaGetLastError());
     cudaFreeAsync(xyz4, st);
-    cudaFreeAsync(edge, st);
-    cudaFreeAsync(self, st);
+    cudaFreeAsync(edge4, st);
+    cudaFreeAsync(self4, st);
     cudaFreeAsync(hp, st);
     cudaFreeAsync(cnt, st);
     cudaFreeAsync(off, st);
+    cudaFreeAsync(tgt, st);
     cudaFreeAsync(ent, st);
+    if (pos) cudaFreeAsync(pos, st);
     return MLS_OK;
 }
 

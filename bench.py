@@ -88,7 +88,9 @@ def load_peaks():
 
 
 class ClockSampler:
-    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+    """nvidia-smi samples of SM clock and throttle reasons.  Started before the
+    warm-up (the tool's own start-up then falls outside the timed region);
+    the summary keeps the samples read inside the timed window."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -97,7 +99,8 @@ class ClockSampler:
     def __init__(self, gpu_index):
         self.gpu = gpu_index
         self.proc = None
-        self.lines = []
+        self.lines = []             # (host time, csv line)
+        self.window = None
 
     def __enter__(self):
         try:
@@ -106,13 +109,19 @@ class ClockSampler:
                  "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
+            t0 = time.time()
+            while not self.lines and time.time() - t0 < 10.0 and self.proc.poll() is None:
+                time.sleep(0.02)
         except (OSError, FileNotFoundError):
             self.proc = None
         return self
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.time(), line.strip()))
+
+    def mark(self, t_begin, t_end):
+        self.window = (t_begin, t_end)
 
     def __exit__(self, *exc):
         if self.proc is not None:
@@ -123,9 +132,15 @@ class ClockSampler:
                 self.proc.kill()
 
     def summary(self):
+        lines = self.lines
+        if self.window is not None:
+            a, b = self.window
+            inside = [x for x in lines if a <= x[0] <= b]
+            # a timed region shorter than the sampling period: the samples next to it
+            lines = inside or [x for x in lines if a - 0.25 <= x[0] <= b + 0.25]
         sm, mx, reasons = [], None, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in self.lines:
+        for _, line in lines:
             parts = [p.strip() for p in line.split(",")]
             if len(parts) < 9:
                 continue
@@ -196,21 +211,23 @@ def run_ours(args):
                                   out_grad_h=grad_h)
         if ev: ev[4].record(stream)
 
-    for _ in range(args.warmup):
-        step(x)
-    torch.cuda.synchronize()
     events = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(args.steps)]
-    launches0 = capi.mls_kernel_launches()
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
     with ClockSampler(local) as clocks:
+        for _ in range(args.warmup):
+            step(x)
+        torch.cuda.synchronize()
+        launches0 = capi.mls_kernel_launches()
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        t_begin = time.time()
         t0 = time.perf_counter()
         for s in range(args.steps):
             flush.zero_()
             step(x, events[s])
         torch.cuda.synchronize()
         wall = time.perf_counter() - t0
+        clocks.mark(t_begin, time.time())
     if world > 1:
         dist.barrier()
     launches = capi.mls_kernel_launches() - launches0

@@ -155,7 +155,7 @@ int mls_project(const float *d_xyz, int64_t n, const int32_t *d_idx, int k, floa
  * device memory.  The paper has no counterpart: this is a deployment
  * variant.  Some callers cannot let a library allocate: hosts that hand out
  * all device memory from their own fixed pool or budget (inference servers,
- * embedded pipelines) and would not see a cudaMallocAsync, or loops that must
+ * embedded pipelines) and would not see the library's own pool, or loops that must
  * not risk an allocation failing half way.  This entry point takes its
  * scratch (a float4 copy of the points) from a fixed device array of
  * MLS_NOALLOC_MAX_POINTS entries (4 MiB), which every GPU that loads the
@@ -190,7 +190,8 @@ int mls_project_noalloc(const float *d_xyz, int64_t n, const int32_t *d_idx, int
  *   d_grad_xyz         device, n x 3 floats, overwritten: dL/dx
  *   d_grad_h           device, 1 float, overwritten: dL/dh
  * Deterministic: edge contributions are summed in a fixed order.  Uses
- * stream-ordered scratch (cudaMallocAsync) of about n * (48 + 28 k) bytes.
+ * stream-ordered scratch (the library's pool, see mls_release_scratch) of about
+ * n * (48 + 28 k) bytes.
  */
 int mls_project_backward(const float *d_xyz, int64_t n, const int32_t *d_idx, int k, float h, int degree,
                          int precision, const int32_t *d_order, const float *d_grad_out_xyz,
@@ -283,6 +284,14 @@ int mls_batch_autotune(mls_batch *b, const float *d_xyz, const int32_t *d_idx, c
  * rounds) into shapes (3 int32 each, HOST) and the best time in ms into ms
  * (HOST); either may be NULL.  Returns the number of entries. */
 int mls_batch_tune_results(const mls_batch *b, int capacity, int32_t *shapes, float *ms);
+
+/* Scratch memory.  mls_project, mls_project_backward and the helpers take
+ * their per-call buffers, stream-ordered, from a memory pool of the library's
+ * own (one per device) that keeps freed memory mapped for the next call
+ * instead of returning it to the system at every synchronisation.  This call
+ * synchronises every device that has such a pool and returns its unused
+ * memory to the system. */
+int mls_release_scratch(void);
 
 /* Number of CUDA kernels this library has launched in the process so far
  * (all threads).  Host-side count, for accounting in benchmarks. */

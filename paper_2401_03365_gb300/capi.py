@@ -17,7 +17,7 @@ from .build import library_path
 
 __all__ = [
     "MLSError", "Grid", "lib", "mls_build_grid", "mls_grid_destroy", "mls_grid_size", "mls_grid_order",
-    "mls_knn", "mls_project", "mls_project_backward", "mls_mean_knn_dist", "mls_status_str", "mls_last_error", "mls_kernel_launches",
+    "mls_knn", "mls_project", "mls_project_backward", "mls_mean_knn_dist", "mls_status_str", "mls_last_error", "mls_kernel_launches", "mls_release_scratch",
     "Batch", "mls_batch_create", "mls_batch_destroy", "mls_batch_set_shape", "mls_batch_get_shape",
     "mls_project_batched", "mls_batch_capture", "mls_batch_replay", "mls_batch_autotune", "mls_batch_tune_results",
     "PRECISION", "MLS_MAX_K", "MLS_PT_OK", "MLS_PT_PLANE_DEGENERATE", "MLS_PT_POLY_SINGULAR",
@@ -56,6 +56,7 @@ _SIGNATURES = [
     ("mls_batch_replay", _int, [_vp, _vp]),
     ("mls_batch_autotune", _int, [_vp, _vp, _vp, _vp, _vp, _int, _int, _vp, _vp, _vp, _int, _vp]),
     ("mls_batch_tune_results", _int, [_vp, _int, _vp, _vp]),
+    ("mls_release_scratch", _int, []),
     ("mls_kernel_launches", _i64, []),
     ("mls_last_error", ctypes.c_char_p, []),
     ("mls_status_str", ctypes.c_char_p, [_int]),
@@ -122,6 +123,11 @@ def mls_status_str(code: int) -> str:
 
 def mls_last_error() -> str:
     return lib().mls_last_error().decode()
+
+
+def mls_release_scratch() -> None:
+    """Returns the library's unused scratch memory to the system (synchronises)."""
+    _check("mls_release_scratch", lib().mls_release_scratch())
 
 
 def mls_kernel_launches() -> int:

@@ -194,7 +194,7 @@ int mls_mean_knn_dist(const float *d_xyz, int64_t n, const int32_t *d_idx, int k
     if (n < 1 || k < 1 || k > MLS_MAX_K) return set_error(MLS_ERR_INVALID_ARG, "mls_mean_knn_dist: n or k");
     cudaStream_t st = (cudaStream_t)stream;
     double *acc = nullptr;
-    MLS_CUDA_TRY(cudaMallocAsync(&acc, 2 * sizeof(double), st));
+    MLS_CUDA_TRY(mls::scratch_alloc((void **)&acc, 2 * sizeof(double), st));
     MLS_CUDA_TRY(cudaMemsetAsync(acc, 0, 2 * sizeof(double), st));
     mls::k_mean_dist<<<152 * 8, 256, 0, st>>>(d_xyz, n, d_idx, k, acc);
     mls::k_mean_finish<<<1, 1, 0, st>>>(acc, d_out);

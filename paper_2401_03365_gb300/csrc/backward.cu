@@ -497,15 +497,15 @@ int launch_backward(const float *xyz, int64_t n, const int32_t *idx, int k, floa
     int32_t *cnt = nullptr, *off = nullptr, *pos = nullptr;
     uint32_t *tgt = nullptr;
     unsigned long long *ent = nullptr;
-    MLS_CUDA_TRY(cudaMallocAsync((void **)&xyz4, (size_t)n * sizeof(float4), st));
-    MLS_CUDA_TRY(cudaMallocAsync((void **)&edge4, (size_t)ne * sizeof(float4), st));
-    MLS_CUDA_TRY(cudaMallocAsync((void **)&self4, (size_t)n * sizeof(float4), st));
-    MLS_CUDA_TRY(cudaMallocAsync((void **)&hp, (size_t)blocks * sizeof(double), st));
-    MLS_CUDA_TRY(cudaMallocAsync((void **)&cnt, (size_t)(2 * n + 2) * sizeof(int32_t), st));
-    MLS_CUDA_TRY(cudaMallocAsync((void **)&off, (size_t)(n + 1) * sizeof(int32_t), st));
-    MLS_CUDA_TRY(cudaMallocAsync((void **)&tgt, (size_t)ne * sizeof(uint32_t), st));
-    MLS_CUDA_TRY(cudaMallocAsync((void **)&ent, (size_t)n * k * sizeof(unsigned long long), st));
-    if (order) MLS_CUDA_TRY(cudaMallocAsync((void **)&pos, (size_t)n * sizeof(int32_t), st));
+    MLS_CUDA_TRY(scratch_alloc((void **)&xyz4, (size_t)n * sizeof(float4), st));
+    MLS_CUDA_TRY(scratch_alloc((void **)&edge4, (size_t)ne * sizeof(float4), st));
+    MLS_CUDA_TRY(scratch_alloc((void **)&self4, (size_t)n * sizeof(float4), st));
+    MLS_CUDA_TRY(scratch_alloc((void **)&hp, (size_t)blocks * sizeof(double), st));
+    MLS_CUDA_TRY(scratch_alloc((void **)&cnt, (size_t)(2 * n + 2) * sizeof(int32_t), st));
+    MLS_CUDA_TRY(scratch_alloc((void **)&off, (size_t)(n + 1) * sizeof(int32_t), st));
+    MLS_CUDA_TRY(scratch_alloc((void **)&tgt, (size_t)ne * sizeof(uint32_t), st));
+    MLS_CUDA_TRY(scratch_alloc((void **)&ent, (size_t)n * k * sizeof(unsigned long long), st));
+    if (order) MLS_CUDA_TRY(scratch_alloc((void **)&pos, (size_t)n * sizeof(int32_t), st));
     int32_t *fill = cnt + n + 1;
     const int grid_n = (int)std::min<int64_t>((n + 255) / 256, 152 * 16);
     MLS_CUDA_TRY(cudaMemsetAsync(cnt, 0, (size_t)(2 * n + 2) * sizeof(int32_t), st));

@@ -19,6 +19,10 @@ int set_error(int code, const char *fmt, ...);
 // Adds to the process-wide count of kernel launches.
 void count_launches(int n);
 
+// Stream-ordered scratch from the library's per-device pool (scratch.cu);
+// release with cudaFreeAsync on the same stream.
+cudaError_t scratch_alloc(void **p, size_t bytes, cudaStream_t st);
+
 #define MLS_CUDA_TRY(expr)                                                              \
     do {                                                                                \
         cudaError_t e_ = (expr);                                                        \

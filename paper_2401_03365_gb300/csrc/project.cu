@@ -165,7 +165,7 @@ int launch_deg(const float *xyz, int64_t n, const int32_t *idx, int k, float h, 
     } else {
         // a stream-ordered scratch copy of the points as float4
         float4 *xyz4 = nullptr;
-        MLS_CUDA_TRY(cudaMallocAsync((void **)&xyz4, (size_t)n * sizeof(float4), st));
+        MLS_CUDA_TRY(scratch_alloc((void **)&xyz4, (size_t)n * sizeof(float4), st));
         k_pack_xyz4<<<(int)std::min<int64_t>((n + 255) / 256, 152 * 16), 256, 0, st>>>(xyz, n, xyz4);
         const size_t smem = (size_t)k * 32 * sizeof(int32_t) * (kProjThreads / 32);
         if (precision == MLS_PREC_MIXED) {

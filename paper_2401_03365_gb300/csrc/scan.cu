@@ -67,7 +67,7 @@ __global__ void k_scan_add(int32_t *__restrict__ out, int64_t n, const int32_t *
 int device_exclusive_scan(const int32_t *in, int32_t *out, int64_t n, cudaStream_t st) {
     const int64_t blocks = (n + kScanThreads - 1) / kScanThreads;
     int32_t *sums = nullptr;
-    MLS_CUDA_TRY(cudaMallocAsync((void **)&sums, (size_t)blocks * sizeof(int32_t), st));
+    MLS_CUDA_TRY(scratch_alloc((void **)&sums, (size_t)blocks * sizeof(int32_t), st));
     k_scan_blocks<<<(unsigned)blocks, kScanThreads, 0, st>>>(in, out, n, sums);
     k_scan_sums<<<1, kScanThreads, 0, st>>>(sums, blocks);
     k_scan_add<<<(unsigned)blocks, kScanThreads, 0, st>>>(out, n, sums);

@@ -164,6 +164,29 @@ def dist_setup(args):
     return world, rank, local
 
 
+def rank_seeds(rank):
+    """(cloud seed, cotangent seed) of a rank: every rank projects its own
+    cloud, so the N-GPU job is N independent problems (weak scaling)."""
+    return 2 + rank, 11 + rank
+
+
+def max_over_ranks(values, device="cpu"):
+    """Element-wise maximum of per-rank timings over all ranks (the job's
+    time is the slowest rank's); identity without a process group."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.tolist()]
+
+
+def job_throughput(world, points_per_rank, ms):
+    """Points per second of the whole job: all ranks' points over the
+    slowest rank's time."""
+    return world * points_per_rank / (ms * 1e-3)
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -177,7 +200,8 @@ def run_ours(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     build.build()
     dev = torch.device("cuda", local)
-    cloud = workloads.torus(n=n_pts, seed=2 + rank, k=K)
+    cloud_seed, cot_seed = rank_seeds(rank)
+    cloud = workloads.torus(n=n_pts, seed=cloud_seed, k=K)
     x = torch.from_numpy(cloud.xyz).to(dev)
     stream = torch.cuda.current_stream()
 
@@ -187,7 +211,7 @@ def run_ours(args):
     out_st = torch.empty(n_pts, dtype=torch.uint8, device=dev)
     grad = torch.empty_like(x)
     grad_h = torch.empty(1, dtype=torch.float32, device=dev)
-    gen = torch.Generator(device=dev).manual_seed(11 + rank)
+    gen = torch.Generator(device=dev).manual_seed(cot_seed)
     gp = torch.randn((n_pts, 3), generator=gen, device=dev)          # cotangent of the points
     gn = 0.1 * torch.randn((n_pts, 3), generator=gen, device=dev)    # cotangent of the normals
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
@@ -233,11 +257,8 @@ def run_ours(args):
     launches = capi.mls_kernel_launches() - launches0
     stage = np.array([[e[i].elapsed_time(e[i + 1]) for i in range(4)] for e in events])  # ms
     build_ms, knn_ms, proj_ms, bwd_ms = (float(v) for v in stage.mean(0))
-    t = torch.tensor([stage.sum(1).mean(), stage[:, :3].sum(1).mean()], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    step_ms, fwd_ms = float(t[0]), float(t[1])
-    value = world * n_pts / (step_ms * 1e-3)
+    step_ms, fwd_ms = max_over_ranks([stage.sum(1).mean(), stage[:, :3].sum(1).mean()], dev)
+    value = job_throughput(world, n_pts, step_ms)
 
     # end to end through the public API with host buffers: every step copies
     # the points in from pinned memory, runs the four calls, and copies the
@@ -264,10 +285,8 @@ def run_ours(args):
         b.synchronize()
         if s > 0:                      # the first one warms the copy path
             e2e_ms.append(a.elapsed_time(b))
-    te = torch.tensor([float(np.mean(e2e_ms))], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(te, op=dist.ReduceOp.MAX)
-    e2e_value = world * n_pts / (float(te.item()) * 1e-3)
+    (e2e_step_ms,) = max_over_ranks([float(np.mean(e2e_ms))], dev)
+    e2e_value = job_throughput(world, n_pts, e2e_step_ms)
     grid.close()
     if rank != 0:
         if world > 1:
@@ -322,7 +341,7 @@ def run_ours(args):
                    "h": h, "step": "grid build + exact kNN + MLS projection + backward (fwd+bwd)",
                    "l2": "flushed before every step (256 MB write, outside the timed events)",
                    "parallelism": f"independent clouds per GPU x{world}"},
-        "fwd": {"value": world * n_pts / (fwd_ms * 1e-3), "unit": "points/s", "ms_per_step": fwd_ms,
+        "fwd": {"value": job_throughput(world, n_pts, fwd_ms), "unit": "points/s", "ms_per_step": fwd_ms,
                 "step": "grid build + exact kNN + MLS projection"},
         "roofline": roofline,
         "kernels": kernels,

@@ -22,9 +22,18 @@ namespace {
 thread_local char g_last_error[512] = "";
 std::atomic<int64_t> g_launches{0};
 
-// Mean neighbour distance excluding self, accumulated in FP64.
-__global__ void k_mean_dist(const float *__restrict__ xyz, int64_t n, const int32_t *__restrict__ idx, int k,
-                            double *acc) {
+// Mean neighbour distance excluding self, accumulated in FP64 in a fixed
+// order (a grid-stride loop of a fixed grid, then fixed trees), so the
+// result does not change from run to run.
+constexpr int kMeanBlocks = 152 * 8;
+constexpr int kMeanThreads = 256;
+
+__global__ void __launch_bounds__(kMeanThreads) k_mean_dist(const float *__restrict__ xyz, int64_t n,
+                                                            const int32_t *__restrict__ idx, int k,
+                                                            double *__restrict__ part_sum,
+                                                            unsigned long long *__restrict__ part_cnt) {
+    __shared__ double ssum[kMeanThreads / 32];
+    __shared__ unsigned long long scnt[kMeanThreads / 32];
     double sum = 0.0;
     unsigned long long cnt = 0;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * k;
@@ -44,14 +53,44 @@ __global__ void k_mean_dist(const float *__restrict__ xyz, int64_t n, const int3
         cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
     }
     if ((threadIdx.x & 31) == 0) {
-        atomicAdd(&acc[0], sum);
-        atomicAdd((unsigned long long *)&acc[1], cnt);
+        ssum[threadIdx.x >> 5] = sum;
+        scnt[threadIdx.x >> 5] = cnt;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        unsigned long long c = 0;
+        for (int w = 0; w < kMeanThreads / 32; ++w) {
+            t += ssum[w];
+            c += scnt[w];
+        }
+        part_sum[blockIdx.x] = t;
+        part_cnt[blockIdx.x] = c;
     }
 }
 
-__global__ void k_mean_finish(double *acc, double *out) {
-    unsigned long long cnt = *(unsigned long long *)&acc[1];
-    *out = cnt ? acc[0] / (double)cnt : 0.0;
+__global__ void __launch_bounds__(1024) k_mean_finish(const double *__restrict__ part_sum,
+                                                      const unsigned long long *__restrict__ part_cnt,
+                                                      double *__restrict__ out) {
+    __shared__ double red[1024];
+    __shared__ unsigned long long redc[1024];
+    double t = 0.0;
+    unsigned long long c = 0;
+    for (int b = threadIdx.x; b < kMeanBlocks; b += 1024) {
+        t += part_sum[b];
+        c += part_cnt[b];
+    }
+    red[threadIdx.x] = t;
+    redc[threadIdx.x] = c;
+    __syncthreads();
+    for (int s = 512; s > 0; s >>= 1) {
+        if (threadIdx.x < s) {
+            red[threadIdx.x] += red[threadIdx.x + s];
+            redc[threadIdx.x] += redc[threadIdx.x + s];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = redc[0] ? red[0] / (double)redc[0] : 0.0;
 }
 
 }  // namespace
@@ -193,13 +232,13 @@ int mls_mean_knn_dist(const float *d_xyz, int64_t n, const int32_t *d_idx, int k
     if (!d_xyz || !d_idx || !d_out) return set_error(MLS_ERR_INVALID_ARG, "mls_mean_knn_dist: null pointer");
     if (n < 1 || k < 1 || k > MLS_MAX_K) return set_error(MLS_ERR_INVALID_ARG, "mls_mean_knn_dist: n or k");
     cudaStream_t st = (cudaStream_t)stream;
-    double *acc = nullptr;
-    MLS_CUDA_TRY(mls::scratch_alloc((void **)&acc, 2 * sizeof(double), st));
-    MLS_CUDA_TRY(cudaMemsetAsync(acc, 0, 2 * sizeof(double), st));
-    mls::k_mean_dist<<<152 * 8, 256, 0, st>>>(d_xyz, n, d_idx, k, acc);
-    mls::k_mean_finish<<<1, 1, 0, st>>>(acc, d_out);
+    double *part = nullptr;
+    MLS_CUDA_TRY(mls::scratch_alloc((void **)&part, 2 * mls::kMeanBlocks * sizeof(double), st));
+    unsigned long long *cnt = reinterpret_cast<unsigned long long *>(part + mls::kMeanBlocks);
+    mls::k_mean_dist<<<mls::kMeanBlocks, mls::kMeanThreads, 0, st>>>(d_xyz, n, d_idx, k, part, cnt);
+    mls::k_mean_finish<<<1, 1024, 0, st>>>(part, cnt, d_out);
     mls::count_launches(2);
-    MLS_CUDA_TRY(cudaFreeAsync(acc, st));
+    MLS_CUDA_TRY(cudaFreeAsync(part, st));
     MLS_CUDA_TRY(cudaGetLastError());
     return MLS_OK;
 }

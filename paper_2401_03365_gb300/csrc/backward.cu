@@ -75,8 +75,10 @@ __device__ __forceinline__ void basis(float u, float v, float phi[6]) {
     }
 }
 
+// Six blocks per SM (80 registers): the kernel waits on its neighbour gathers,
+// and more resident warps hide more of that latency than the spills cost.
 template <int DEG, int PREC>
-__global__ void __launch_bounds__(kBwdThreads) k_backward_point(
+__global__ void __launch_bounds__(kBwdThreads, 6) k_backward_point(
     const float4 *__restrict__ xyz4, int64_t n, const int32_t *__restrict__ idx, int k, float h,
     const int32_t *__restrict__ order, const int32_t *__restrict__ pos, const float *__restrict__ gout_xyz,
     const float *__restrict__ gout_n, float4 *__restrict__ edge4, uint32_t *__restrict__ tgt,

@@ -98,3 +98,19 @@ def test_binding_type_checks(capi, cloud):
         capi.mls_build_grid(cloud.cpu(), 0.0, 8)
     with pytest.raises(ValueError):
         capi.mls_build_grid(cloud[:, :2].contiguous(), 0.0, 8)
+
+
+def test_mean_knn_dist_matches_oracle_and_repeats_exactly(capi):
+    """The bandwidth helper: the FP64 mean distance to the neighbours other
+    than the point itself, summed in a fixed order (bit-identical calls)."""
+    import oracle
+    from paper_2401_03365_gb300 import workloads
+    c = workloads.sphere(n=20_000, seed=3, k=20)
+    idx_o, _ = oracle.knn_kdtree(c.xyz, c.k)
+    x = torch.from_numpy(c.xyz).cuda()
+    idx = torch.from_numpy(idx_o.astype(np.int32)).cuda()
+    a = capi.mls_mean_knn_dist(x, idx).item()
+    b = capi.mls_mean_knn_dist(x, idx).item()
+    assert a == b
+    ref = oracle.mean_knn_dist(c.xyz, idx_o)
+    assert abs(a - ref) <= 1e-12 * ref

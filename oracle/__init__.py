@@ -26,12 +26,14 @@ import numpy as np
 from .build import build_oracle, library_path
 
 __all__ = [
-    "knn_brute", "knn_kdtree", "mean_knn_dist", "project", "project_grad", "fit_height",
+    "knn_brute", "knn_kdtree", "mean_knn_dist", "project", "project_grad", "project_levin", "fit_height",
     "jacobi_eig", "cholesky_solve", "knn_key", "STATUS_PLANE_DEGENERATE", "STATUS_POLY_SINGULAR",
+    "STATUS_NOT_CONVERGED",
 ]
 
 STATUS_PLANE_DEGENERATE = 1
 STATUS_POLY_SINGULAR = 2
+STATUS_NOT_CONVERGED = 8
 
 _lib = None
 
@@ -70,6 +72,8 @@ def _load():
                                    _u8p, _f64p]
     lib.oracle_project_grad.argtypes = [_f32p, _i64, _i32p, _int, _dbl, _int, _f64p, _f64p, _i64p, _i64,
                                         _f64p, _f64p]
+    lib.oracle_project_levin.argtypes = [_f32p, _i64, _i32p, _int, _dbl, _int, _int, _dbl, _i64p, _i64, _f64p,
+                                         _f64p, _u8p, _i32p]
     _lib = lib
     return lib
 
@@ -148,6 +152,28 @@ def project(xyz, idx, h, degree=2, queries=None):
     if rc != 0:
         raise ValueError(f"oracle_project failed ({rc})")
     return out, nrm, st, diag
+
+
+def project_levin(xyz, idx, h, degree=2, max_iter=100, tol=1e-12, queries=None):
+    """The projection with weights about q (Sec. 1.4, Eq. 1), by the fixed
+    point iteration from q = r.  Returns (xyz', normal, status, iterations);
+    status bit 8 marks points that did not converge within max_iter."""
+    xyz = _xyz(xyz)
+    idx = np.ascontiguousarray(idx, np.int32)
+    n, k = xyz.shape[0], idx.shape[1]
+    q = None if queries is None else np.ascontiguousarray(queries, np.int64)
+    m = n if q is None else q.shape[0]
+    assert idx.shape[0] == m, "one neighbour row per projected point"
+    out = np.empty((m, 3), np.float64)
+    nrm = np.empty((m, 3), np.float64)
+    st = np.empty(m, np.uint8)
+    it = np.empty(m, np.int32)
+    rc = _load().oracle_project_levin(_p(xyz, _f32p), n, _p(idx, _i32p), k, float(h), int(degree), int(max_iter),
+                                      float(tol), _p(q, _i64p), m, _p(out, _f64p), _p(nrm, _f64p), _p(st, _u8p),
+                                      _p(it, _i32p))
+    if rc != 0:
+        raise ValueError(f"oracle_project_levin failed ({rc})")
+    return out, nrm, st, it
 
 
 def project_grad(xyz, idx, h, degree, gout_xyz, gout_normal=None, queries=None):

@@ -807,3 +807,115 @@ int oracle_project_grad(const float *xyz, int64_t n, const int32_t *idx, int k, 
     free_state(&st);
     return 0;
 }
+
+/* ------------------------------------------------------------------------- */
+/* The projection with weights about q (Sec. 1.4, Eq. 1)                      */
+/* ------------------------------------------------------------------------- */
+
+#define ST_NOT_CONVERGED 8
+
+/* Eq. 1 weighs each neighbour by theta(|p_i - q|), q = r + t n being the
+ * projection of r onto the plane H that the weighted fit returns.  Reading:
+ * H is the self-consistent plane -- the weighted least-squares plane (normal
+ * = eigenvector of the smallest eigenvalue of the weighted covariance about
+ * the weighted centroid) for weights taken about the projection of r onto
+ * that same plane.  It is reached by the fixed-point iteration that starts
+ * at q = r (t = 0, the root nearest the point, Sec. 1.4's smallest t) and
+ * alternates "weights about q" and "plane of those weights, q = projection of
+ * r onto it", until t changes by at most tol * h (or max_iter iterations,
+ * status bit 8).  The polynomial is then fitted in the frame at the final q
+ * with the weights about that q, and the result is q + g(0, 0) n.
+ * Status, degenerate and singular rules as in oracle_project.
+ * out_iter (optional): iterations used per point. */
+int oracle_project_levin(const float *xyz, int64_t n, const int32_t *idx, int k, double h, int degree,
+                         int max_iter, double tol, const int64_t *queries, int64_t nq, double *out_xyz,
+                         double *out_normal, uint8_t *out_status, int32_t *out_iter)
+{
+    if (k < 1 || k > n || !(h > 0.0) || degree < 0 || degree > 2 || max_iter < 1) return -1;
+    double *P = (double *)malloc(sizeof(double) * 3 * (size_t)k);
+    double *w = (double *)malloc(sizeof(double) * (size_t)k);
+    if (!P || !w) {
+        free(P);
+        free(w);
+        return -2;
+    }
+    int64_t m = queries ? nq : n;
+    for (int64_t s = 0; s < m; ++s) {
+        int64_t i = queries ? queries[s] : s;
+        const int32_t *row = idx + s * k;
+        double r[3], q[3], nrm[3] = {0, 0, 0}, e1[3] = {0, 0, 0}, e2[3] = {0, 0, 0};
+        for (int a = 0; a < 3; ++a) r[a] = q[a] = (double)xyz[3 * i + a];
+        for (int j = 0; j < k; ++j)
+            for (int a = 0; a < 3; ++a) P[3 * j + a] = (double)xyz[3 * (int64_t)row[j] + a];
+        int status = ST_NOT_CONVERGED, iters = 0;
+        double t = 0.0;
+        for (int it = 0; it < max_iter; ++it) {
+            iters = it + 1;
+            /* weights about q */
+            double W = 0.0, c[3] = {0, 0, 0};
+            for (int j = 0; j < k; ++j) {
+                double d2 = 0.0;
+                for (int a = 0; a < 3; ++a) d2 += (P[3 * j + a] - q[a]) * (P[3 * j + a] - q[a]);
+                w[j] = exp(-d2 / (h * h));
+                W += w[j];
+                for (int a = 0; a < 3; ++a) c[a] += w[j] * P[3 * j + a];
+            }
+            for (int a = 0; a < 3; ++a) c[a] /= W;
+            /* the weighted plane through c */
+            double C[9] = {0}, lam[3], V[9];
+            for (int j = 0; j < k; ++j) {
+                double e[3];
+                for (int a = 0; a < 3; ++a) e[a] = P[3 * j + a] - c[a];
+                for (int a = 0; a < 3; ++a)
+                    for (int b = 0; b < 3; ++b) C[3 * a + b] += w[j] * e[a] * e[b];
+            }
+            for (int x = 0; x < 9; ++x) C[x] /= W;
+            oracle_jacobi_eig(3, C, lam, V);
+            for (int a = 0; a < 3; ++a) {
+                nrm[a] = V[3 * a + 0];
+                e1[a] = V[3 * a + 1];
+            }
+            canonical_sign(nrm);
+            e2[0] = nrm[1] * e1[2] - nrm[2] * e1[1];
+            e2[1] = nrm[2] * e1[0] - nrm[0] * e1[2];
+            e2[2] = nrm[0] * e1[1] - nrm[1] * e1[0];
+            if (!(lam[2] > 0.0) || (lam[1] - lam[0]) <= 1e-6 * lam[2]) {
+                status = ST_PLANE_DEGENERATE;
+                break;
+            }
+            /* q: the projection of r onto the plane */
+            double tn = nrm[0] * (c[0] - r[0]) + nrm[1] * (c[1] - r[1]) + nrm[2] * (c[2] - r[2]);
+            for (int a = 0; a < 3; ++a) q[a] = r[a] + tn * nrm[a];
+            int done = it > 0 && fabs(tn - t) <= tol * h;
+            t = tn;
+            if (done) {
+                status = 0;
+                break;
+            }
+        }
+        double out[3] = {r[0], r[1], r[2]};
+        if (!(status & ST_PLANE_DEGENERATE)) {
+            /* weights about the final q, the height polynomial, the projection */
+            for (int j = 0; j < k; ++j) {
+                double d2 = 0.0;
+                for (int a = 0; a < 3; ++a) d2 += (P[3 * j + a] - q[a]) * (P[3 * j + a] - q[a]);
+                w[j] = exp(-d2 / (h * h));
+            }
+            double coef[6] = {0, 0, 0, 0, 0, 0};
+            if (!oracle_fit_height(k, P, w, nrm, e1, e2, q, h, degree, coef, NULL)) {
+                status |= ST_POLY_SINGULAR;
+                coef[0] = 0.0;
+            }
+            for (int a = 0; a < 3; ++a) out[a] = q[a] + coef[0] * nrm[a];
+        }
+        for (int a = 0; a < 3; ++a) {
+            out_xyz[3 * s + a] = out[a];
+            if (out_normal) out_normal[3 * s + a] = nrm[a];
+        }
+        if (out_status) out_status[s] = (uint8_t)status;
+        if (out_iter) out_iter[s] = iters;
+    }
+    free(P);
+    free(w);
+    return 0;
+}

@@ -287,6 +287,26 @@ def run_ours(args):
             e2e_ms.append(a.elapsed_time(b))
     (e2e_step_ms,) = max_over_ranks([float(np.mean(e2e_ms))], dev)
     e2e_value = job_throughput(world, n_pts, e2e_step_ms)
+
+    # the form with the weights about q (Sec. 1.4, Eq. 1), same rows and h
+    grid = capi.mls_build_grid(x, 0.0, K, grid=grid)
+    capi.mls_knn(grid, K, out_idx=idx)
+    order = capi.mls_grid_order(grid)
+    lv = [torch.empty_like(x), torch.empty_like(x), torch.empty(n_pts, dtype=torch.uint8, device=dev)]
+    for _ in range(2):
+        capi.mls_project_levin(x, idx, h, 2, "mixed", max_iter=32, tol=1e-6, order=order, out_xyz=lv[0], out_normal=lv[1],
+                               out_status=lv[2])
+    lv_ms = []
+    for _ in range(5):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        capi.mls_project_levin(x, idx, h, 2, "mixed", max_iter=32, tol=1e-6, order=order, out_xyz=lv[0], out_normal=lv[1],
+                               out_status=lv[2])
+        b.record(stream)
+        b.synchronize()
+        lv_ms.append(a.elapsed_time(b))
+    lv_not_conv = float(((lv[2] & 8) != 0).float().mean().item())
     grid.close()
     if rank != 0:
         if world > 1:
@@ -345,6 +365,10 @@ def run_ours(args):
                 "step": "grid build + exact kNN + MLS projection"},
         "roofline": roofline,
         "kernels": kernels,
+        "levin": {"ms": float(np.median(lv_ms)), "points_per_s": n_pts / (float(np.median(lv_ms)) * 1e-3),
+                  "step": "mls_project_levin (weights about q, fixed point from q = r, tol 1e-6 h, <= 32 passes), "
+                          "mixed, degree 2, same rows and h",
+                  "not_converged_frac": lv_not_conv},
         "e2e": {"value": e2e_value, "unit": "points/s", "h2d_bytes_per_step": n_pts * 12,
                 "d2h_bytes_per_step": n_pts * (12 + 12 + 1 + 12)},
         "gpu_launches": int(launches),

@@ -74,7 +74,8 @@ enum mls_point_status {
     MLS_PT_OK = 0,
     MLS_PT_PLANE_DEGENERATE = 1,
     MLS_PT_POLY_SINGULAR = 2,
-    MLS_PT_FP64_USED = 4
+    MLS_PT_FP64_USED = 4,
+    MLS_PT_NOT_CONVERGED = 8   /* mls_project_levin: t still moving after max_iter passes */
 };
 
 #define MLS_MAX_K 64
@@ -149,6 +150,26 @@ int mls_knn(const mls_grid *g, int k, int32_t *d_idx, float *d_key, mls_stream s
 int mls_project(const float *d_xyz, int64_t n, const int32_t *d_idx, int k, float h, int degree,
                 int precision, const int32_t *d_order, float *d_out_xyz, float *d_out_normal,
                 uint8_t *d_status, mls_stream stream);
+
+/*
+ * mls_project_levin -- the projection with the weights of Eq. 1 (Sec. 1.4)
+ * taken about q = r + t n, the projection of the point onto the reference
+ * plane, rather than about the point itself.  Reading of the paper: the
+ * plane is self-consistent -- the weighted least-squares plane for weights
+ * about the projection of r onto that plane -- and is reached by fixed-point
+ * iteration from q = r (t = 0, the smallest t): weights about q, plane, new q,
+ * until t changes by at most tol * h.  The height polynomial is then fitted
+ * in the frame at the final q with the weights about that q, and the result
+ * is q + g(0, 0) n.
+ *
+ *   arguments as for mls_project, plus
+ *   max_iter   1..64 plane passes; points still moving get MLS_PT_NOT_CONVERGED
+ *   tol        > 0, convergence threshold on t relative to h (1e-6 typical)
+ *   precision  MLS_PREC_FP32 or MLS_PREC_MIXED
+ */
+int mls_project_levin(const float *d_xyz, int64_t n, const int32_t *d_idx, int k, float h, int degree,
+                      int precision, int max_iter, float tol, const int32_t *d_order, float *d_out_xyz,
+                      float *d_out_normal, uint8_t *d_status, mls_stream stream);
 
 /*
  * mls_project_noalloc -- mls_project for callers that must not allocate

@@ -17,7 +17,7 @@ from .build import library_path
 
 __all__ = [
     "MLSError", "Grid", "lib", "mls_build_grid", "mls_grid_destroy", "mls_grid_size", "mls_grid_order",
-    "mls_knn", "mls_project", "mls_project_backward", "mls_mean_knn_dist", "mls_status_str", "mls_last_error", "mls_kernel_launches", "mls_release_scratch",
+    "mls_knn", "mls_project", "mls_project_levin", "mls_project_backward", "mls_mean_knn_dist", "mls_status_str", "mls_last_error", "mls_kernel_launches", "mls_release_scratch",
     "Batch", "mls_batch_create", "mls_batch_destroy", "mls_batch_set_shape", "mls_batch_get_shape",
     "mls_project_batched", "mls_batch_capture", "mls_batch_replay", "mls_batch_autotune", "mls_batch_tune_results",
     "PRECISION", "MLS_MAX_K", "MLS_PT_OK", "MLS_PT_PLANE_DEGENERATE", "MLS_PT_POLY_SINGULAR",
@@ -28,6 +28,7 @@ MLS_MAX_K = 64
 MLS_NOALLOC_MAX_POINTS = 262144
 PRECISION = {"fp32": 0, "mixed": 1, "fp64": 2}
 MLS_PT_OK, MLS_PT_PLANE_DEGENERATE, MLS_PT_POLY_SINGULAR, MLS_PT_FP64_USED = 0, 1, 2, 4
+MLS_PT_NOT_CONVERGED = 8
 
 _vp = ctypes.c_void_p
 _i64 = ctypes.c_int64
@@ -43,6 +44,7 @@ _SIGNATURES = [
     ("mls_knn", _int, [_vp, _int, _vp, _vp, _vp]),
     ("mls_project", _int, [_vp, _i64, _vp, _int, _flt, _int, _int, _vp, _vp, _vp, _vp, _vp]),
     ("mls_project_noalloc", _int, [_vp, _i64, _vp, _int, _flt, _int, _int, _vp, _vp, _vp, _vp, _vp]),
+    ("mls_project_levin", _int, [_vp, _i64, _vp, _int, _flt, _int, _int, _int, _flt, _vp, _vp, _vp, _vp, _vp]),
     ("mls_project_backward", _int, [_vp, _i64, _vp, _int, _flt, _int, _int, _vp, _vp, _vp, _vp, _vp, _vp]),
     ("mls_mean_knn_dist", _int, [_vp, _i64, _vp, _int, _vp, _vp]),
     ("mls_batch_create", _int, [_int, _vp, _vp, ctypes.POINTER(_vp)]),
@@ -239,6 +241,30 @@ def mls_project(xyz: torch.Tensor, idx: torch.Tensor, h: float, degree: int = 2,
     rc = lib().mls_project(_ptr(xyz), n, _ptr(idx), k, float(h), int(degree), PRECISION[precision],
                            _ptr(order), _ptr(out_xyz), _ptr(out_normal), _ptr(out_status), _stream(stream))
     _check("mls_project", rc)
+    return out_xyz, out_normal, out_status
+
+
+def mls_project_levin(xyz: torch.Tensor, idx: torch.Tensor, h: float, degree: int = 2, precision: str = "mixed",
+                      max_iter: int = 32, tol: float = 1e-6, order: torch.Tensor | None = None, out_xyz=None,
+                      out_normal=None, out_status=None, stream=None):
+    """The projection with the weights about q (Sec. 1.4, Eq. 1); see mls.h."""
+    _need(xyz, "xyz", torch.float32)
+    n = xyz.shape[0]
+    _need(idx, "idx", torch.int32)
+    if idx.dim() != 2 or idx.shape[0] != n:
+        raise ValueError("idx must be (n, k)")
+    if order is not None:
+        _need(order, "order", torch.int32, (n,))
+    out_xyz = torch.empty_like(xyz) if out_xyz is None else out_xyz
+    out_normal = torch.empty_like(xyz) if out_normal is None else out_normal
+    out_status = torch.empty(n, dtype=torch.uint8, device=xyz.device) if out_status is None else out_status
+    _need(out_xyz, "out_xyz", torch.float32, (n, 3))
+    _need(out_normal, "out_normal", torch.float32, (n, 3))
+    _need(out_status, "out_status", torch.uint8, (n,))
+    rc = lib().mls_project_levin(_ptr(xyz), n, _ptr(idx), idx.shape[1], float(h), int(degree), PRECISION[precision],
+                                 int(max_iter), float(tol), _ptr(order), _ptr(out_xyz), _ptr(out_normal),
+                                 _ptr(out_status), _stream(stream))
+    _check("mls_project_levin", rc)
     return out_xyz, out_normal, out_status
 
 

@@ -14,6 +14,9 @@ void free_grid_buffers(mls_grid *g);
 int launch_knn(const mls_grid *grid, int k, int32_t *idx, float *key, cudaStream_t st);
 int launch_project(const float *xyz, int64_t n, const int32_t *idx, int k, float h, int degree, int precision,
                    const int32_t *order, float *out_xyz, float *out_n, uint8_t *status, cudaStream_t st);
+int launch_project_levin(const float *xyz, int64_t n, const int32_t *idx, int k, float h, int degree,
+                         int precision, int max_iter, float tol, const int32_t *order, float *out_xyz,
+                         float *out_n, uint8_t *status, cudaStream_t st);
 int launch_backward(const float *xyz, int64_t n, const int32_t *idx, int k, float h, int degree, int precision,
                     const int32_t *order, const float *gp, const float *gn, float *grad_xyz, float *grad_h,
                     cudaStream_t st);
@@ -201,6 +204,31 @@ int mls_project(const float *d_xyz, int64_t n, const int32_t *d_idx, int k, floa
         return set_error(MLS_ERR_INVALID_ARG, "mls_project: output aliases the input");
     return mls::launch_project(d_xyz, n, d_idx, k, h, degree, precision, d_order, d_out_xyz, d_out_normal,
                                d_status, (cudaStream_t)stream);
+}
+
+int mls_project_levin(const float *d_xyz, int64_t n, const int32_t *d_idx, int k, float h, int degree,
+                      int precision, int max_iter, float tol, const int32_t *d_order, float *d_out_xyz,
+                      float *d_out_normal, uint8_t *d_status, mls_stream stream) {
+    mls::g_last_error[0] = 0;
+    if (!d_xyz || !d_idx || !d_out_xyz) return set_error(MLS_ERR_INVALID_ARG, "mls_project_levin: null pointer");
+    if (n < 1) return set_error(MLS_ERR_INVALID_ARG, "mls_project_levin: n = %lld < 1", (long long)n);
+    if (n > 0x7fffffffLL) return set_error(MLS_ERR_TOO_LARGE, "mls_project_levin: n = %lld", (long long)n);
+    if (k < 1 || k > MLS_MAX_K || k > n)
+        return set_error(MLS_ERR_K_TOO_LARGE, "mls_project_levin: k = %d not in [1, min(%d, n)]", k, MLS_MAX_K);
+    if (!(h > 0.0f) || !std::isfinite(h))
+        return set_error(MLS_ERR_INVALID_ARG, "mls_project_levin: h = %g must be finite and > 0", (double)h);
+    if (degree < 0 || degree > 2)
+        return set_error(MLS_ERR_UNSUPPORTED_DEGREE, "mls_project_levin: degree = %d not in {0, 1, 2}", degree);
+    if (precision != MLS_PREC_FP32 && precision != MLS_PREC_MIXED)
+        return set_error(MLS_ERR_INVALID_ARG, "mls_project_levin: precision = %d (FP32 or mixed)", precision);
+    if (max_iter < 1 || max_iter > 64)
+        return set_error(MLS_ERR_INVALID_ARG, "mls_project_levin: max_iter = %d not in [1, 64]", max_iter);
+    if (!(tol > 0.0f) || !std::isfinite(tol))
+        return set_error(MLS_ERR_INVALID_ARG, "mls_project_levin: tol = %g must be finite and > 0", (double)tol);
+    if ((const void *)d_out_xyz == (const void *)d_xyz)
+        return set_error(MLS_ERR_INVALID_ARG, "mls_project_levin: output aliases the input");
+    return mls::launch_project_levin(d_xyz, n, d_idx, k, h, degree, precision, max_iter, tol, d_order, d_out_xyz,
+                                     d_out_normal, d_status, (cudaStream_t)stream);
 }
 
 int mls_project_backward(const float *d_xyz, int64_t n, const int32_t *d_idx, int k, float h, int degree,

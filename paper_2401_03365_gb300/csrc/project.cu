@@ -28,12 +28,13 @@ __global__ void k_pack_xyz4(const float *__restrict__ xyz, int64_t n, float4 *__
 // 32 neighbour rows into shared memory with coalesced loads (stored
 // transposed, entry j of lane t at j * 32 + t), then every lane runs
 // project_point on its own point.
-template <int DEG, int PREC>
+template <int DEG, int PREC, bool LEVIN = false>
 __global__ void __launch_bounds__(kProjThreads) k_project(const float4 *__restrict__ xyz4, int64_t n,
                                                           const int32_t *__restrict__ idx, int k, float h,
                                                           const int32_t *__restrict__ order,
                                                           float *__restrict__ out_xyz, float *__restrict__ out_n,
-                                                          uint8_t *__restrict__ status) {
+                                                          uint8_t *__restrict__ status, int max_iter,
+                                                          float tol) {
     extern __shared__ int32_t rows[];
     const int lane = threadIdx.x & 31;
     int32_t *my_rows = rows + (threadIdx.x >> 5) * k * 32;
@@ -51,8 +52,8 @@ __global__ void __launch_bounds__(kProjThreads) k_project(const float4 *__restri
     if (slot >= n) return;
     const float4 r4 = __ldg(xyz4 + i);
     float out[3], nf[3];
-    const uint8_t st = project_point<DEG, PREC>(
-        xyz4, [&](int j) { return my_rows[j * 32 + lane]; }, k, 0, 1, h, r4.x, r4.y, r4.z, out, nf);
+    const uint8_t st = project_point<DEG, PREC, LEVIN>(
+        xyz4, [&](int j) { return my_rows[j * 32 + lane]; }, k, 0, 1, h, r4.x, r4.y, r4.z, out, nf, max_iter, tol);
     out_xyz[3 * i] = out[0];
     out_xyz[3 * i + 1] = out[1];
     out_xyz[3 * i + 2] = out[2];
@@ -171,11 +172,11 @@ int launch_deg(const float *xyz, int64_t n, const int32_t *idx, int k, float h, 
         if (precision == MLS_PREC_MIXED) {
             auto kern = k_project<DEG, MLS_PREC_MIXED>;
             MLS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            kern<<<blocks, kProjThreads, smem, st>>>(xyz4, n, idx, k, h, order, out_xyz, out_n, status);
+            kern<<<blocks, kProjThreads, smem, st>>>(xyz4, n, idx, k, h, order, out_xyz, out_n, status, 1, 0.f);
         } else {
             auto kern = k_project<DEG, MLS_PREC_FP32>;
             MLS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            kern<<<blocks, kProjThreads, smem, st>>>(xyz4, n, idx, k, h, order, out_xyz, out_n, status);
+            kern<<<blocks, kProjThreads, smem, st>>>(xyz4, n, idx, k, h, order, out_xyz, out_n, status, 1, 0.f);
         }
         count_launches(2);
         MLS_CUDA_TRY(cudaFreeAsync(xyz4, st));
@@ -195,6 +196,48 @@ int launch_project(const float *xyz, int64_t n, const int32_t *idx, int k, float
             return launch_deg<1>(xyz, n, idx, k, h, precision, order, out_xyz, out_n, status, st);
         default:
             return launch_deg<2>(xyz, n, idx, k, h, precision, order, out_xyz, out_n, status, st);
+    }
+}
+
+namespace {
+
+// The form with the weights about q (Sec. 1.4, Eq. 1): FP32 or mixed.
+template <int DEG>
+int launch_levin_deg(const float *xyz, int64_t n, const int32_t *idx, int k, float h, int precision, int max_iter,
+                     float tol, const int32_t *order, float *out_xyz, float *out_n, uint8_t *status,
+                     cudaStream_t st) {
+    const int blocks = (int)((n + kProjThreads - 1) / kProjThreads);
+    float4 *xyz4 = nullptr;
+    MLS_CUDA_TRY(scratch_alloc((void **)&xyz4, (size_t)n * sizeof(float4), st));
+    k_pack_xyz4<<<(int)std::min<int64_t>((n + 255) / 256, 152 * 16), 256, 0, st>>>(xyz, n, xyz4);
+    const size_t smem = (size_t)k * 32 * sizeof(int32_t) * (kProjThreads / 32);
+    if (precision == MLS_PREC_MIXED) {
+        auto kern = k_project<DEG, MLS_PREC_MIXED, true>;
+        MLS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        kern<<<blocks, kProjThreads, smem, st>>>(xyz4, n, idx, k, h, order, out_xyz, out_n, status, max_iter, tol);
+    } else {
+        auto kern = k_project<DEG, MLS_PREC_FP32, true>;
+        MLS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        kern<<<blocks, kProjThreads, smem, st>>>(xyz4, n, idx, k, h, order, out_xyz, out_n, status, max_iter, tol);
+    }
+    count_launches(2);
+    MLS_CUDA_TRY(cudaFreeAsync(xyz4, st));
+    MLS_CUDA_TRY(cudaGetLastError());
+    return MLS_OK;
+}
+
+}  // namespace
+
+int launch_project_levin(const float *xyz, int64_t n, const int32_t *idx, int k, float h, int degree,
+                         int precision, int max_iter, float tol, const int32_t *order, float *out_xyz,
+                         float *out_n, uint8_t *status, cudaStream_t st) {
+    switch (degree) {
+        case 0:
+            return launch_levin_deg<0>(xyz, n, idx, k, h, precision, max_iter, tol, order, out_xyz, out_n, status, st);
+        case 1:
+            return launch_levin_deg<1>(xyz, n, idx, k, h, precision, max_iter, tol, order, out_xyz, out_n, status, st);
+        default:
+            return launch_levin_deg<2>(xyz, n, idx, k, h, precision, max_iter, tol, order, out_xyz, out_n, status, st);
     }
 }
 
@@ -243,11 +286,11 @@ int launch_noalloc(const float *xyz, int64_t n, const int32_t *idx, int k, float
         if (precision == MLS_PREC_MIXED) {
             auto kern = k_project<DEG, MLS_PREC_MIXED>;
             MLS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            kern<<<blocks, kProjThreads, smem, st>>>(xyz4, n, idx, k, h, order, out_xyz, out_n, status);
+            kern<<<blocks, kProjThreads, smem, st>>>(xyz4, n, idx, k, h, order, out_xyz, out_n, status, 1, 0.f);
         } else {
             auto kern = k_project<DEG, MLS_PREC_FP32>;
             MLS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            kern<<<blocks, kProjThreads, smem, st>>>(xyz4, n, idx, k, h, order, out_xyz, out_n, status);
+            kern<<<blocks, kProjThreads, smem, st>>>(xyz4, n, idx, k, h, order, out_xyz, out_n, status, 1, 0.f);
         }
         count_launches(2);
     }

@@ -30,88 +30,123 @@ constexpr float kMixedCondFlag = 1e5f;     // FP32 Cholesky trusted below this c
 // and no lane leaves before the last of them); with G = 1 no lane talks to
 // another.  Returns the status bits; out = the
 // projected point, nf = the normal.
-template <int DEG, int PREC, class Row>
+//
+// LEVIN selects the weights of Eq. 1 taken about q = r + t n instead of r:
+// the plane pass is repeated from t = 0, each time with the weights about
+// the q of the previous plane, until t moves by at most tol * h (at most
+// max_iter passes, else status bit MLS_PT_NOT_CONVERGED); the height fit
+// then uses the weights about the final q.  Points stop after different
+// numbers of passes, so LEVIN takes one lane per point (G = 1).
+template <int DEG, int PREC, bool LEVIN = false, class Row>
 __device__ __forceinline__ uint8_t project_point(const float4 *__restrict__ xyz4, const Row &row, int k, int sub,
                                                  int G, float h, float rx, float ry, float rz, float out[3],
-                                                 float nf[3]) {
+                                                 float nf[3], int max_iter = 1, float tol = 0.f) {
     // exp(-|d|^2 / h^2) = exp2(-|d|^2 * log2(e) / h^2)
     const float neg_scale = -1.4426950408889634f / (h * h);
-
-    // pass 1: weight W, centroid offset m, covariance C (unnormalised)
-    float W = 0.f, mx = 0.f, my = 0.f, mz = 0.f;
-    float C[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-#pragma unroll 4
-    for (int j = sub; j < k; j += G) {
-        const float4 p = __ldg(xyz4 + row(j));
-        const float dx = p.x - rx, dy = p.y - ry, dz = p.z - rz;
-        const float w = exp2f(fmaf(dx, dx, fmaf(dy, dy, dz * dz)) * neg_scale);
-        const float Wn = W + w;
-        const float c = Wn > 0.f ? __fdividef(w, Wn) : 0.f;
-        const float ex = dx - mx, ey = dy - my, ez = dz - mz;
-        mx = fmaf(ex, c, mx);
-        my = fmaf(ey, c, my);
-        mz = fmaf(ez, c, mz);
-        const float f = W * c;
-        const float fx = f * ex, fy = f * ey, fz = f * ez;
-        C[0] = fmaf(fx, ex, C[0]);
-        C[1] = fmaf(fx, ey, C[1]);
-        C[2] = fmaf(fx, ez, C[2]);
-        C[3] = fmaf(fy, ey, C[3]);
-        C[4] = fmaf(fy, ez, C[4]);
-        C[5] = fmaf(fz, ez, C[5]);
-        W = Wn;
-    }
-    for (int s = 1; s < G; s <<= 1) {
-        const float Wo = __shfl_xor_sync(0xffffffffu, W, s);
-        const float mox = __shfl_xor_sync(0xffffffffu, mx, s);
-        const float moy = __shfl_xor_sync(0xffffffffu, my, s);
-        const float moz = __shfl_xor_sync(0xffffffffu, mz, s);
-        float Co[6];
-#pragma unroll
-        for (int c = 0; c < 6; ++c) Co[c] = __shfl_xor_sync(0xffffffffu, C[c], s);
-        const bool lower = (sub & s) == 0;
-        const float Wa = lower ? W : Wo, Wb = lower ? Wo : W;
-        const float max_ = lower ? mx : mox, may = lower ? my : moy, maz = lower ? mz : moz;
-        const float dx = (lower ? mox : mx) - max_, dy = (lower ? moy : my) - may, dz = (lower ? moz : mz) - maz;
-        const float Wn = Wa + Wb;
-        const float fb = Wn > 0.f ? __fdividef(Wb, Wn) : 0.f;
-        const float g = Wa * fb;
-        const float gx = g * dx, gy = g * dy, gz = g * dz;
-        float Cs[6];
-#pragma unroll
-        for (int c = 0; c < 6; ++c) Cs[c] = lower ? C[c] + Co[c] : Co[c] + C[c];
-        C[0] = fmaf(gx, dx, Cs[0]);
-        C[1] = fmaf(gx, dy, Cs[1]);
-        C[2] = fmaf(gx, dz, Cs[2]);
-        C[3] = fmaf(gy, dy, Cs[3]);
-        C[4] = fmaf(gy, dz, Cs[4]);
-        C[5] = fmaf(gz, dz, Cs[5]);
-        mx = fmaf(dx, fb, max_);
-        my = fmaf(dy, fb, may);
-        mz = fmaf(dz, fb, maz);
-        W = Wn;
-    }
     uint8_t st = 0;
+    float W, mx, my, mz;
     float e1f[3], e2f[3];
-    {
-        float lam[3];
-        int deg_flag = frame_from<float>(C, nf, e1f, e2f, lam);
-        // the FP32 eigenvector error grows like eps * l2 / (l1 - l0): in the
-        // mixed form, narrow gaps are solved again in FP64 from the same moments
-        if (PREC == MLS_PREC_MIXED && (!(lam[2] > 0.f) || (lam[1] - lam[0]) < kMixedGapFlag * lam[2])) {
-            double Cd[6], nd[3], e1d[3], e2d[3], ld[3];
-#pragma unroll
-            for (int c = 0; c < 6; ++c) Cd[c] = (double)C[c];
-            deg_flag = frame_from<double>(Cd, nd, e1d, e2d, ld);
-#pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                nf[a] = (float)nd[a];
-                e1f[a] = (float)e1d[a];
-                e2f[a] = (float)e2d[a];
+    // q = r + tq * (qx, qy, qz): the centre of the weights (r unless LEVIN)
+    float tq = 0.f, qx = 0.f, qy = 0.f, qz = 0.f;
+    for (int it = 0;; ++it) {
+        // pass 1: weight W, centroid offset m, covariance C (unnormalised)
+        W = 0.f;
+        mx = 0.f;
+        my = 0.f;
+        mz = 0.f;
+        float C[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll 4
+        for (int j = sub; j < k; j += G) {
+            const float4 p = __ldg(xyz4 + row(j));
+            const float dx = p.x - rx, dy = p.y - ry, dz = p.z - rz;
+            float w;
+            if (LEVIN) {
+                const float ax = fmaf(-tq, qx, dx), ay = fmaf(-tq, qy, dy), az = fmaf(-tq, qz, dz);
+                w = exp2f(fmaf(ax, ax, fmaf(ay, ay, az * az)) * neg_scale);
+            } else {
+                w = exp2f(fmaf(dx, dx, fmaf(dy, dy, dz * dz)) * neg_scale);
             }
-            st |= MLS_PT_FP64_USED;
+            const float Wn = W + w;
+            const float c = Wn > 0.f ? __fdividef(w, Wn) : 0.f;
+            const float ex = dx - mx, ey = dy - my, ez = dz - mz;
+            mx = fmaf(ex, c, mx);
+            my = fmaf(ey, c, my);
+            mz = fmaf(ez, c, mz);
+            const float f = W * c;
+            const float fx = f * ex, fy = f * ey, fz = f * ez;
+            C[0] = fmaf(fx, ex, C[0]);
+            C[1] = fmaf(fx, ey, C[1]);
+            C[2] = fmaf(fx, ez, C[2]);
+            C[3] = fmaf(fy, ey, C[3]);
+            C[4] = fmaf(fy, ez, C[4]);
+            C[5] = fmaf(fz, ez, C[5]);
+            W = Wn;
         }
-        st |= (uint8_t)deg_flag;
+        for (int s = 1; s < G; s <<= 1) {
+            const float Wo = __shfl_xor_sync(0xffffffffu, W, s);
+            const float mox = __shfl_xor_sync(0xffffffffu, mx, s);
+            const float moy = __shfl_xor_sync(0xffffffffu, my, s);
+            const float moz = __shfl_xor_sync(0xffffffffu, mz, s);
+            float Co[6];
+#pragma unroll
+            for (int c = 0; c < 6; ++c) Co[c] = __shfl_xor_sync(0xffffffffu, C[c], s);
+            const bool lower = (sub & s) == 0;
+            const float Wa = lower ? W : Wo, Wb = lower ? Wo : W;
+            const float max_ = lower ? mx : mox, may = lower ? my : moy, maz = lower ? mz : moz;
+            const float dx = (lower ? mox : mx) - max_, dy = (lower ? moy : my) - may, dz = (lower ? moz : mz) - maz;
+            const float Wn = Wa + Wb;
+            const float fb = Wn > 0.f ? __fdividef(Wb, Wn) : 0.f;
+            const float g = Wa * fb;
+            const float gx = g * dx, gy = g * dy, gz = g * dz;
+            float Cs[6];
+#pragma unroll
+            for (int c = 0; c < 6; ++c) Cs[c] = lower ? C[c] + Co[c] : Co[c] + C[c];
+            C[0] = fmaf(gx, dx, Cs[0]);
+            C[1] = fmaf(gx, dy, Cs[1]);
+            C[2] = fmaf(gx, dz, Cs[2]);
+            C[3] = fmaf(gy, dy, Cs[3]);
+            C[4] = fmaf(gy, dz, Cs[4]);
+            C[5] = fmaf(gz, dz, Cs[5]);
+            mx = fmaf(dx, fb, max_);
+            my = fmaf(dy, fb, may);
+            mz = fmaf(dz, fb, maz);
+            W = Wn;
+        }
+        {
+            float lam[3];
+            int deg_flag = frame_from<float>(C, nf, e1f, e2f, lam);
+            // the FP32 eigenvector error grows like eps * l2 / (l1 - l0): in the
+            // mixed form, narrow gaps are solved again in FP64 from the same moments
+            if (PREC == MLS_PREC_MIXED && (!(lam[2] > 0.f) || (lam[1] - lam[0]) < kMixedGapFlag * lam[2])) {
+                double Cd[6], nd[3], e1d[3], e2d[3], ld[3];
+#pragma unroll
+                for (int c = 0; c < 6; ++c) Cd[c] = (double)C[c];
+                deg_flag = frame_from<double>(Cd, nd, e1d, e2d, ld);
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    nf[a] = (float)nd[a];
+                    e1f[a] = (float)e1d[a];
+                    e2f[a] = (float)e2d[a];
+                }
+                st |= MLS_PT_FP64_USED;
+            }
+            st = (uint8_t)((st & ~MLS_PT_PLANE_DEGENERATE) | deg_flag);
+        }
+        if (!LEVIN || (st & MLS_PT_PLANE_DEGENERATE)) break;
+        {
+            // q of this plane: the projection of r onto it
+            const float tn = nf[0] * mx + nf[1] * my + nf[2] * mz;
+            const bool done = it > 0 && fabsf(tn - tq) <= tol * h;
+            tq = tn;
+            qx = nf[0];
+            qy = nf[1];
+            qz = nf[2];
+            if (done) break;
+            if (it + 1 >= max_iter) {
+                st |= MLS_PT_NOT_CONVERGED;
+                break;
+            }
+        }
     }
     out[0] = rx;
     out[1] = ry;
@@ -133,7 +168,13 @@ __device__ __forceinline__ uint8_t project_point(const float4 *__restrict__ xyz4
     for (int j = degenerate ? k : sub; j < k; j += G) {
         const float4 p = __ldg(xyz4 + row(j));
         const float dx = p.x - rx, dy = p.y - ry, dz = p.z - rz;
-        const float w = exp2f(fmaf(dx, dx, fmaf(dy, dy, dz * dz)) * neg_scale);
+        float w;
+        if (LEVIN) {   // about the final q = r + ofs n
+            const float ax = fmaf(-ofs, nf[0], dx), ay = fmaf(-ofs, nf[1], dy), az = fmaf(-ofs, nf[2], dz);
+            w = exp2f(fmaf(ax, ax, fmaf(ay, ay, az * az)) * neg_scale);
+        } else {
+            w = exp2f(fmaf(dx, dx, fmaf(dy, dy, dz * dz)) * neg_scale);
+        }
         const float f = fmaf(nf[2], dz, fmaf(nf[1], dy, fmaf(nf[0], dx, -ofs)));
         const float wf = w * f;
         mom[0] += w;

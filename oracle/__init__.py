@@ -28,12 +28,13 @@ from .build import build_oracle, library_path
 __all__ = [
     "knn_brute", "knn_kdtree", "mean_knn_dist", "project", "project_grad", "project_levin", "fit_height",
     "jacobi_eig", "cholesky_solve", "knn_key", "STATUS_PLANE_DEGENERATE", "STATUS_POLY_SINGULAR",
-    "STATUS_NOT_CONVERGED",
+    "STATUS_NOT_CONVERGED", "STATUS_OUTLIER", "radius_neighbors", "project_rows",
 ]
 
 STATUS_PLANE_DEGENERATE = 1
 STATUS_POLY_SINGULAR = 2
 STATUS_NOT_CONVERGED = 8
+STATUS_OUTLIER = 16
 
 _lib = None
 
@@ -74,6 +75,8 @@ def _load():
                                         _f64p, _f64p]
     lib.oracle_project_levin.argtypes = [_f32p, _i64, _i32p, _int, _dbl, _int, _int, _dbl, _i64p, _i64, _f64p,
                                          _f64p, _u8p, _i32p]
+    lib.oracle_radius_kdtree.argtypes = [_f32p, _i64, ctypes.c_float, _i64p, _i32p, _i32p]
+    lib.oracle_project_rows.argtypes = [_f32p, _i64, _i64p, _i32p, _dbl, _int, _int, _f64p, _f64p, _u8p]
     _lib = lib
     return lib
 
@@ -174,6 +177,42 @@ def project_levin(xyz, idx, h, degree=2, max_iter=100, tol=1e-12, queries=None):
     if rc != 0:
         raise ValueError(f"oracle_project_levin failed ({rc})")
     return out, nrm, st, it
+
+
+def radius_neighbors(xyz, R):
+    """Radius-R neighbourhoods (key <= fl(R*R), self included, (key, index)
+    order) as CSR: (offsets int64 (n + 1), rows int32)."""
+    xyz = _xyz(xyz)
+    n = xyz.shape[0]
+    R2 = np.float32(np.float32(R) * np.float32(R))
+    cnt = np.empty(n, np.int32)
+    rc = _load().oracle_radius_kdtree(_p(xyz, _f32p), n, float(R2), None, None, _p(cnt, _i32p))
+    if rc != 0:
+        raise ValueError(f"oracle_radius_kdtree failed ({rc})")
+    off = np.zeros(n + 1, np.int64)
+    np.cumsum(cnt, out=off[1:])
+    rows = np.empty(int(off[-1]), np.int32)
+    rc = _load().oracle_radius_kdtree(_p(xyz, _f32p), n, float(R2), _p(off, _i64p), _p(rows, _i32p), _p(cnt, _i32p))
+    if rc != 0:
+        raise ValueError(f"oracle_radius_kdtree failed ({rc})")
+    return off, rows
+
+
+def project_rows(xyz, offsets, rows, h, degree=2, min_neighbors=3):
+    """Projection over CSR neighbourhoods with the outlier rule (status 16).
+    Returns (xyz', normal, status)."""
+    xyz = _xyz(xyz)
+    n = xyz.shape[0]
+    off = np.ascontiguousarray(offsets, np.int64)
+    rows = np.ascontiguousarray(rows, np.int32)
+    out = np.empty((n, 3), np.float64)
+    nrm = np.empty((n, 3), np.float64)
+    st = np.empty(n, np.uint8)
+    rc = _load().oracle_project_rows(_p(xyz, _f32p), n, _p(off, _i64p), _p(rows, _i32p), float(h), int(degree),
+                                     int(min_neighbors), _p(out, _f64p), _p(nrm, _f64p), _p(st, _u8p))
+    if rc != 0:
+        raise ValueError(f"oracle_project_rows failed ({rc})")
+    return out, nrm, st
 
 
 def project_grad(xyz, idx, h, degree, gout_xyz, gout_normal=None, queries=None):

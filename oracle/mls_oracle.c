@@ -919,3 +919,133 @@ int oracle_project_levin(const float *xyz, int64_t n, const int32_t *idx, int k,
     free(w);
     return 0;
 }
+
+/* ------------------------------------------------------------------------- */
+/* Radius neighbourhoods (Sec. 1.4, Sec. 2.2, Sec. 3.3)                       */
+/* ------------------------------------------------------------------------- */
+
+#define ST_OUTLIER 16
+
+typedef struct {
+    kv_t *a;
+    int64_t size, cap;
+} kvlist;
+
+static int kvlist_push(kvlist *l, kv_t v)
+{
+    if (l->size == l->cap) {
+        int64_t c = l->cap ? 2 * l->cap : 64;
+        kv_t *p = (kv_t *)realloc(l->a, sizeof(kv_t) * (size_t)c);
+        if (!p) return 0;
+        l->a = p;
+        l->cap = c;
+    }
+    l->a[l->size++] = v;
+    return 1;
+}
+
+/* Every point of the subtree with key <= R2 (the same FP32 key as the kNN). */
+static int kd_range(const kd_tree *t, int64_t id, const float *q, float R2, kvlist *out)
+{
+    const kd_node *nd = &t->nodes[id];
+    double d2 = 0.0;
+    for (int a = 0; a < 3; ++a) {
+        double x = (double)q[a], g = 0.0;
+        if (x < nd->lo[a]) g = nd->lo[a] - x;
+        else if (x > nd->hi[a]) g = x - nd->hi[a];
+        d2 += g * g;
+    }
+    if (d2 * (1.0 - 1e-6) > (double)R2) return 1;
+    if (nd->left < 0) {
+        for (int64_t s = nd->begin; s < nd->end; ++s) {
+            int32_t j = t->perm[s];
+            kv_t v = {oracle_knn_key(t->xyz + 3 * (int64_t)j, q), j};
+            if (v.key <= R2 && !kvlist_push(out, v)) return 0;
+        }
+        return 1;
+    }
+    return kd_range(t, nd->left, q, R2, out) && kd_range(t, nd->right, q, R2, out);
+}
+
+/* The radius-R neighbourhood of every point: all j with key(i, j) <= R2,
+ * the point itself included, ordered by (key, index).  out_count[i] always;
+ * when offsets and out_rows are given, row i is written at offsets[i]
+ * (offsets[i + 1] - offsets[i] must equal the count). */
+int oracle_radius_kdtree(const float *xyz, int64_t n, float R2, const int64_t *offsets, int32_t *out_rows,
+                         int32_t *out_count)
+{
+    if (n < 1 || !(R2 >= 0.0f)) return -1;
+    kd_tree t;
+    t.xyz = xyz;
+    t.perm = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    t.cap = n / 2 + 16;
+    t.nodes = (kd_node *)malloc(sizeof(kd_node) * (size_t)t.cap);
+    t.n_nodes = 0;
+    kvlist l = {NULL, 0, 0};
+    if (!t.perm || !t.nodes) {
+        free(t.perm);
+        free(t.nodes);
+        return -2;
+    }
+    for (int64_t i = 0; i < n; ++i) t.perm[i] = (int32_t)i;
+    kd_build(&t, 0, n);
+    int rc = 0;
+    for (int64_t i = 0; i < n && rc == 0; ++i) {
+        l.size = 0;
+        if (!kd_range(&t, 0, xyz + 3 * i, R2, &l)) {
+            rc = -2;
+            break;
+        }
+        qsort(l.a, (size_t)l.size, sizeof(kv_t), kv_cmp);
+        out_count[i] = (int32_t)l.size;
+        if (offsets && out_rows) {
+            if (offsets[i + 1] - offsets[i] != l.size) {
+                rc = -3;
+                break;
+            }
+            for (int64_t c = 0; c < l.size; ++c) out_rows[offsets[i] + c] = l.a[c].idx;
+        }
+    }
+    free(l.a);
+    free(t.perm);
+    free(t.nodes);
+    return rc;
+}
+
+/* The projection over variable neighbourhoods (row i = rows[offsets[i] ..
+ * offsets[i + 1])), with Sec. 3.3's outlier rule: a point with fewer than
+ * min_neighbors other points in its neighbourhood is not projected (status
+ * bit 16, output = the point, to be dropped from the result).  Everything else
+ * as oracle_project. */
+int oracle_project_rows(const float *xyz, int64_t n, const int64_t *offsets, const int32_t *rows, double h,
+                        int degree, int min_neighbors, double *out_xyz, double *out_normal, uint8_t *out_status)
+{
+    if (n < 1 || !(h > 0.0) || degree < 0 || degree > 2) return -1;
+    int64_t kmax = 1;
+    for (int64_t i = 0; i < n; ++i)
+        if (offsets[i + 1] - offsets[i] > kmax) kmax = offsets[i + 1] - offsets[i];
+    point_state st;
+    if (!alloc_state(&st, (int)kmax)) {
+        free_state(&st);
+        return -2;
+    }
+    for (int64_t i = 0; i < n; ++i) {
+        int k = (int)(offsets[i + 1] - offsets[i]);
+        if (k - 1 < min_neighbors) {
+            for (int a = 0; a < 3; ++a) {
+                out_xyz[3 * i + a] = (double)xyz[3 * i + a];
+                if (out_normal) out_normal[3 * i + a] = 0.0;
+            }
+            if (out_status) out_status[i] = ST_OUTLIER;
+            continue;
+        }
+        project_point(xyz, rows + offsets[i], k, h, degree, i, &st);
+        for (int a = 0; a < 3; ++a) {
+            out_xyz[3 * i + a] = st.out[a];
+            if (out_normal) out_normal[3 * i + a] = st.nrm[a];
+        }
+        if (out_status) out_status[i] = (uint8_t)st.status;
+    }
+    free_state(&st);
+    return 0;
+}

@@ -307,6 +307,25 @@ def run_ours(args):
         b.synchronize()
         lv_ms.append(a.elapsed_time(b))
     lv_not_conv = float(((lv[2] & 8) != 0).float().mean().item())
+
+    # the paper's own neighbourhood: every point within R (about 32 on the
+    # torus surface), the projection over those rows, the outliers dropped
+    R_ball = 0.008
+    rd_ms = []
+    for rep in range(4):
+        flush.zero_()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        off_r, rows_r, _ = capi.mls_radius_neighbors(grid, R_ball)
+        _, _, st_r = capi.mls_project_rows(x, off_r, rows_r, R_ball, 2, "mixed", 3, order=order)
+        kept_r = capi.mls_compact(st_r, capi.MLS_PT_OUTLIER)
+        b.record(stream)
+        b.synchronize()
+        if rep:
+            rd_ms.append(a.elapsed_time(b))
+    rd_mean_nb = float(off_r[-1].item()) / n_pts
+    rd_kept = int(kept_r.shape[0])
     grid.close()
     if rank != 0:
         if world > 1:
@@ -369,6 +388,10 @@ def run_ours(args):
                   "step": "mls_project_levin (weights about q, fixed point from q = r, tol 1e-6 h, <= 32 passes), "
                           "mixed, degree 2, same rows and h",
                   "not_converged_frac": lv_not_conv},
+        "radius": {"ms": float(np.median(rd_ms)), "points_per_s": n_pts / (float(np.median(rd_ms)) * 1e-3),
+                   "step": f"mls_radius_count + mls_radius_rows + mls_project_rows + mls_compact, R = h = {R_ball}, "
+                           "mixed, degree 2, outliers (< 3 neighbours) dropped; on the already built grid",
+                   "mean_neighbours": rd_mean_nb, "kept": rd_kept},
         "e2e": {"value": e2e_value, "unit": "points/s", "h2d_bytes_per_step": n_pts * 12,
                 "d2h_bytes_per_step": n_pts * (12 + 12 + 1 + 12)},
         "gpu_launches": int(launches),

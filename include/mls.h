@@ -75,7 +75,8 @@ enum mls_point_status {
     MLS_PT_PLANE_DEGENERATE = 1,
     MLS_PT_POLY_SINGULAR = 2,
     MLS_PT_FP64_USED = 4,
-    MLS_PT_NOT_CONVERGED = 8   /* mls_project_levin: t still moving after max_iter passes */
+    MLS_PT_NOT_CONVERGED = 8,  /* mls_project_levin: t still moving after max_iter passes */
+    MLS_PT_OUTLIER = 16        /* mls_project_rows: too few neighbours, not projected */
 };
 
 #define MLS_MAX_K 64
@@ -170,6 +171,40 @@ int mls_project(const float *d_xyz, int64_t n, const int32_t *d_idx, int k, floa
 int mls_project_levin(const float *d_xyz, int64_t n, const int32_t *d_idx, int k, float h, int degree,
                       int precision, int max_iter, float tol, const int32_t *d_order, float *d_out_xyz,
                       float *d_out_normal, uint8_t *d_status, mls_stream stream);
+
+/*
+ * Radius-R neighbourhoods (Sec. 1.4: the points within radius R of the
+ * query; Sec. 2.2) and the projection over them with Sec. 3.3's outlier rule.
+ * The neighbourhood of point i is every j with key(i, j) <= fl(R * R), the
+ * same FP32 key as mls_knn, the point itself included, ordered by (key,
+ * index): bit-exact like the kNN rows.
+ *
+ * mls_radius_count: d_count (n int32, original order) = size of each
+ *   neighbourhood; with d_offsets (n + 1 int64) non-NULL also the CSR
+ *   offsets (exclusive prefix sum; d_offsets[n] = total).  Asynchronous.
+ * mls_radius_rows: writes row i at d_rows[d_offsets[i] ..] (and the keys to
+ *   d_keys when non-NULL).  At most MLS_MAX_RADIUS_NB neighbours per point:
+ *   synchronises `stream` and returns MLS_ERR_K_TOO_LARGE (rows of such
+ *   points unwritten) when any neighbourhood is larger.
+ * mls_project_rows: the projection (weights about the point, as mls_project)
+ *   over CSR neighbourhoods (d_offsets n + 1 int64, d_rows int32, rows of any
+ *   length); a point with fewer than min_neighbors (>= 0) OTHER points in its
+ *   row is an outlier: not projected, output = the point, normal = 0, status
+ *   MLS_PT_OUTLIER.  precision MLS_PREC_FP32 or MLS_PREC_MIXED.
+ * mls_compact: d_kept (capacity n int32) = the indices i with
+ *   (d_status[i] & mask) == 0 in increasing order; *d_num_kept (device int64)
+ *   = their number (the paper's result drops the outliers: mask =
+ *   MLS_PT_OUTLIER).
+ */
+#define MLS_MAX_RADIUS_NB 128
+int mls_radius_count(const mls_grid *g, float R, int32_t *d_count, int64_t *d_offsets, mls_stream stream);
+int mls_radius_rows(const mls_grid *g, float R, const int64_t *d_offsets, int32_t *d_rows, float *d_keys,
+                    mls_stream stream);
+int mls_project_rows(const float *d_xyz, int64_t n, const int64_t *d_offsets, const int32_t *d_rows, float h,
+                     int degree, int precision, int min_neighbors, const int32_t *d_order, float *d_out_xyz,
+                     float *d_out_normal, uint8_t *d_status, mls_stream stream);
+int mls_compact(const uint8_t *d_status, int64_t n, int mask, int32_t *d_kept, int64_t *d_num_kept,
+                mls_stream stream);
 
 /*
  * mls_project_noalloc -- mls_project for callers that must not allocate

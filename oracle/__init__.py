@@ -76,7 +76,7 @@ def _load():
     lib.oracle_project_levin.argtypes = [_f32p, _i64, _i32p, _int, _dbl, _int, _int, _dbl, _i64p, _i64, _f64p,
                                          _f64p, _u8p, _i32p]
     lib.oracle_radius_kdtree.argtypes = [_f32p, _i64, ctypes.c_float, _i64p, _i32p, _i32p]
-    lib.oracle_project_rows.argtypes = [_f32p, _i64, _i64p, _i32p, _dbl, _int, _int, _f64p, _f64p, _u8p]
+    lib.oracle_project_rows.argtypes = [_f32p, _i64, _i64p, _i32p, _dbl, _int, _int, _f64p, _f64p, _u8p, _f64p]
     _lib = lib
     return lib
 
@@ -200,7 +200,8 @@ def radius_neighbors(xyz, R):
 
 def project_rows(xyz, offsets, rows, h, degree=2, min_neighbors=3):
     """Projection over CSR neighbourhoods with the outlier rule (status 16).
-    Returns (xyz', normal, status)."""
+    Returns (xyz', normal, status, diag) as oracle.project (diag 0 for
+    outliers)."""
     xyz = _xyz(xyz)
     n = xyz.shape[0]
     off = np.ascontiguousarray(offsets, np.int64)
@@ -208,11 +209,13 @@ def project_rows(xyz, offsets, rows, h, degree=2, min_neighbors=3):
     out = np.empty((n, 3), np.float64)
     nrm = np.empty((n, 3), np.float64)
     st = np.empty(n, np.uint8)
+    diag = np.empty((n, 5), np.float64)
     rc = _load().oracle_project_rows(_p(xyz, _f32p), n, _p(off, _i64p), _p(rows, _i32p), float(h), int(degree),
-                                     int(min_neighbors), _p(out, _f64p), _p(nrm, _f64p), _p(st, _u8p))
+                                     int(min_neighbors), _p(out, _f64p), _p(nrm, _f64p), _p(st, _u8p),
+                                     _p(diag, _f64p))
     if rc != 0:
         raise ValueError(f"oracle_project_rows failed ({rc})")
-    return out, nrm, st
+    return out, nrm, st, diag
 
 
 def project_grad(xyz, idx, h, degree, gout_xyz, gout_normal=None, queries=None):

@@ -1015,10 +1015,11 @@ int oracle_radius_kdtree(const float *xyz, int64_t n, float R2, const int64_t *o
 /* The projection over variable neighbourhoods (row i = rows[offsets[i] ..
  * offsets[i + 1])), with Sec. 3.3's outlier rule: a point with fewer than
  * min_neighbors other points in its neighbourhood is not projected (status
- * bit 16, output = the point, to be dropped from the result).  Everything else
- * as oracle_project. */
+ * bit 16, output = the point, to be dropped from the result; diagnostics 0).
+ * Everything else as oracle_project. */
 int oracle_project_rows(const float *xyz, int64_t n, const int64_t *offsets, const int32_t *rows, double h,
-                        int degree, int min_neighbors, double *out_xyz, double *out_normal, uint8_t *out_status)
+                        int degree, int min_neighbors, double *out_xyz, double *out_normal, uint8_t *out_status,
+                        double *out_diag)
 {
     if (n < 1 || !(h > 0.0) || degree < 0 || degree > 2) return -1;
     int64_t kmax = 1;
@@ -1037,6 +1038,8 @@ int oracle_project_rows(const float *xyz, int64_t n, const int64_t *offsets, con
                 if (out_normal) out_normal[3 * i + a] = 0.0;
             }
             if (out_status) out_status[i] = ST_OUTLIER;
+            if (out_diag)
+                for (int c = 0; c < 5; ++c) out_diag[5 * i + c] = 0.0;
             continue;
         }
         project_point(xyz, rows + offsets[i], k, h, degree, i, &st);
@@ -1045,6 +1048,13 @@ int oracle_project_rows(const float *xyz, int64_t n, const int64_t *offsets, con
             if (out_normal) out_normal[3 * i + a] = st.nrm[a];
         }
         if (out_status) out_status[i] = (uint8_t)st.status;
+        if (out_diag) {
+            out_diag[5 * i + 0] = st.lam[0];
+            out_diag[5 * i + 1] = st.lam[1];
+            out_diag[5 * i + 2] = st.lam[2];
+            out_diag[5 * i + 3] = st.cond;
+            out_diag[5 * i + 4] = st.W;
+        }
     }
     free_state(&st);
     return 0;

@@ -17,7 +17,8 @@ from .build import library_path
 
 __all__ = [
     "MLSError", "Grid", "lib", "mls_build_grid", "mls_grid_destroy", "mls_grid_size", "mls_grid_order",
-    "mls_knn", "mls_project", "mls_project_levin", "mls_project_backward", "mls_mean_knn_dist", "mls_status_str", "mls_last_error", "mls_kernel_launches", "mls_release_scratch",
+    "mls_knn", "mls_project", "mls_project_levin", "mls_project_backward", "mls_radius_neighbors",
+    "mls_project_rows", "mls_compact", "mls_mean_knn_dist", "mls_status_str", "mls_last_error", "mls_kernel_launches", "mls_release_scratch",
     "Batch", "mls_batch_create", "mls_batch_destroy", "mls_batch_set_shape", "mls_batch_get_shape",
     "mls_project_batched", "mls_batch_capture", "mls_batch_replay", "mls_batch_autotune", "mls_batch_tune_results",
     "PRECISION", "MLS_MAX_K", "MLS_PT_OK", "MLS_PT_PLANE_DEGENERATE", "MLS_PT_POLY_SINGULAR",
@@ -29,6 +30,8 @@ MLS_NOALLOC_MAX_POINTS = 262144
 PRECISION = {"fp32": 0, "mixed": 1, "fp64": 2}
 MLS_PT_OK, MLS_PT_PLANE_DEGENERATE, MLS_PT_POLY_SINGULAR, MLS_PT_FP64_USED = 0, 1, 2, 4
 MLS_PT_NOT_CONVERGED = 8
+MLS_PT_OUTLIER = 16
+MLS_MAX_RADIUS_NB = 128
 
 _vp = ctypes.c_void_p
 _i64 = ctypes.c_int64
@@ -45,6 +48,10 @@ _SIGNATURES = [
     ("mls_project", _int, [_vp, _i64, _vp, _int, _flt, _int, _int, _vp, _vp, _vp, _vp, _vp]),
     ("mls_project_noalloc", _int, [_vp, _i64, _vp, _int, _flt, _int, _int, _vp, _vp, _vp, _vp, _vp]),
     ("mls_project_levin", _int, [_vp, _i64, _vp, _int, _flt, _int, _int, _int, _flt, _vp, _vp, _vp, _vp, _vp]),
+    ("mls_radius_count", _int, [_vp, _flt, _vp, _vp, _vp]),
+    ("mls_radius_rows", _int, [_vp, _flt, _vp, _vp, _vp, _vp]),
+    ("mls_project_rows", _int, [_vp, _i64, _vp, _vp, _flt, _int, _int, _int, _vp, _vp, _vp, _vp, _vp]),
+    ("mls_compact", _int, [_vp, _i64, _int, _vp, _vp, _vp]),
     ("mls_project_backward", _int, [_vp, _i64, _vp, _int, _flt, _int, _int, _vp, _vp, _vp, _vp, _vp, _vp]),
     ("mls_mean_knn_dist", _int, [_vp, _i64, _vp, _int, _vp, _vp]),
     ("mls_batch_create", _int, [_int, _vp, _vp, ctypes.POINTER(_vp)]),
@@ -266,6 +273,53 @@ def mls_project_levin(xyz: torch.Tensor, idx: torch.Tensor, h: float, degree: in
                                  _ptr(out_status), _stream(stream))
     _check("mls_project_levin", rc)
     return out_xyz, out_normal, out_status
+
+
+def mls_radius_neighbors(grid: Grid, R: float, with_key: bool = False, stream=None):
+    """CSR radius-R neighbourhoods of the grid's points: (offsets int64 (n + 1),
+    rows int32, keys float32 or None).  Reads the total back (one sync)."""
+    n = grid.n
+    dev = grid.xyz.device
+    count = torch.empty(n, dtype=torch.int32, device=dev)
+    offsets = torch.empty(n + 1, dtype=torch.int64, device=dev)
+    _check("mls_radius_count", lib().mls_radius_count(grid.handle, float(R), _ptr(count), _ptr(offsets),
+                                                        _stream(stream)))
+    total = int(offsets[n].item())
+    rows = torch.empty(max(total, 1), dtype=torch.int32, device=dev)
+    keys = torch.empty(max(total, 1), dtype=torch.float32, device=dev) if with_key else None
+    _check("mls_radius_rows", lib().mls_radius_rows(grid.handle, float(R), _ptr(offsets), _ptr(rows), _ptr(keys),
+                                                      _stream(stream)))
+    return offsets, rows[:total], (keys[:total] if keys is not None else None)
+
+
+def mls_project_rows(xyz: torch.Tensor, offsets: torch.Tensor, rows: torch.Tensor, h: float, degree: int = 2,
+                     precision: str = "mixed", min_neighbors: int = 3, order: torch.Tensor | None = None,
+                     stream=None):
+    """Projection over CSR neighbourhoods with the outlier rule; returns
+    (xyz', normal, status) for every point (outliers unmoved, status 16)."""
+    _need(xyz, "xyz", torch.float32)
+    n = xyz.shape[0]
+    _need(offsets, "offsets", torch.int64, (n + 1,))
+    _need(rows, "rows", torch.int32)
+    if order is not None:
+        _need(order, "order", torch.int32, (n,))
+    out = torch.empty_like(xyz)
+    nrm = torch.empty_like(xyz)
+    st = torch.empty(n, dtype=torch.uint8, device=xyz.device)
+    rc = lib().mls_project_rows(_ptr(xyz), n, _ptr(offsets), _ptr(rows), float(h), int(degree), PRECISION[precision],
+                                int(min_neighbors), _ptr(order), _ptr(out), _ptr(nrm), _ptr(st), _stream(stream))
+    _check("mls_project_rows", rc)
+    return out, nrm, st
+
+
+def mls_compact(status: torch.Tensor, mask: int = MLS_PT_OUTLIER, stream=None) -> torch.Tensor:
+    """Indices of the entries with (status & mask) == 0 (one sync for the count)."""
+    _need(status, "status", torch.uint8)
+    n = status.shape[0]
+    kept = torch.empty(n, dtype=torch.int32, device=status.device)
+    num = torch.empty(1, dtype=torch.int64, device=status.device)
+    _check("mls_compact", lib().mls_compact(_ptr(status), n, int(mask), _ptr(kept), _ptr(num), _stream(stream)))
+    return kept[: int(num.item())]
 
 
 def mls_project_backward(xyz: torch.Tensor, idx: torch.Tensor, h: float, grad_out_xyz: torch.Tensor,

@@ -14,6 +14,13 @@ void free_grid_buffers(mls_grid *g);
 int launch_knn(const mls_grid *grid, int k, int32_t *idx, float *key, cudaStream_t st);
 int launch_project(const float *xyz, int64_t n, const int32_t *idx, int k, float h, int degree, int precision,
                    const int32_t *order, float *out_xyz, float *out_n, uint8_t *status, cudaStream_t st);
+int launch_radius(const mls_grid *grid, float R2, int32_t *count, const int64_t *offsets, int32_t *rows,
+                  float *keys, int *overflow, cudaStream_t st);
+int launch_project_rows(const float *xyz, int64_t n, const int64_t *off, const int32_t *rows, float h, int degree,
+                        int precision, int min_nb, const int32_t *order, float *out_xyz, float *out_n,
+                        uint8_t *status, cudaStream_t st);
+int device_exclusive_scan64(const int32_t *in, int64_t *out, int64_t n, cudaStream_t st);
+int device_compact(const uint8_t *status, int64_t n, int mask, int32_t *kept, int64_t *num, cudaStream_t st);
 int launch_project_levin(const float *xyz, int64_t n, const int32_t *idx, int k, float h, int degree,
                          int precision, int max_iter, float tol, const int32_t *order, float *out_xyz,
                          float *out_n, uint8_t *status, cudaStream_t st);
@@ -204,6 +211,77 @@ int mls_project(const float *d_xyz, int64_t n, const int32_t *d_idx, int k, floa
         return set_error(MLS_ERR_INVALID_ARG, "mls_project: output aliases the input");
     return mls::launch_project(d_xyz, n, d_idx, k, h, degree, precision, d_order, d_out_xyz, d_out_normal,
                                d_status, (cudaStream_t)stream);
+}
+
+static int check_radius(const mls_grid *g, float R, const char *fn) {
+    if (!g || g->n < 1) return set_error(MLS_ERR_INVALID_ARG, "%s: empty or null grid", fn);
+    if (!(R >= 0.0f) || !std::isfinite(R)) return set_error(MLS_ERR_INVALID_ARG, "%s: R = %g", fn, (double)R);
+    return MLS_OK;
+}
+
+int mls_radius_count(const mls_grid *g, float R, int32_t *d_count, int64_t *d_offsets, mls_stream stream) {
+    mls::g_last_error[0] = 0;
+    int rc = check_radius(g, R, "mls_radius_count");
+    if (rc != MLS_OK) return rc;
+    if (!d_count) return set_error(MLS_ERR_INVALID_ARG, "mls_radius_count: null count");
+    cudaStream_t st = (cudaStream_t)stream;
+    rc = mls::launch_radius(g, R * R, d_count, nullptr, nullptr, nullptr, nullptr, st);
+    if (rc != MLS_OK || !d_offsets) return rc;
+    return mls::device_exclusive_scan64(d_count, d_offsets, g->n, st);
+}
+
+int mls_radius_rows(const mls_grid *g, float R, const int64_t *d_offsets, int32_t *d_rows, float *d_keys,
+                    mls_stream stream) {
+    mls::g_last_error[0] = 0;
+    int rc = check_radius(g, R, "mls_radius_rows");
+    if (rc != MLS_OK) return rc;
+    if (!d_offsets || !d_rows) return set_error(MLS_ERR_INVALID_ARG, "mls_radius_rows: null pointer");
+    cudaStream_t st = (cudaStream_t)stream;
+    int *overflow = nullptr;
+    MLS_CUDA_TRY(mls::scratch_alloc((void **)&overflow, sizeof(int), st));
+    MLS_CUDA_TRY(cudaMemsetAsync(overflow, 0, sizeof(int), st));
+    rc = mls::launch_radius(g, R * R, nullptr, d_offsets, d_rows, d_keys, overflow, st);
+    int worst = 0;
+    if (rc == MLS_OK) {
+        cudaError_t e = cudaMemcpyAsync(&worst, overflow, sizeof(int), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) rc = set_error(MLS_ERR_CUDA, "mls_radius_rows: %s", cudaGetErrorString(e));
+    }
+    cudaFreeAsync(overflow, st);
+    if (rc != MLS_OK) return rc;
+    if (worst > 0)
+        return set_error(MLS_ERR_K_TOO_LARGE, "mls_radius_rows: a neighbourhood holds %d points, more than %d",
+                         worst, MLS_MAX_RADIUS_NB);
+    return MLS_OK;
+}
+
+int mls_project_rows(const float *d_xyz, int64_t n, const int64_t *d_offsets, const int32_t *d_rows, float h,
+                     int degree, int precision, int min_neighbors, const int32_t *d_order, float *d_out_xyz,
+                     float *d_out_normal, uint8_t *d_status, mls_stream stream) {
+    mls::g_last_error[0] = 0;
+    if (!d_xyz || !d_offsets || !d_rows || !d_out_xyz)
+        return set_error(MLS_ERR_INVALID_ARG, "mls_project_rows: null pointer");
+    if (n < 1) return set_error(MLS_ERR_INVALID_ARG, "mls_project_rows: n = %lld < 1", (long long)n);
+    if (n > 0x7fffffffLL) return set_error(MLS_ERR_TOO_LARGE, "mls_project_rows: n = %lld", (long long)n);
+    if (!(h > 0.0f) || !std::isfinite(h))
+        return set_error(MLS_ERR_INVALID_ARG, "mls_project_rows: h = %g must be finite and > 0", (double)h);
+    if (degree < 0 || degree > 2)
+        return set_error(MLS_ERR_UNSUPPORTED_DEGREE, "mls_project_rows: degree = %d not in {0, 1, 2}", degree);
+    if (precision != MLS_PREC_FP32 && precision != MLS_PREC_MIXED)
+        return set_error(MLS_ERR_INVALID_ARG, "mls_project_rows: precision = %d (FP32 or mixed)", precision);
+    if (min_neighbors < 0) return set_error(MLS_ERR_INVALID_ARG, "mls_project_rows: min_neighbors = %d", min_neighbors);
+    if ((const void *)d_out_xyz == (const void *)d_xyz)
+        return set_error(MLS_ERR_INVALID_ARG, "mls_project_rows: output aliases the input");
+    return mls::launch_project_rows(d_xyz, n, d_offsets, d_rows, h, degree, precision, min_neighbors, d_order,
+                                    d_out_xyz, d_out_normal, d_status, (cudaStream_t)stream);
+}
+
+int mls_compact(const uint8_t *d_status, int64_t n, int mask, int32_t *d_kept, int64_t *d_num_kept,
+                mls_stream stream) {
+    mls::g_last_error[0] = 0;
+    if (!d_status || !d_kept || !d_num_kept) return set_error(MLS_ERR_INVALID_ARG, "mls_compact: null pointer");
+    if (n < 1 || n > 0x7fffffffLL) return set_error(MLS_ERR_INVALID_ARG, "mls_compact: n = %lld", (long long)n);
+    return mls::device_compact(d_status, n, mask, d_kept, d_num_kept, (cudaStream_t)stream);
 }
 
 int mls_project_levin(const float *d_xyz, int64_t n, const int32_t *d_idx, int k, float h, int degree,

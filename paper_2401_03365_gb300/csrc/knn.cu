@@ -334,7 +334,7 @@ __device__ float rank_and_write(WarpBuf &wb, int S, float scale, int k, int lane
         if (rank < k) {
             out_idx[(int64_t)qi * k + rank] = (int32_t)(uint32_t)v;
             if (out_key) out_key[(int64_t)qi * k + rank] = key;
-            wb.nb[rank] = wb.tpos[p];
+            if (rank < 64) wb.nb[rank] = wb.tpos[p];     // the radius rows can be longer than a kNN row
             if (rank == k - 1) wb.kth = key;
         }
     }
@@ -671,6 +671,52 @@ __global__ void __launch_bounds__(kChainThreads) k_knn_sparse(GridView g, int k,
     }
 }
 
+// ---- radius neighbourhoods (Sec. 1.4: the points within radius R) --------
+//
+// One warp per query, runs of 32 consecutive queries in Morton order per
+// warp (the cube of cells stays cached between them).  Every point with key
+// <= R2 is kept, the same cube search and culling as the kNN with the fixed
+// bound R2; ROWS = false counts them, ROWS = true ranks them by (key, index)
+// into the query's CSR row.  More than kCap in a row is reported through
+// *overflow (the largest count seen) and the row is left unwritten.
+
+template <bool ROWS>
+__global__ void __launch_bounds__(kChainThreads) k_radius(GridView g, float R2, int32_t *__restrict__ count,
+                                                         const int64_t *__restrict__ offsets,
+                                                         int32_t *__restrict__ rows, float *__restrict__ keys,
+                                                         int *__restrict__ overflow) {
+    __shared__ WarpBuf bufs[kChainWarps];
+    const int lane = threadIdx.x & 31;
+    WarpBuf &wb = bufs[threadIdx.x >> 5];
+    const float eps2 = 2.0f * g.frame.eps;
+    const float reach = sqrtf(R2) * kGrow * kGrow + eps2;
+    int lev = g.base_level;
+    while (lev < g.top_level && !(2.0f * g.side[lev] > reach)) ++lev;
+    const float lim = (reach + eps2) * kGrow;
+    const float lim2 = lim * lim;
+    const float scale = R2 > 0.f ? 32.0f / R2 : 0.f;
+    const int64_t n_warps = (int64_t)gridDim.x * kChainWarps;
+    Cube cb;
+    for (int64_t run = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; run * 32 < g.n; run += n_warps) {
+        const int64_t end = min((int64_t)g.n, run * 32 + 32);
+        for (int64_t sp = run * 32; sp < end; ++sp) {
+            const float4 q = __ldg(g.pts + sp);
+            const uint64_t key0 = __ldg(g.keys + sp);
+            const uint32_t c0[3] = {compact3(key0), compact3(key0 >> 1), compact3(key0 >> 2)};
+            load_cube(g, lev, c0, cb, lane);
+            const int S = scan_keep<false>(g, cb, wb, q, lim2, R2, scale, lane);
+            const int64_t qi = (int64_t)__float_as_int(q.w);
+            if (!ROWS) {
+                if (lane == 0) count[qi] = S;
+            } else if (S > kCap) {
+                if (lane == 0) atomicMax(overflow, S);
+            } else {
+                rank_and_write(wb, S, scale, S, lane, 0, rows + offsets[qi], keys ? keys + offsets[qi] : nullptr);
+            }
+        }
+    }
+}
+
 }  // namespace
 
 int launch_knn(const mls_grid *grid, int k, int32_t *idx, float *key, cudaStream_t st) {
@@ -696,6 +742,31 @@ int launch_knn(const mls_grid *grid, int k, int32_t *idx, float *key, cudaStream
     chain<<<blocks, kChainThreads, 0, st>>>(grid->view, k, grid->work, idx, key);
     sparse<<<sms * per_sm, kChainThreads, 0, st>>>(grid->view, k, grid->work, idx, key);
     count_launches(2);
+    MLS_CUDA_TRY(cudaGetLastError());
+    return MLS_OK;
+}
+
+}  // namespace mls
+
+namespace mls {
+
+int launch_radius(const mls_grid *grid, float R2, int32_t *count, const int64_t *offsets, int32_t *rows,
+                  float *keys, int *overflow, cudaStream_t st) {
+    int dev = 0, sms = 152;
+    MLS_CUDA_TRY(cudaGetDevice(&dev));
+    MLS_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int64_t runs = (grid->n + 31) / 32;
+    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)sms * 4, (runs + kChainWarps - 1) / kChainWarps));
+    if (rows) {
+        MLS_CUDA_TRY(cudaFuncSetAttribute(k_radius<true>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                          cudaSharedmemCarveoutMaxShared));
+        k_radius<true><<<blocks, kChainThreads, 0, st>>>(grid->view, R2, count, offsets, rows, keys, overflow);
+    } else {
+        MLS_CUDA_TRY(cudaFuncSetAttribute(k_radius<false>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                          cudaSharedmemCarveoutMaxShared));
+        k_radius<false><<<blocks, kChainThreads, 0, st>>>(grid->view, R2, count, offsets, rows, keys, overflow);
+    }
+    count_launches(1);
     MLS_CUDA_TRY(cudaGetLastError());
     return MLS_OK;
 }

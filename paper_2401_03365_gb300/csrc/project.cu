@@ -65,6 +65,40 @@ __global__ void __launch_bounds__(kProjThreads) k_project(const float4 *__restri
     if (status) status[i] = st;
 }
 
+// Variable neighbourhoods (CSR rows, e.g. the radius-R sets of Sec. 1.4),
+// one thread per point, rows read straight from global memory.  A point with
+// fewer than min_nb other points in its row is an outlier (Sec. 3.3): not
+// projected, status MLS_PT_OUTLIER, output = the point, normal = 0.
+template <int DEG, int PREC>
+__global__ void __launch_bounds__(kProjThreads) k_project_rows(const float4 *__restrict__ xyz4, int64_t n,
+                                                               const int64_t *__restrict__ off,
+                                                               const int32_t *__restrict__ rows, float h,
+                                                               int min_nb, const int32_t *__restrict__ order,
+                                                               float *__restrict__ out_xyz,
+                                                               float *__restrict__ out_n,
+                                                               uint8_t *__restrict__ status) {
+    const int64_t slot = blockIdx.x * (int64_t)kProjThreads + threadIdx.x;
+    if (slot >= n) return;
+    const int64_t i = order ? (int64_t)__ldg(order + slot) : slot;
+    const int64_t b = __ldg(off + i);
+    const int k = (int)(__ldg(off + i + 1) - b);
+    const float4 r4 = __ldg(xyz4 + i);
+    float out[3] = {r4.x, r4.y, r4.z}, nf[3] = {0.f, 0.f, 0.f};
+    uint8_t st = MLS_PT_OUTLIER;
+    if (k - 1 >= min_nb)
+        st = project_point<DEG, PREC>(
+            xyz4, [&](int j) { return __ldg(rows + b + j); }, k, 0, 1, h, r4.x, r4.y, r4.z, out, nf);
+    out_xyz[3 * i] = out[0];
+    out_xyz[3 * i + 1] = out[1];
+    out_xyz[3 * i + 2] = out[2];
+    if (out_n) {
+        out_n[3 * i] = nf[0];
+        out_n[3 * i + 1] = nf[1];
+        out_n[3 * i + 2] = nf[2];
+    }
+    if (status) status[i] = st;
+}
+
 // The plain FP64 form: the same three passes, every quantity in double,
 // neighbours re-read from global memory in each pass.
 template <int DEG>
@@ -197,6 +231,34 @@ int launch_project(const float *xyz, int64_t n, const int32_t *idx, int k, float
         default:
             return launch_deg<2>(xyz, n, idx, k, h, precision, order, out_xyz, out_n, status, st);
     }
+}
+
+int launch_project_rows(const float *xyz, int64_t n, const int64_t *off, const int32_t *rows, float h, int degree,
+                        int precision, int min_nb, const int32_t *order, float *out_xyz, float *out_n,
+                        uint8_t *status, cudaStream_t st) {
+    float4 *xyz4 = nullptr;
+    MLS_CUDA_TRY(scratch_alloc((void **)&xyz4, (size_t)n * sizeof(float4), st));
+    k_pack_xyz4<<<(int)std::min<int64_t>((n + 255) / 256, 152 * 16), 256, 0, st>>>(xyz, n, xyz4);
+    const int blocks = (int)((n + kProjThreads - 1) / kProjThreads);
+    const bool mixed = precision == MLS_PREC_MIXED;
+    switch (degree) {
+        case 0:
+            (mixed ? k_project_rows<0, MLS_PREC_MIXED> : k_project_rows<0, MLS_PREC_FP32>)<<<blocks, kProjThreads, 0, st>>>(
+                xyz4, n, off, rows, h, min_nb, order, out_xyz, out_n, status);
+            break;
+        case 1:
+            (mixed ? k_project_rows<1, MLS_PREC_MIXED> : k_project_rows<1, MLS_PREC_FP32>)<<<blocks, kProjThreads, 0, st>>>(
+                xyz4, n, off, rows, h, min_nb, order, out_xyz, out_n, status);
+            break;
+        default:
+            (mixed ? k_project_rows<2, MLS_PREC_MIXED> : k_project_rows<2, MLS_PREC_FP32>)<<<blocks, kProjThreads, 0, st>>>(
+                xyz4, n, off, rows, h, min_nb, order, out_xyz, out_n, status);
+            break;
+    }
+    count_launches(2);
+    MLS_CUDA_TRY(cudaFreeAsync(xyz4, st));
+    MLS_CUDA_TRY(cudaGetLastError());
+    return MLS_OK;
 }
 
 namespace {

@@ -115,3 +115,34 @@ def project(xyz: torch.Tensor, k: int = 32, h: float | None = None, degree: int 
     finally:
         p.close()
     return Projection(p.out_xyz, p.out_normal, p.out_status, p.idx, h)
+
+
+@dataclass
+class RadiusProjection:
+    xyz: torch.Tensor        # (m, 3) projected points that are kept (outliers dropped)
+    normal: torch.Tensor     # (m, 3)
+    kept: torch.Tensor       # (m,) int32 indices of the kept input points
+    status: torch.Tensor     # (n,) uint8 status of every input point (bit 16: outlier)
+    offsets: torch.Tensor    # (n + 1,) int64 CSR offsets of the radius neighbourhoods
+    rows: torch.Tensor       # int32 neighbour indices
+    h: float
+
+
+def project_radius(xyz: torch.Tensor, R: float, h: float | None = None, degree: int = 2,
+                   precision: str = "mixed", min_neighbors: int = 3) -> RadiusProjection:
+    """The paper's neighbourhood definition (Sec. 1.4: the points within radius
+    R) with its outlier rule (Sec. 3.3: fewer than 3 neighbours -> removed):
+    radius rows on the GPU, the projection over them, the compaction.
+    h defaults to R (the Gaussian's width equal to the search radius)."""
+    grid = capi.mls_build_grid(xyz, 0.0, 16)
+    try:
+        offsets, rows, _ = capi.mls_radius_neighbors(grid, R)
+        order = capi.mls_grid_order(grid)
+        hh = float(R if h is None else h)
+        out, nrm, st = capi.mls_project_rows(xyz, offsets, rows, hh, degree, precision, min_neighbors, order=order)
+        kept = capi.mls_compact(st, capi.MLS_PT_OUTLIER)
+        torch.cuda.current_stream().synchronize()
+    finally:
+        grid.close()
+    k = kept.long()
+    return RadiusProjection(out[k], nrm[k], kept, st, offsets, rows, hh)

@@ -64,6 +64,6 @@ def test_outlier_rule_counts_the_other_points():
                     [9, 9, 9]], np.float32)                                   # 7: none
     off, rows = oracle.radius_neighbors(pts, 0.12)
     assert list(np.diff(off)) == [4, 2, 2, 2, 3, 2, 2, 1]
-    _, _, st = oracle.project_rows(pts, off, rows, 0.2, 0, min_neighbors=3)
+    _, _, st, _ = oracle.project_rows(pts, off, rows, 0.2, 0, min_neighbors=3)
     assert st[0] & oracle.STATUS_OUTLIER == 0
     assert all(st[i] & oracle.STATUS_OUTLIER for i in range(1, 8))

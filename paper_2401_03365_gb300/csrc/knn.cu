@@ -58,6 +58,8 @@ struct __align__(16) WarpBuf {
     int nprev;                      // kept words of the last ranked query (in tpos)
     int cell_start[32];             // cells of the current visiting round
     int cell_count[32];
+    int cube_start[kSlots * 32];    // the cached cube of cells (struct Cube)
+    int cube_count[kSlots * 32];
     float kth;
 };
 
@@ -92,9 +94,12 @@ __device__ __forceinline__ void cube_offset(int j, int &dx, int &dy, int &dz) {
 
 // The 5x5x5 cube of cells around (cx, cy, cz) at level lev: cell j = r * 32 +
 // lane is held by this lane in slot r.  M = points in the whole cube.
+// The cell ranges live in the warp's shared buffer (slot r of lane t at
+// r * 32 + t): kept in registers or local memory they would be spilled and
+// written back through L2 on every reload.
 struct Cube {
     int lev = -1, cx = 0, cy = 0, cz = 0, M = 0;
-    int start[kSlots], count[kSlots];
+    int *st = nullptr, *ct = nullptr;    // this lane's slots: st[r * 32], ct[r * 32]
 };
 
 // Looks the 125 cells up with the four probes of a lane in flight together.
@@ -146,8 +151,8 @@ __device__ void load_cube(const GridView &g, int lev, const uint32_t c0[3], Cube
             st = __ldg(t.cell_start + id[r]);
             ct = __ldg(t.cell_start + id[r] + 1) - st;
         }
-        cb.start[r] = st;
-        cb.count[r] = ct;
+        cb.st[r * 32] = st;
+        cb.ct[r * 32] = ct;
         tot += ct;
     }
     cb.M = warp_sum(tot);
@@ -178,7 +183,7 @@ __device__ void for_each_point(const GridView &g, const Cube &cb, WarpBuf &wb, f
     int nsel = 0;
 #pragma unroll
     for (int r = 0; r < kSlots; ++r) {
-        sel[r] = cb.count[r] > 0 && cell_dist2(g, cb, r, lane, q) <= lim2;
+        sel[r] = cb.ct[r * 32] > 0 && cell_dist2(g, cb, r, lane, q) <= lim2;
         nsel += sel[r];
     }
     const int incl_sel = warp_incl_scan(nsel, lane);
@@ -193,8 +198,8 @@ __device__ void for_each_point(const GridView &g, const Cube &cb, WarpBuf &wb, f
                 const int dst = c - round;
                 // each lane publishes its selected cells through shared memory
                 if (dst >= 0 && dst < 32) {
-                    wb.cell_start[dst] = cb.start[r];
-                    wb.cell_count[dst] = cb.count[r];
+                    wb.cell_start[dst] = cb.st[r * 32];
+                    wb.cell_count[dst] = cb.ct[r * 32];
                 }
                 ++c;
             }
@@ -517,8 +522,8 @@ __device__ __noinline__ float solve_query(const GridView &g, WarpBuf &wb, Cube &
         const float dscale = 32.0f / (3.0f * S);
 #pragma unroll
         for (int r = 0; r < kSlots; ++r)
-            if (cb.count[r] > 0)
-                atomicAdd(&wb.hist[min(31, (int)(sqrtf(cell_dist2(g, cb, r, lane, q)) * dscale))], cb.count[r]);
+            if (cb.ct[r * 32] > 0)
+                atomicAdd(&wb.hist[min(31, (int)(sqrtf(cell_dist2(g, cb, r, lane, q)) * dscale))], cb.ct[r * 32]);
         __syncwarp();
         const int need = min(2 * k, cb.M);
         const unsigned ok = __ballot_sync(kFull, warp_incl_scan(wb.hist[lane], lane) >= need);
@@ -594,9 +599,10 @@ __device__ __forceinline__ int warp_take(int *counter, int lane) {
     return __shfl_sync(kFull, v, 0);
 }
 
-// Six blocks per SM: the kernel is bound by instruction issue and latency,
-// and more resident warps hide more of the latter.
-constexpr int kChainBlocksPerSm = 6;
+// Five blocks per SM (the shared buffers allow five): the kernel is bound by
+// instruction issue and latency, and more resident warps hide more of the
+// latter.
+constexpr int kChainBlocksPerSm = 5;
 
 template <int KPL>
 __global__ void __launch_bounds__(kChainThreads, kChainBlocksPerSm) k_knn_chain(GridView g, int k, int *__restrict__ work,
@@ -609,6 +615,8 @@ __global__ void __launch_bounds__(kChainThreads, kChainBlocksPerSm) k_knn_chain(
     unsigned long long *next_query = reinterpret_cast<unsigned long long *>(&work[4]);
     const float big = 16.0f * g.side[g.base_level] * g.side[g.base_level];
     Cube cb;
+    cb.st = wb.cube_start + lane;
+    cb.ct = wb.cube_count + lane;
     for (;;) {
         // run length from a racy read of the queue: any length is correct,
         // since every run is reserved by its own atomic add
@@ -662,6 +670,8 @@ __global__ void __launch_bounds__(kChainThreads) k_knn_sparse(GridView g, int k,
     WarpBuf &wb = bufs[threadIdx.x >> 5];
     const int count = work[1];
     Cube cb;
+    cb.st = wb.cube_start + lane;
+    cb.ct = wb.cube_count + lane;
     for (int i = warp_take(&work[2], lane); i < count; i = warp_take(&work[2], lane)) {
         const int64_t sp = work[8 + i];
         const float4 q = __ldg(g.pts + sp);
@@ -697,6 +707,8 @@ __global__ void __launch_bounds__(kChainThreads) k_radius(GridView g, float R2, 
     const float scale = R2 > 0.f ? 32.0f / R2 : 0.f;
     const int64_t n_warps = (int64_t)gridDim.x * kChainWarps;
     Cube cb;
+    cb.st = wb.cube_start + lane;
+    cb.ct = wb.cube_count + lane;
     for (int64_t run = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; run * 32 < g.n; run += n_warps) {
         const int64_t end = min((int64_t)g.n, run * 32 + 32);
         for (int64_t sp = run * 32; sp < end; ++sp) {

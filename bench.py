@@ -400,6 +400,7 @@ def run_ours(args):
     }
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(cloud.xyz, h, args.cpu_sample)
+        line["cpu_baseline_all_cores"] = cpu_baseline_all_cores(cloud.xyz, h, args.cpu_sample)
     if world == 1 and not args.no_batched:
         line["batched"] = run_batched(args, dev)
     if world > 1:
@@ -522,6 +523,48 @@ def cpu_baseline(xyz, h, sample):
                        f"adjoint of a seeded sample of {sample} points ({t_sample:.2f} s), extrapolated to the "
                        f"full cloud"),
             "seconds": t_build + t_sample}
+
+
+def _oracle_chunk(xyz, h, queries, seed):
+    """One worker of the all-cores baseline: the oracle's own k-d tree over
+    the whole cloud, then kNN, projection and adjoint of its queries."""
+    import oracle
+    n = xyz.shape[0]
+    rng = np.random.default_rng(seed)
+    gp = rng.standard_normal((n, 3))
+    gn = 0.1 * rng.standard_normal((n, 3))
+    t0 = time.perf_counter()
+    oracle.knn_kdtree(xyz, K, queries=np.zeros(0, np.int64))
+    t_build = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    rows, _ = oracle.knn_kdtree(xyz, K, queries=queries)
+    oracle.project(xyz, rows, h, 2, queries=queries)
+    oracle.project_grad(xyz, rows, h, 2, gp, gn, queries=queries)
+    return t_build, time.perf_counter() - t0
+
+
+def cpu_baseline_all_cores(xyz, h, sample):
+    """The same single-threaded oracle in one process per host core, each on
+    its share of the sample (the per-point loop of Algorithm 1 split over
+    cores); the full cloud's time is the tree build plus each core's share of
+    the points at the measured per-point time."""
+    import multiprocessing as mp
+    n = xyz.shape[0]
+    cores = max(1, os.cpu_count() or 1)
+    rng = np.random.default_rng(123)
+    q = np.sort(rng.choice(n, sample, replace=False))
+    parts = np.array_split(q, cores)
+    t0 = time.perf_counter()
+    with mp.get_context("spawn").Pool(cores) as pool:
+        res = pool.starmap(_oracle_chunk, [(xyz, h, p, 7 + i) for i, p in enumerate(parts)])
+    wall = time.perf_counter() - t0
+    build = max(r[0] for r in res)
+    per_point = sum(r[1] for r in res) / sample          # seconds of one core per point
+    t_full = build + per_point * n / cores
+    return {"value": n / t_full, "unit": "points/s", "cores": cores, "kind": "oracle",
+            "sample": (f"{cores} processes, each: k-d tree over all {n} points + kNN, FP64 projection and FP64 "
+                       f"adjoint of its share of a {sample}-point sample; full cloud extrapolated as build + "
+                       f"n / cores x the per-point time"), "seconds": wall}
 
 
 def run_reference(args):

@@ -111,3 +111,41 @@ def test_autograd_function(capi):
     torch.cuda.synchronize()
     assert torch.allclose(x.grad, gx, rtol=1e-4, atol=1e-6 * gx.abs().max().item())
     assert torch.allclose(h.grad.reshape(1), gh, rtol=1e-4)
+
+
+def test_backward_full_size_torus_sampled(capi):
+    """The benchmark workload (2M points with outliers, k = 32, mixed, Morton
+    order): the gradient at a seeded sample of points j equals the sum over
+    the queries whose rows hold j (and j itself); the oracle's adjoint over
+    exactly those queries gives it in FP64."""
+    c = workloads.torus()
+    x = torch.from_numpy(c.xyz).cuda()
+    grid = capi.mls_build_grid(x, 0.0, c.k)
+    idx, _ = capi.mls_knn(grid, c.k)
+    order = capi.mls_grid_order(grid)
+    h = 2.0 * float(capi.mls_mean_knn_dist(x, idx).item())
+    rng = np.random.default_rng(31)
+    gp = rng.standard_normal((c.n, 3)).astype(np.float32)
+    gn = (0.1 * rng.standard_normal((c.n, 3))).astype(np.float32)
+    gx, _ = capi.mls_project_backward(x, idx, h, torch.from_numpy(gp).cuda(), torch.from_numpy(gn).cuda(), 2,
+                                      "mixed", order=order)
+    torch.cuda.synchronize()
+    grid.close()
+    rows = idx.cpu().numpy()
+    g = gx.cpu().numpy().astype(np.float64)
+    targets = np.sort(rng.choice(c.n, 300, replace=False))
+    hit = np.isin(rows, targets).any(axis=1)
+    hit[targets] = True
+    queries = np.nonzero(hit)[0]
+    # the sampled rows must be the oracle's own rows
+    rows_o, _ = oracle.knn_kdtree(c.xyz, c.k, queries=queries)
+    assert np.array_equal(rows_o, rows[queries])
+    g_o, _ = oracle.project_grad(c.xyz, rows_o, float(np.float32(h)), 2, gp.astype(np.float64),
+                                 gn.astype(np.float64), queries=queries)
+    err = np.linalg.norm(g[targets] - g_o[targets], axis=1)
+    scale = np.linalg.norm(g_o[targets], axis=1)
+    ref = np.median(scale)
+    # points near ill-posed neighbourhoods (outliers) carry gradients that
+    # FP32 cannot resolve: the bound holds for all but a stated few
+    ok = err <= 2e-3 * scale + 2e-4 * ref
+    assert ok.mean() >= 0.98, (np.sort(err / (scale + 1e-30))[-10:])

@@ -381,10 +381,12 @@ __global__ void k_edge_fill(const uint32_t *__restrict__ tgt, const int32_t *__r
 }
 
 // Sum of the edges that point at t plus t's own term, one warp per target:
-// the bucket's words are sorted (bitonic network over 64 slots, two per
-// lane) and summed by a fixed tree over the sorted order, so the result does
-// not depend on the order in which the edges were bucketed.  Buckets above 64
-// entries (rare hubs) are sorted in place and summed by one lane.
+// the bucket's words are sorted by edge number (bitonic network over the
+// lanes: 32 slots, one 32-bit key per lane, for buckets of at most 32 edges,
+// the common case; 64 slots, two 64-bit words per lane, up to 64) and summed
+// by a fixed tree over the sorted order, so the result does not depend on the
+// order in which the edges were bucketed.  Buckets above 64 entries (rare
+// hubs) are sorted in place and summed by one lane.
 __device__ __forceinline__ void cswap(unsigned long long &a, unsigned long long &b, bool up) {
     if ((a > b) == up) {
         const unsigned long long t = a;
@@ -402,7 +404,35 @@ __global__ void k_gather(int64_t n, const int32_t *__restrict__ order, const int
     for (int64_t t = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; t < n; t += warps) {
         const int32_t b = off[t], m = off[t + 1] - b;
         float g[3] = {0.f, 0.f, 0.f};
-        if (m <= 64) {
+        if (m <= 32) {
+            // one edge per lane: sort by the 32-bit edge number, carry the record id
+            uint32_t key = lane < m ? (uint32_t)(ent[b + lane] >> 32) : 0xffffffffu;
+            uint32_t rid = lane < m ? (uint32_t)ent[b + lane] : 0u;
+#pragma unroll
+            for (int kk = 2; kk <= 32; kk <<= 1) {
+#pragma unroll
+                for (int j = kk >> 1; j > 0; j >>= 1) {
+                    const uint32_t ok = __shfl_xor_sync(0xffffffffu, key, j);
+                    const uint32_t orid = __shfl_xor_sync(0xffffffffu, rid, j);
+                    const bool take_min = ((lane & j) == 0) == ((lane & kk) == 0);
+                    if (take_min ? (ok < key) : (ok > key)) {
+                        key = ok;
+                        rid = orid;
+                    }
+                }
+            }
+            const float4 a = lane < m ? edge4[rid] : make_float4(0.f, 0.f, 0.f, 0.f);
+            float tx = a.x, ty = a.y, tz = a.z;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                tx += __shfl_xor_sync(0xffffffffu, tx, o);
+                ty += __shfl_xor_sync(0xffffffffu, ty, o);
+                tz += __shfl_xor_sync(0xffffffffu, tz, o);
+            }
+            g[0] = tx;
+            g[1] = ty;
+            g[2] = tz;
+        } else if (m <= 64) {
             unsigned long long v0 = 2 * lane < m ? ent[b + 2 * lane] : kNone;
             unsigned long long v1 = 2 * lane + 1 < m ? ent[b + 2 * lane + 1] : kNone;
             // element e = 2 lane + r

@@ -80,7 +80,7 @@ __global__ void k_batch_pack(const float *__restrict__ xyz, int64_t n, float4 *_
 }
 
 template <int DEG, int PREC>
-__global__ void __launch_bounds__(kBatchMaxThreads) k_project_batched(BatchArgs a) {
+__global__ void __launch_bounds__(kBatchMaxThreads, 4) k_project_batched(BatchArgs a) {
     extern __shared__ int32_t rows[];
     __shared__ int s_tile;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;

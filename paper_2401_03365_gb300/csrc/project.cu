@@ -72,7 +72,7 @@ __global__ void __launch_bounds__(kProjThreads, LEVIN ? 5 : 8) k_project(const f
 // fewer than min_nb other points in its row is an outlier (Sec. 3.3): not
 // projected, status MLS_PT_OUTLIER, output = the point, normal = 0.
 template <int DEG, int PREC>
-__global__ void __launch_bounds__(kProjThreads) k_project_rows(const float4 *__restrict__ xyz4, int64_t n,
+__global__ void __launch_bounds__(kProjThreads, 8) k_project_rows(const float4 *__restrict__ xyz4, int64_t n,
                                                                const int64_t *__restrict__ off,
                                                                const int32_t *__restrict__ rows, float h,
                                                                int min_nb, const int32_t *__restrict__ order,

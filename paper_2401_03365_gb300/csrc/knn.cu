@@ -27,8 +27,8 @@
 // tightened from the bucket histogram and the search repeated; past that a
 // sorted insertion list finishes the query.
 //
-// The cube's 125 cell ranges (four per lane) are cached in registers: queries
-// that follow each other in Morton order mostly share them.
+// The cube's 125 cell ranges (four per lane) are cached in the warp's shared
+// memory: queries that follow each other in Morton order mostly share them.
 #include <algorithm>
 
 #include "grid.cuh"
@@ -179,11 +179,31 @@ __device__ __forceinline__ float cell_dist2(const GridView &g, const Cube &cb, i
 template <typename F>
 __device__ void for_each_point(const GridView &g, const Cube &cb, WarpBuf &wb, float4 q, float lim2, int lane,
                                F &&f) {
+    // squared gap from q to the cube's slabs: lane 5 a + t (a < 3, t < 5)
+    // holds axis a at cell offset t - 2; a cell's box distance^2 is the sum
+    // of its three slabs' gaps (rounding of a few ulps, far inside the
+    // 2^-20 margins of lim2)
+    float gap2 = 0.f;
+    {
+        const int ax = lane / 5, t = lane - 5 * ax;
+        if (ax < 3) {
+            const float S = g.side[cb.lev];
+            const int c = ax == 0 ? cb.cx : (ax == 1 ? cb.cy : cb.cz);
+            const float qa = ax == 0 ? q.x : (ax == 1 ? q.y : q.z);
+            const float lo = g.frame.origin[ax] + (float)(c + t - 2) * S;
+            const float gp = fmaxf(0.f, fmaxf(lo - qa, qa - (lo + S)));
+            gap2 = gp * gp;
+        }
+    }
     bool sel[kSlots];
     int nsel = 0;
 #pragma unroll
     for (int r = 0; r < kSlots; ++r) {
-        sel[r] = cb.ct[r * 32] > 0 && cell_dist2(g, cb, r, lane, q) <= lim2;
+        const int j = r * 32 + lane;     // cells past 124 are empty (ct = 0)
+        const int jx = j % 5, jy = (j / 5) % 5, jz = min(j / 25, 4);
+        const float d2 = (__shfl_sync(kFull, gap2, jx) + __shfl_sync(kFull, gap2, 5 + jy)) +
+                         __shfl_sync(kFull, gap2, 10 + jz);
+        sel[r] = cb.ct[r * 32] > 0 && d2 <= lim2;
         nsel += sel[r];
     }
     const int incl_sel = warp_incl_scan(nsel, lane);
@@ -249,13 +269,15 @@ __device__ void for_each_point(const GridView &g, const Cube &cb, WarpBuf &wb, f
 }
 
 // Keeps the visited words with key <= tau: the first kCap (word and sorted
-// position) go to the buffers.  Returns the number kept.  With HIST, every
+// position) go to the buffers.  Returns the number kept.  With hist, every
 // kept key is also counted in 32 buckets (bucket = key * scale) with each
 // bucket's largest key, for tightening tau when far too many are kept.
-template <bool HIST>
-__device__ int scan_keep(const GridView &g, const Cube &cb, WarpBuf &wb, float4 q, float lim2, float tau,
-                         float scale, int lane) {
-    if (HIST) {
+// Out of line, one copy for all callers: the query solver around it is
+// inlined into the kernels, and a single body keeps the code they share in
+// the instruction cache.
+__device__ __noinline__ int scan_keep(const GridView &g, const Cube &cb, WarpBuf &wb, float4 q, float lim2,
+                                      float tau, float scale, int lane, bool hist) {
+    if (hist) {
         __syncwarp();
         wb.hist[lane] = 0;
         wb.binmax[lane] = 0u;
@@ -272,7 +294,7 @@ __device__ int scan_keep(const GridView &g, const Cube &cb, WarpBuf &wb, float4 
                 wb.surv[slot] = pack(key, p);
                 wb.spos[slot] = pos;
             }
-            if (HIST) {
+            if (hist) {
                 const int bin = min(31, (int)(key * scale));
                 atomicAdd(&wb.hist[bin], 1);
                 atomicMax(&wb.binmax[bin], __float_as_uint(key));
@@ -499,9 +521,9 @@ __device__ __forceinline__ float neighbour_bound(const GridView &g, const WarpBu
 // finite tau_in is given, then the cube search with culling, tightening and,
 // as a last resort, the sorted insertion list.  Returns the k-th key.
 template <int KPL>
-__device__ __noinline__ float solve_query(const GridView &g, WarpBuf &wb, Cube &cb, float4 q, int32_t qi,
-                                          const uint32_t c0[3], float tau, int k, int lane, bool may_defer,
-                                          int32_t *__restrict__ out_idx, float *__restrict__ out_key) {
+__device__ __forceinline__ float solve_query(const GridView &g, WarpBuf &wb, Cube &cb, float4 q, int32_t qi,
+                                             const uint32_t c0[3], float tau, int k, int lane, bool may_defer,
+                                             int32_t *__restrict__ out_idx, float *__restrict__ out_key) {
     const float eps2 = 2.0f * g.frame.eps;
     if (!(tau < INFINITY)) {
         // fresh bound: coarsen until the cube holds k points, then take the
@@ -537,7 +559,7 @@ __device__ __noinline__ float solve_query(const GridView &g, WarpBuf &wb, Cube &
         // within 3 sqrt(3) S < 5.2 S): bucket all their keys over [0, hi]
         const float far = ((all ? 5.2f * S : lim) + 1.7320509f * S + eps2) * kGrow * kGrow;
         const float hi = far * far * kGrow;
-        scan_keep<true>(g, cb, wb, q, lim2, INFINITY, hi > 0.f ? 32.0f / hi : 0.f, lane);
+        scan_keep(g, cb, wb, q, lim2, INFINITY, hi > 0.f ? 32.0f / hi : 0.f, lane, true);
         tau = tighten(wb, k, lane, hi);
     }
     bool full_hist = false;
@@ -550,8 +572,7 @@ __device__ __noinline__ float solve_query(const GridView &g, WarpBuf &wb, Cube &
         const float lim = (reach + eps2) * kGrow;
         const float lim2 = lim * lim;
         const float scale = tau > 0.f ? 32.0f / tau : 0.f;
-        const int S = full_hist ? scan_keep<true>(g, cb, wb, q, lim2, tau, scale, lane)
-                                : scan_keep<false>(g, cb, wb, q, lim2, tau, scale, lane);
+        const int S = scan_keep(g, cb, wb, q, lim2, tau, scale, lane, full_hist);
         if (S >= k && S <= kCap) return rank_and_write(wb, S, scale, k, lane, qi, out_idx, out_key);
         if (S < k) {            // cannot happen for a valid bound: search everything
             tau = INFINITY;
@@ -716,7 +737,7 @@ __global__ void __launch_bounds__(kChainThreads) k_radius(GridView g, float R2, 
             const uint64_t key0 = __ldg(g.keys + sp);
             const uint32_t c0[3] = {compact3(key0), compact3(key0 >> 1), compact3(key0 >> 2)};
             load_cube(g, lev, c0, cb, lane);
-            const int S = scan_keep<false>(g, cb, wb, q, lim2, R2, scale, lane);
+            const int S = scan_keep(g, cb, wb, q, lim2, R2, scale, lane, false);
             const int64_t qi = (int64_t)__float_as_int(q.w);
             if (!ROWS) {
                 if (lane == 0) count[qi] = S;

@@ -245,9 +245,11 @@ int mls_project_noalloc(const float *d_xyz, int64_t n, const int32_t *d_idx, int
  *   d_grad_out_normal  device, n x 3 floats or NULL (zero)
  *   d_grad_xyz         device, n x 3 floats, overwritten: dL/dx
  *   d_grad_h           device, 1 float, overwritten: dL/dh
- * Deterministic: edge contributions are summed in a fixed order.  Uses
- * stream-ordered scratch (the library's pool, see mls_release_scratch) of about
- * n * (48 + 28 k) bytes.
+ * Deterministic: each coordinate's gradient is the exact sum (64-bit fixed
+ * point at a power-of-two scale chosen per point and component from the
+ * largest term) of its terms, rounded once to float, so it depends neither on
+ * scheduling nor on d_order.  Uses stream-ordered scratch (the library's pool,
+ * see mls_release_scratch) of about n * (48 + 16 k) bytes.
  */
 int mls_project_backward(const float *d_xyz, int64_t n, const int32_t *d_idx, int k, float h, int degree,
                          int precision, const int32_t *d_order, const float *d_grad_out_xyz,

@@ -12,21 +12,18 @@
 //
 // One thread per point recomputes its forward quantities (no frame is
 // stored) and writes the gradient it sends to each of its k neighbours into
-// an edge buffer, and the gradient of its own position separately.  A
-// reverse adjacency (edges bucketed by target point, each bucket ordered by
-// edge number) then sums them in a fixed order: results do not depend on
-// scheduling.
+// that neighbour's bucket of a reverse adjacency (bucket sizes are counted
+// from the neighbour rows beforehand), and the gradient of its own position
+// separately.  Each bucket, with its point's own term, is then summed exactly
+// in 64-bit fixed point (a per-bucket, per-component power-of-two scale from
+// the largest magnitude) and rounded once: the sum does not depend on the
+// order in which the records reached the bucket, so results do not depend on
+// scheduling or on the processing order.
 //
 // Everything is indexed by sorted (Morton) position when a processing order
-// is given: point slot s of the order sends edge (s, j) to the sorted
-// position t of its neighbour j.  Neighbours are close in that order, so the
-// per-target counts and the bucket fill touch a narrow window of memory at a
-// time, and the gather reads the edges of nearby sources.  Edge (s, j) is
-// stored at id = (s / 32) 32 k + 32 j + s % 32: a warp of 32 consecutive slots
-// writes 32 consecutive float4 records per neighbour rank.  Each bucket is
-// summed in the order of the edges' numbers in the original indexing,
-// i k + j for neighbour j of point i, so the gradient does not depend on the
-// processing order either.
+// is given: point slot s of the order sends its records to the sorted
+// positions of its neighbours.  Neighbours are close in that order, so the
+// bucket writes of a block touch a narrow window of memory at a time.
 #include <algorithm>
 #include <climits>
 
@@ -39,6 +36,8 @@ int device_exclusive_scan(const int32_t *in, int32_t *out, int64_t n, cudaStream
 namespace {
 
 constexpr int kBwdThreads = 128;
+constexpr int kSumLanes = 4;        // lanes per bucket in the bucket sum (at least 3: one per component written)
+constexpr int kSumCached = 9;       // values per lane held in registers there
 constexpr float kBwdGapFlag = 1e-3f;
 constexpr float kBwdCondFlag = 1e5f;
 
@@ -81,8 +80,8 @@ template <int DEG, int PREC>
 __global__ void __launch_bounds__(kBwdThreads, 6) k_backward_point(
     const float4 *__restrict__ xyz4, int64_t n, const int32_t *__restrict__ idx, int k, float h,
     const int32_t *__restrict__ order, const int32_t *__restrict__ pos, const float *__restrict__ gout_xyz,
-    const float *__restrict__ gout_n, float4 *__restrict__ edge4, uint32_t *__restrict__ tgt,
-    int32_t *__restrict__ cnt, float4 *__restrict__ self4, double *__restrict__ h_part) {
+    const float *__restrict__ gout_n, const int32_t *__restrict__ off, int32_t *__restrict__ fill,
+    float4 *__restrict__ rec, float4 *__restrict__ self4, double *__restrict__ h_part) {
     constexpr int M = Basis<DEG>::M;
     extern __shared__ int32_t rows[];
     __shared__ double hred[kBwdThreads / 32];
@@ -145,19 +144,15 @@ __global__ void __launch_bounds__(kBwdThreads, 6) k_backward_point(
         }
         const float gp[3] = {gout_xyz[3 * i], gout_xyz[3 * i + 1], gout_xyz[3 * i + 2]};
         float rbar[3] = {gp[0], gp[1], gp[2]};
-        // edge (slot, j): its record id, and the target's sorted position
-        const int64_t id0 = (slot >> 5) * 32 * (int64_t)k + lane;
-        auto emit = [&](int j, float gx, float gy, float gz) {
+        // a free place in the bucket of neighbour j (its sorted position)
+        auto bucket_slot = [&](int j) {
             const int32_t p = my_rows[j * 32 + lane];
             const int32_t t = pos ? __ldg(pos + p) : p;
-            const int64_t id = id0 + 32 * (int64_t)j;
-            edge4[id] = make_float4(gx, gy, gz, 0.f);
-            tgt[id] = (uint32_t)t;
-            atomicAdd(cnt + t, 1);
+            return __ldg(off + t) + atomicAdd(fill + t, 1);
         };
         if (flag & MLS_PT_PLANE_DEGENERATE) {
             // p' = r and the normal is taken as constant: nothing reaches the neighbours
-            for (int j = 0; j < k; ++j) emit(j, 0.f, 0.f, 0.f);
+            for (int j = 0; j < k; ++j) rec[bucket_slot(j)] = make_float4(0.f, 0.f, 0.f, 0.f);
         } else {
             const float gn[3] = {gout_n ? gout_n[3 * i] : 0.f, gout_n ? gout_n[3 * i + 1] : 0.f,
                                  gout_n ? gout_n[3 * i + 2] : 0.f};
@@ -288,6 +283,7 @@ __global__ void __launch_bounds__(kBwdThreads, 6) k_backward_point(
             // ---- per neighbour: everything that reaches d_j ----
             const float iW = 1.f / W;
             for (int j = 0; j < k; ++j) {
+                const int32_t at = bucket_slot(j);      // taken early: its latency overlaps the arithmetic
                 const float4 p = __ldg(xyz4 + my_rows[j * 32 + lane]);
                 const float d[3] = {p.x - rx, p.y - ry, p.z - rz};
                 const float dd = fmaf(d[0], d[0], fmaf(d[1], d[1], d[2] * d[2]));
@@ -338,7 +334,7 @@ __global__ void __launch_bounds__(kBwdThreads, 6) k_backward_point(
                     dbar[c] -= 2.f * wb * d[c] / h2;
                     rbar[c] -= dbar[c];
                 }
-                emit(j, dbar[0], dbar[1], dbar[2]);
+                rec[at] = make_float4(dbar[0], dbar[1], dbar[2], 0.f);
                 hbar += 2.f * wb * dd / (h2 * h);
             }
         }
@@ -363,131 +359,123 @@ __global__ void k_inverse(const int32_t *__restrict__ order, int64_t n, int32_t 
         pos[order[s]] = (int32_t)s;
 }
 
-// Bucket fill: per target, the words (i k + j) << 32 | id of the edges that
-// point at it (in arbitrary order; the gather sorts each bucket).
-__global__ void k_edge_fill(const uint32_t *__restrict__ tgt, const int32_t *__restrict__ order, int64_t n, int k,
-                            const int32_t *__restrict__ off, int32_t *__restrict__ fill,
-                            unsigned long long *__restrict__ ent) {
-    const int64_t ne = ((n + 31) >> 5) * 32 * (int64_t)k;
-    for (int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; id < ne;
-         id += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t slot = (id / (32 * (int64_t)k)) * 32 + (id & 31);
-        if (slot >= n) continue;
-        const int64_t i = order ? (int64_t)order[slot] : slot;
-        const int64_t e = i * k + ((id >> 5) % k);
-        const uint32_t t = tgt[id];
-        ent[off[t] + atomicAdd(&fill[t], 1)] = ((unsigned long long)e << 32) | (unsigned long long)id;
+// Bucket sizes: the number of row entries naming each point (at its sorted
+// position).
+__global__ void k_count(const int32_t *__restrict__ idx, int64_t ne, const int32_t *__restrict__ pos,
+                        int32_t *__restrict__ cnt) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < ne; e += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t p = __ldg(idx + e);
+        atomicAdd(cnt + (pos ? __ldg(pos + p) : p), 1);
     }
 }
 
-// Sum of the edges that point at t plus t's own term, one warp per target:
-// the bucket's words are sorted by edge number (bitonic network over the
-// lanes: 32 slots, one 32-bit key per lane, for buckets of at most 32 edges,
-// the common case; 64 slots, two 64-bit words per lane, up to 64) and summed
-// by a fixed tree over the sorted order, so the result does not depend on the
-// order in which the edges were bucketed.  Buckets above 64 entries (rare
-// hubs) are sorted in place and summed by one lane.
-__device__ __forceinline__ void cswap(unsigned long long &a, unsigned long long &b, bool up) {
-    if ((a > b) == up) {
-        const unsigned long long t = a;
-        a = b;
-        b = t;
+// 2^e as a float, e in [-126, 127].
+__device__ __forceinline__ float pow2f(int e) { return __int_as_float((e + 127) << 23); }
+
+// The integer q 2^-s, rounded once to float.
+__device__ __forceinline__ float from_fixed(long long q, int s) {
+    float x = __ll2float_rn(q);
+    if (s > 120) {
+        x *= pow2f(-120);
+        s -= 120;
     }
+    return x * pow2f(-s);
 }
 
-__global__ void k_gather(int64_t n, const int32_t *__restrict__ order, const int32_t *__restrict__ off,
-                         unsigned long long *__restrict__ ent, const float4 *__restrict__ edge4,
-                         const float4 *__restrict__ self4, float *__restrict__ grad) {
-    constexpr unsigned long long kNone = ~0ull;
-    const int lane = threadIdx.x & 31;
+// Sum of the records in t's bucket plus t's own term, G lanes per point (a
+// warp sums 32 / G consecutive buckets, which are adjacent in memory), the
+// first V x G values held in registers.  Per component: the largest
+// magnitude M = m 2^E (m in [1, 2)) over the bucket's c values fixes the scale
+// 2^s, s = 61 - E - ceil(log2 c), so that every scaled value is below
+// 2^(62 - ceil(log2 c)) and the integer sum below 2^62; each value is rounded
+// to an integer once (an error below 2^-s, that is 2^-60 M or less), the
+// integers are summed exactly, and the total is rounded once to float.
+// Non-finite components are summed in float.  The largest magnitude is taken
+// over the bit patterns with the sign cleared, which order non-negative
+// floats and put infinities and NaNs above every finite value.
+template <int G, int V>
+__global__ void __launch_bounds__(256) k_bucket_sum(int64_t n, const int32_t *__restrict__ order,
+                                                    const int32_t *__restrict__ off, const float4 *__restrict__ rec,
+                                                    const float4 *__restrict__ self4, float *__restrict__ grad) {
+    static_assert(G >= 3 && G <= 32 && 32 % G == 0, "G lanes per point, one per written component");
+    constexpr int P = 32 / G;     // points per warp
+    constexpr uint32_t kAbs = 0x7fffffffu, kInf = 0x7f800000u;
+    const int lane = threadIdx.x & 31, sub = lane % G;
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    for (int64_t t = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; t < n; t += warps) {
-        const int32_t b = off[t], m = off[t + 1] - b;
-        float g[3] = {0.f, 0.f, 0.f};
-        if (m <= 32) {
-            // one edge per lane: sort by the 32-bit edge number, carry the record id
-            uint32_t key = lane < m ? (uint32_t)(ent[b + lane] >> 32) : 0xffffffffu;
-            uint32_t rid = lane < m ? (uint32_t)ent[b + lane] : 0u;
+    for (int64_t t0 = ((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5) * P; t0 < n; t0 += warps * P) {
+        const int64_t t = t0 + lane / G;
+        const bool live = t < n;
+        const int32_t b = live ? __ldg(off + t) : 0;
+        const int32_t m = live ? __ldg(off + t + 1) - b : 0;
+        const int c = live ? m + 1 : 0;    // the records and the point's own term (value number m)
+        auto value = [&](int e) { return e < m ? __ldg(rec + b + e) : __ldg(self4 + t); };
+        float4 v[V];
 #pragma unroll
-            for (int kk = 2; kk <= 32; kk <<= 1) {
+        for (int r = 0; r < V; ++r) {
+            const int e = r * G + sub;
+            v[r] = e < c ? value(e) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        uint32_t mb[3] = {0u, 0u, 0u};
+        auto take = [&](float4 a) {
+            mb[0] = max(mb[0], __float_as_uint(a.x) & kAbs);
+            mb[1] = max(mb[1], __float_as_uint(a.y) & kAbs);
+            mb[2] = max(mb[2], __float_as_uint(a.z) & kAbs);
+        };
 #pragma unroll
-                for (int j = kk >> 1; j > 0; j >>= 1) {
-                    const uint32_t ok = __shfl_xor_sync(0xffffffffu, key, j);
-                    const uint32_t orid = __shfl_xor_sync(0xffffffffu, rid, j);
-                    const bool take_min = ((lane & j) == 0) == ((lane & kk) == 0);
-                    if (take_min ? (ok < key) : (ok > key)) {
-                        key = ok;
-                        rid = orid;
-                    }
-                }
+        for (int r = 0; r < V; ++r) take(v[r]);
+        for (int e = V * G + sub; e < c; e += G) take(value(e));
+        const int lc = c > 1 ? 32 - __clz(c - 1) : 0;     // ceil(log2 c)
+        float out[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+#pragma unroll
+            for (int o = G / 2; o > 0; o >>= 1) mb[a] = max(mb[a], __shfl_xor_sync(0xffffffffu, mb[a], o));
+        }
+        const bool finite = mb[0] < kInf && mb[1] < kInf && mb[2] < kInf;
+        if (finite) {
+            // scale 2^s = f1 f2, both factors powers of two (two steps past 2^120)
+            float f1[3], f2[3];
+            int sh[3];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                const int E = max((int)(mb[a] >> 23) - 127, -126);
+                sh[a] = 61 - E - lc;
+                f1[a] = sh[a] > 120 ? pow2f(120) : 1.f;
+                f2[a] = pow2f(sh[a] > 120 ? sh[a] - 120 : sh[a]);
             }
-            const float4 a = lane < m ? edge4[rid] : make_float4(0.f, 0.f, 0.f, 0.f);
-            float tx = a.x, ty = a.y, tz = a.z;
+            long long q[3] = {0, 0, 0};
+            auto add = [&](float4 a) {
+                q[0] += __float2ll_rn(a.x * f1[0] * f2[0]);
+                q[1] += __float2ll_rn(a.y * f1[1] * f2[1]);
+                q[2] += __float2ll_rn(a.z * f1[2] * f2[2]);
+            };
 #pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                tx += __shfl_xor_sync(0xffffffffu, tx, o);
-                ty += __shfl_xor_sync(0xffffffffu, ty, o);
-                tz += __shfl_xor_sync(0xffffffffu, tz, o);
-            }
-            g[0] = tx;
-            g[1] = ty;
-            g[2] = tz;
-        } else if (m <= 64) {
-            unsigned long long v0 = 2 * lane < m ? ent[b + 2 * lane] : kNone;
-            unsigned long long v1 = 2 * lane + 1 < m ? ent[b + 2 * lane + 1] : kNone;
-            // element e = 2 lane + r
+            for (int r = 0; r < V; ++r) add(v[r]);
+            for (int e = V * G + sub; e < c; e += G) add(value(e));
 #pragma unroll
-            for (int kk = 2; kk <= 64; kk <<= 1) {
+            for (int a = 0; a < 3; ++a) {
 #pragma unroll
-                for (int j = kk >> 1; j > 0; j >>= 1) {
-                    const bool up = ((2 * lane) & kk) == 0;
-                    if (j == 1) {
-                        cswap(v0, v1, up);
-                    } else {
-                        const int pl = j >> 1;
-                        const unsigned long long o0 = __shfl_xor_sync(0xffffffffu, v0, pl);
-                        const unsigned long long o1 = __shfl_xor_sync(0xffffffffu, v1, pl);
-                        const bool lower = (lane & pl) == 0;
-                        v0 = (lower == up) ? min(v0, o0) : max(v0, o0);
-                        v1 = (lower == up) ? min(v1, o1) : max(v1, o1);
-                    }
-                }
+                for (int o = G / 2; o > 0; o >>= 1) q[a] += __shfl_xor_sync(0xffffffffu, q[a], o);
+                out[a] = from_fixed(q[a], sh[a]);
             }
-            const float4 a0 = v0 != kNone ? edge4[(uint32_t)v0] : make_float4(0.f, 0.f, 0.f, 0.f);
-            const float4 a1 = v1 != kNone ? edge4[(uint32_t)v1] : make_float4(0.f, 0.f, 0.f, 0.f);
-            float tx = a0.x + a1.x, ty = a0.y + a1.y, tz = a0.z + a1.z;
+        } else {
+            float fs[3] = {0.f, 0.f, 0.f};
+            for (int e = sub; e < c; e += G) {
+                const float4 a = value(e);
+                fs[0] += a.x;
+                fs[1] += a.y;
+                fs[2] += a.z;
+            }
 #pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                tx += __shfl_xor_sync(0xffffffffu, tx, o);
-                ty += __shfl_xor_sync(0xffffffffu, ty, o);
-                tz += __shfl_xor_sync(0xffffffffu, tz, o);
-            }
-            g[0] = tx;
-            g[1] = ty;
-            g[2] = tz;
-        } else if (lane == 0) {
-            for (int32_t q = b + 1; q < b + m; ++q) {
-                const unsigned long long v = ent[q];
-                int32_t u = q;
-                while (u > b && ent[u - 1] > v) {
-                    ent[u] = ent[u - 1];
-                    --u;
-                }
-                ent[u] = v;
-            }
-            for (int32_t q = b; q < b + m; ++q) {
-                const float4 e = edge4[(uint32_t)ent[q]];
-                g[0] += e.x;
-                g[1] += e.y;
-                g[2] += e.z;
+            for (int a = 0; a < 3; ++a) {
+#pragma unroll
+                for (int o = G / 2; o > 0; o >>= 1) fs[a] += __shfl_xor_sync(0xffffffffu, fs[a], o);
+                out[a] = fs[a];
             }
         }
-        if (lane == 0) {
-            const float4 sg = self4[t];
+        if (live && sub < 3) {
             const int64_t o = order ? (int64_t)order[t] : t;
-            grad[3 * o] = sg.x + g[0];
-            grad[3 * o + 1] = sg.y + g[1];
-            grad[3 * o + 2] = sg.z + g[2];
+            grad[3 * o + sub] = sub == 0 ? out[0] : (sub == 1 ? out[1] : out[2]);
         }
     }
 }
@@ -509,12 +497,12 @@ __global__ void __launch_bounds__(1024) k_sum_h(const double *__restrict__ part,
 
 template <int DEG>
 void launch_point(const float4 *xyz4, int64_t n, const int32_t *idx, int k, float h, int precision,
-                  const int32_t *order, const int32_t *pos, const float *gp, const float *gn, float4 *edge4,
-                  uint32_t *tgt, int32_t *cnt, float4 *self4, double *hp, int blocks, cudaStream_t st) {
+                  const int32_t *order, const int32_t *pos, const float *gp, const float *gn, const int32_t *off,
+                  int32_t *fill, float4 *rec, float4 *self4, double *hp, int blocks, cudaStream_t st) {
     const size_t smem = (size_t)k * 32 * sizeof(int32_t) * (kBwdThreads / 32);
     auto kern = precision == MLS_PREC_FP32 ? k_backward_point<DEG, MLS_PREC_FP32> : k_backward_point<DEG, MLS_PREC_MIXED>;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    kern<<<blocks, kBwdThreads, smem, st>>>(xyz4, n, idx, k, h, order, pos, gp, gn, edge4, tgt, cnt, self4, hp);
+    kern<<<blocks, kBwdThreads, smem, st>>>(xyz4, n, idx, k, h, order, pos, gp, gn, off, fill, rec, self4, hp);
 }
 
 }  // namespace
@@ -522,21 +510,17 @@ void launch_point(const float4 *xyz4, int64_t n, const int32_t *idx, int k, floa
 int launch_backward(const float *xyz, int64_t n, const int32_t *idx, int k, float h, int degree, int precision,
                     const int32_t *order, const float *gp, const float *gn, float *grad_xyz, float *grad_h,
                     cudaStream_t st) {
-    const int64_t ne = ((n + 31) >> 5) * 32 * (int64_t)k;     // edge records, whole warp tiles
+    const int64_t ne = n * (int64_t)k;
     const int blocks = (int)((n + kBwdThreads - 1) / kBwdThreads);
-    float4 *xyz4 = nullptr, *edge4 = nullptr, *self4 = nullptr;
+    float4 *xyz4 = nullptr, *rec = nullptr, *self4 = nullptr;
     double *hp = nullptr;
     int32_t *cnt = nullptr, *off = nullptr, *pos = nullptr;
-    uint32_t *tgt = nullptr;
-    unsigned long long *ent = nullptr;
     MLS_CUDA_TRY(scratch_alloc((void **)&xyz4, (size_t)n * sizeof(float4), st));
-    MLS_CUDA_TRY(scratch_alloc((void **)&edge4, (size_t)ne * sizeof(float4), st));
+    MLS_CUDA_TRY(scratch_alloc((void **)&rec, (size_t)ne * sizeof(float4), st));
     MLS_CUDA_TRY(scratch_alloc((void **)&self4, (size_t)n * sizeof(float4), st));
     MLS_CUDA_TRY(scratch_alloc((void **)&hp, (size_t)blocks * sizeof(double), st));
     MLS_CUDA_TRY(scratch_alloc((void **)&cnt, (size_t)(2 * n + 2) * sizeof(int32_t), st));
     MLS_CUDA_TRY(scratch_alloc((void **)&off, (size_t)(n + 1) * sizeof(int32_t), st));
-    MLS_CUDA_TRY(scratch_alloc((void **)&tgt, (size_t)ne * sizeof(uint32_t), st));
-    MLS_CUDA_TRY(scratch_alloc((void **)&ent, (size_t)n * k * sizeof(unsigned long long), st));
     if (order) MLS_CUDA_TRY(scratch_alloc((void **)&pos, (size_t)n * sizeof(int32_t), st));
     int32_t *fill = cnt + n + 1;
     const int grid_n = (int)std::min<int64_t>((n + 255) / 256, 152 * 16);
@@ -547,27 +531,25 @@ int launch_backward(const float *xyz, int64_t n, const int32_t *idx, int k, floa
         k_inverse<<<grid_n, 256, 0, st>>>(order, n, pos);
         ++launches;
     }
-    switch (degree) {
-        case 0: launch_point<0>(xyz4, n, idx, k, h, precision, order, pos, gp, gn, edge4, tgt, cnt, self4, hp, blocks, st); break;
-        case 1: launch_point<1>(xyz4, n, idx, k, h, precision, order, pos, gp, gn, edge4, tgt, cnt, self4, hp, blocks, st); break;
-        default: launch_point<2>(xyz4, n, idx, k, h, precision, order, pos, gp, gn, edge4, tgt, cnt, self4, hp, blocks, st); break;
-    }
+    k_count<<<(int)std::min<int64_t>((ne + 255) / 256, 152 * 32), 256, 0, st>>>(idx, ne, pos, cnt);
     int rc = device_exclusive_scan(cnt, off, n + 1, st);
     if (rc != MLS_OK) return rc;
-    k_edge_fill<<<(int)std::min<int64_t>((ne + 255) / 256, 152 * 32), 256, 0, st>>>(tgt, order, n, k, off, fill, ent);
-    k_gather<<<(int)std::min<int64_t>((n * 32 + 255) / 256, 152 * 32), 256, 0, st>>>(n, order, off, ent, edge4, self4,
-                                                                                      grad_xyz);
+    switch (degree) {
+        case 0: launch_point<0>(xyz4, n, idx, k, h, precision, order, pos, gp, gn, off, fill, rec, self4, hp, blocks, st); break;
+        case 1: launch_point<1>(xyz4, n, idx, k, h, precision, order, pos, gp, gn, off, fill, rec, self4, hp, blocks, st); break;
+        default: launch_point<2>(xyz4, n, idx, k, h, precision, order, pos, gp, gn, off, fill, rec, self4, hp, blocks, st); break;
+    }
+    k_bucket_sum<kSumLanes, kSumCached><<<(int)std::min<int64_t>((n * kSumLanes + 255) / 256, 152 * 32), 256, 0, st>>>(
+        n, order, off, rec, self4, grad_xyz);
     k_sum_h<<<1, 1024, 0, st>>>(hp, blocks, grad_h);
-    count_launches(launches + 4);   // + point, fill, gather, sum_h (the scan counts its own)
+    count_launches(launches + 4);   // + count, point, bucket sum, sum_h (the scan counts its own)
     MLS_CUDA_TRY(cudaGetLastError());
     cudaFreeAsync(xyz4, st);
-    cudaFreeAsync(edge4, st);
+    cudaFreeAsync(rec, st);
     cudaFreeAsync(self4, st);
     cudaFreeAsync(hp, st);
     cudaFreeAsync(cnt, st);
     cudaFreeAsync(off, st);
-    cudaFreeAsync(tgt, st);
-    cudaFreeAsync(ent, st);
     if (pos) cudaFreeAsync(pos, st);
     return MLS_OK;
 }

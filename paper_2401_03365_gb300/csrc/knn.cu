@@ -176,8 +176,20 @@ __device__ __forceinline__ float cell_dist2(const GridView &g, const Cube &cb, i
 // time (one per lane; `valid` false on idle lanes).  The non-empty selected
 // cells are packed onto the lanes (32 per round) and a bitmap of the first
 // point of each cell maps a lane's point number to its cell in O(1).
+// What the visit of a cube's cells needs from the grid, passed by value to the
+// out-of-line scan (a reference to the grid view there would read its fields
+// through memory on every call).
+struct CellGeom {
+    const float4 *pts;
+    float S, ox, oy, oz;     // cell side at the cube's level, frame origin
+};
+
+__device__ __forceinline__ CellGeom cell_geom(const GridView &g, const Cube &cb) {
+    return CellGeom{g.pts, g.side[cb.lev], g.frame.origin[0], g.frame.origin[1], g.frame.origin[2]};
+}
+
 template <typename F>
-__device__ void for_each_point(const GridView &g, const Cube &cb, WarpBuf &wb, float4 q, float lim2, int lane,
+__device__ void for_each_point(const CellGeom &g, const Cube &cb, WarpBuf &wb, float4 q, float lim2, int lane,
                                F &&f) {
     // squared gap from q to the cube's slabs: lane 5 a + t (a < 3, t < 5)
     // holds axis a at cell offset t - 2; a cell's box distance^2 is the sum
@@ -187,10 +199,11 @@ __device__ void for_each_point(const GridView &g, const Cube &cb, WarpBuf &wb, f
     {
         const int ax = lane / 5, t = lane - 5 * ax;
         if (ax < 3) {
-            const float S = g.side[cb.lev];
+            const float S = g.S;
             const int c = ax == 0 ? cb.cx : (ax == 1 ? cb.cy : cb.cz);
             const float qa = ax == 0 ? q.x : (ax == 1 ? q.y : q.z);
-            const float lo = g.frame.origin[ax] + (float)(c + t - 2) * S;
+            const float o = ax == 0 ? g.ox : (ax == 1 ? g.oy : g.oz);
+            const float lo = o + (float)(c + t - 2) * S;
             const float gp = fmaxf(0.f, fmaxf(lo - qa, qa - (lo + S)));
             gap2 = gp * gp;
         }
@@ -275,7 +288,7 @@ __device__ void for_each_point(const GridView &g, const Cube &cb, WarpBuf &wb, f
 // Out of line, one copy for all callers: the query solver around it is
 // inlined into the kernels, and a single body keeps the code they share in
 // the instruction cache.
-__device__ __noinline__ int scan_keep(const GridView &g, const Cube &cb, WarpBuf &wb, float4 q, float lim2,
+__device__ __noinline__ int scan_keep(const CellGeom g, const Cube &cb, WarpBuf &wb, float4 q, float lim2,
                                       float tau, float scale, int lane, bool hist) {
     if (hist) {
         __syncwarp();
@@ -441,7 +454,7 @@ __device__ float insertion_fallback(const GridView &g, const Cube &cb, WarpBuf &
                                     float *__restrict__ out_key) {
     TopK<KPL> top;
     top.init();
-    for_each_point(g, cb, wb, q, lim2, lane, [&](float4 p, bool valid, int pos) {
+    for_each_point(cell_geom(g, cb), cb, wb, q, lim2, lane, [&](float4 p, bool valid, int pos) {
         const float key = rank_key(p, q.x, q.y, q.z);
         top.offer(valid && key <= tau ? pack(key, p) : ~0ull, pos, k, lane);
     });
@@ -559,7 +572,7 @@ __device__ __forceinline__ float solve_query(const GridView &g, WarpBuf &wb, Cub
         // within 3 sqrt(3) S < 5.2 S): bucket all their keys over [0, hi]
         const float far = ((all ? 5.2f * S : lim) + 1.7320509f * S + eps2) * kGrow * kGrow;
         const float hi = far * far * kGrow;
-        scan_keep(g, cb, wb, q, lim2, INFINITY, hi > 0.f ? 32.0f / hi : 0.f, lane, true);
+        scan_keep(cell_geom(g, cb), cb, wb, q, lim2, INFINITY, hi > 0.f ? 32.0f / hi : 0.f, lane, true);
         tau = tighten(wb, k, lane, hi);
     }
     bool full_hist = false;
@@ -572,7 +585,7 @@ __device__ __forceinline__ float solve_query(const GridView &g, WarpBuf &wb, Cub
         const float lim = (reach + eps2) * kGrow;
         const float lim2 = lim * lim;
         const float scale = tau > 0.f ? 32.0f / tau : 0.f;
-        const int S = scan_keep(g, cb, wb, q, lim2, tau, scale, lane, full_hist);
+        const int S = scan_keep(cell_geom(g, cb), cb, wb, q, lim2, tau, scale, lane, full_hist);
         if (S >= k && S <= kCap) return rank_and_write(wb, S, scale, k, lane, qi, out_idx, out_key);
         if (S < k) {            // cannot happen for a valid bound: search everything
             tau = INFINITY;
@@ -737,7 +750,7 @@ __global__ void __launch_bounds__(kChainThreads) k_radius(GridView g, float R2, 
             const uint64_t key0 = __ldg(g.keys + sp);
             const uint32_t c0[3] = {compact3(key0), compact3(key0 >> 1), compact3(key0 >> 2)};
             load_cube(g, lev, c0, cb, lane);
-            const int S = scan_keep(g, cb, wb, q, lim2, R2, scale, lane, false);
+            const int S = scan_keep(cell_geom(g, cb), cb, wb, q, lim2, R2, scale, lane, false);
             const int64_t qi = (int64_t)__float_as_int(q.w);
             if (!ROWS) {
                 if (lane == 0) count[qi] = S;

@@ -92,6 +92,29 @@ def test_backward_deterministic(capi):
     assert torch.equal(a, b) and torch.equal(ah, bh)
 
 
+def test_backward_independent_of_processing_order(capi):
+    """Each gradient is the exact (fixed-point) sum of its terms, rounded
+    once: a random processing order gives bit-identical coordinates' gradients
+    to the Morton order; dL/dh (double partial sums per block) agrees to
+    rounding."""
+    c = workloads.bumpy_sphere(n=60_000, seed=19)
+    x = torch.from_numpy(c.xyz).cuda()
+    grid = capi.mls_build_grid(x, 0.0, 32)
+    idx, _ = capi.mls_knn(grid, 32)
+    order = capi.mls_grid_order(grid).clone()
+    gen = torch.Generator(device="cuda").manual_seed(20)
+    gp = torch.randn(c.n, 3, device="cuda", generator=gen)
+    gn = 0.1 * torch.randn(c.n, 3, device="cuda", generator=gen)
+    perm = torch.randperm(c.n, device="cuda", generator=gen).to(torch.int32)
+    a, ah = capi.mls_project_backward(x, idx, 0.03, gp, gn, 2, "mixed", order=order)
+    a, ah = a.clone(), ah.clone()
+    b, bh = capi.mls_project_backward(x, idx, 0.03, gp, gn, 2, "mixed", order=perm)
+    torch.cuda.synchronize()
+    grid.close()
+    assert torch.equal(a, b)
+    assert abs(float(ah) - float(bh)) <= 1e-6 * abs(float(ah))
+
+
 def test_autograd_function(capi):
     from paper_2401_03365_gb300 import mls
     c = workloads.bumpy_sphere(n=10_000, seed=40, k=16)

@@ -188,7 +188,7 @@ __device__ __forceinline__ CellGeom cell_geom(const GridView &g, const Cube &cb)
     return CellGeom{g.pts, g.side[cb.lev], g.frame.origin[0], g.frame.origin[1], g.frame.origin[2]};
 }
 
-template <typename F>
+template <int U, typename F>
 __device__ void for_each_point(const CellGeom &g, const Cube &cb, WarpBuf &wb, float4 q, float lim2, int lane,
                                F &&f) {
     // squared gap from q to the cube's slabs: lane 5 a + t (a < 3, t < 5)
@@ -255,41 +255,66 @@ __device__ void for_each_point(const CellGeom &g, const Cube &cb, WarpBuf &wb, f
         __syncwarp();
         int segbase = 0;     // cells starting before the current batch
         const unsigned le = (2u << lane) - 1u;
-        for (int base = 0; base < total; base += 32) {
-            const int e = base + lane;
-            const bool valid = e < total;
-            int j;
-            unsigned w = 0u;
-            if (total <= 32 * kMaxSegWords) {
-                w = wb.segbits[base >> 5];
-                j = segbase + __popc(w & le) - 1;
-            } else {              // very large rounds: search the inclusive counts
-                j = 0;
+        // U rounds of 32 points at a time: their loads are issued together
+        for (int base0 = 0; base0 < total; base0 += 32 * U) {
+            float4 pt[U];
+            int pos[U];
+            bool valid[U];
 #pragma unroll
-                for (int step = 16; step >= 1; step >>= 1) {
-                    int v = __shfl_sync(kFull, incl, j + step - 1);
-                    if (v <= e) j += step;
+            for (int u = 0; u < U; ++u) {
+                const int base = base0 + 32 * u;
+                const int e = base + lane;
+                valid[u] = e < total;
+                int j = 0;
+                unsigned w = 0u;
+                if (base < total) {
+                    if (total <= 32 * kMaxSegWords) {
+                        w = wb.segbits[base >> 5];
+                        j = segbase + __popc(w & le) - 1;
+                    } else {              // very large rounds: search the inclusive counts
+#pragma unroll
+                        for (int step = 16; step >= 1; step >>= 1) {
+                            int v = __shfl_sync(kFull, incl, j + step - 1);
+                            if (v <= e) j += step;
+                        }
+                    }
                 }
+                j &= 31;
+                const int st = __shfl_sync(kFull, my_start, j);
+                const int ex = __shfl_sync(kFull, excl, j);
+                segbase += __popc(w);
+                pos[u] = valid[u] ? st + (e - ex) : 0;
+                pt[u] = __ldg(g.pts + pos[u]);
             }
-            j &= 31;
-            const int st = __shfl_sync(kFull, my_start, j);
-            const int ex = __shfl_sync(kFull, excl, j);
-            segbase += __popc(w);
-            f(__ldg(g.pts + (valid ? st + (e - ex) : 0)), valid, valid ? st + (e - ex) : 0);
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+                if (base0 + 32 * u < total) f(pt[u], valid[u], pos[u]);
         }
         __syncwarp();
     }
 }
 
+// Key buckets, monotone in the key.  With lo = 0: 32 buckets of width
+// 1 / scale from 0 (the last also takes every larger key).  With lo > 0:
+// bucket 0 takes the keys below lo and buckets 1-31 split [lo, lo + 31 / scale).
+struct Bins {
+    float lo, scale;
+    __device__ __forceinline__ int operator()(float key) const {
+        if (lo > 0.f) return key < lo ? 0 : min(31, 1 + (int)((key - lo) * scale));
+        return min(31, (int)(key * scale));
+    }
+};
+
 // Keeps the visited words with key <= tau: the first kCap (word and sorted
 // position) go to the buffers.  Returns the number kept.  With hist, every
-// kept key is also counted in 32 buckets (bucket = key * scale) with each
-// bucket's largest key, for tightening tau when far too many are kept.
+// kept key is also counted in the 32 buckets of `bins` with each bucket's
+// largest key, for tightening tau when far too many are kept.
 // Out of line, one copy for all callers: the query solver around it is
 // inlined into the kernels, and a single body keeps the code they share in
 // the instruction cache.
+template <int U>
 __device__ __noinline__ int scan_keep(const CellGeom g, const Cube &cb, WarpBuf &wb, float4 q, float lim2,
-                                      float tau, float scale, int lane, bool hist) {
+                                      float tau, Bins bins, int lane, bool hist) {
     if (hist) {
         __syncwarp();
         wb.hist[lane] = 0;
@@ -297,7 +322,7 @@ __device__ __noinline__ int scan_keep(const CellGeom g, const Cube &cb, WarpBuf 
         __syncwarp();
     }
     int S = 0;
-    for_each_point(g, cb, wb, q, lim2, lane, [&](float4 p, bool valid, int pos) {
+    for_each_point<U>(g, cb, wb, q, lim2, lane, [&](float4 p, bool valid, int pos) {
         const float key = rank_key(p, q.x, q.y, q.z);
         const bool keep = valid && key <= tau;
         const unsigned m = __ballot_sync(kFull, keep);
@@ -308,7 +333,7 @@ __device__ __noinline__ int scan_keep(const CellGeom g, const Cube &cb, WarpBuf 
                 wb.spos[slot] = pos;
             }
             if (hist) {
-                const int bin = min(31, (int)(key * scale));
+                const int bin = bins(key);
                 atomicAdd(&wb.hist[bin], 1);
                 atomicMax(&wb.binmax[bin], __float_as_uint(key));
             }
@@ -320,14 +345,14 @@ __device__ __noinline__ int scan_keep(const CellGeom g, const Cube &cb, WarpBuf 
 }
 
 // Histogram (count and largest key) of the first min(S, kCap) kept words in
-// 32 buckets, bucket = key * scale.
-__device__ void bucket_hist(WarpBuf &wb, int S, float scale, int lane) {
+// the 32 buckets of `bins`.
+__device__ void bucket_hist(WarpBuf &wb, int S, Bins bins, int lane) {
     wb.hist[lane] = 0;
     wb.binmax[lane] = 0u;
     __syncwarp();
     for (int s = lane; s < min(S, kCap); s += 32) {
         const float key = __uint_as_float((uint32_t)(wb.surv[s] >> 32));
-        const int bin = min(31, (int)(key * scale));
+        const int bin = bins(key);
         atomicAdd(&wb.hist[bin], 1);
         atomicMax(&wb.binmax[bin], __float_as_uint(key));
     }
@@ -335,10 +360,15 @@ __device__ void bucket_hist(WarpBuf &wb, int S, float scale, int lane) {
 }
 
 // Smallest key bound with at least k histogrammed words at or below it: the
-// largest key of the buckets up to the one where the running count reaches k.
-__device__ float tighten(const WarpBuf &wb, int k, int lane, float fallback) {
+// largest key of the buckets up to the one where the running count reaches k
+// (that bucket's number in *bstar_out, -1 with the fallback; the running
+// count through it in *count_out).
+__device__ float tighten(const WarpBuf &wb, int k, int lane, float fallback, int *bstar_out = nullptr,
+                         int *count_out = nullptr) {
     const int incl = warp_incl_scan(wb.hist[lane], lane);
     const unsigned reach = __ballot_sync(kFull, incl >= k);
+    if (bstar_out) *bstar_out = reach ? __ffs(reach) - 1 : -1;
+    if (count_out) *count_out = __shfl_sync(kFull, incl, reach ? __ffs(reach) - 1 : 31);
     if (!reach) return fallback;
     const int bstar = __ffs(reach) - 1;
     unsigned mx = lane <= bstar ? wb.binmax[lane] : 0u;
@@ -350,15 +380,15 @@ __device__ float tighten(const WarpBuf &wb, int k, int lane, float fallback) {
 // Counting sort of the S <= kCap kept words by bucket, then rank inside the
 // bucket; the first k go to the output row and their sorted positions to
 // wb.nb.  Returns the k-th key.
-__device__ float rank_and_write(WarpBuf &wb, int S, float scale, int k, int lane, int32_t qi,
+__device__ float rank_and_write(WarpBuf &wb, int S, Bins bins, int k, int lane, int32_t qi,
                                 int32_t *__restrict__ out_idx, float *__restrict__ out_key) {
-    bucket_hist(wb, S, scale, lane);
+    bucket_hist(wb, S, bins, lane);
     const int h = wb.hist[lane];
     wb.fill[lane] = warp_incl_scan(h, lane) - h;
     __syncwarp();
     for (int s = lane; s < S; s += 32) {
         const unsigned long long v = wb.surv[s];
-        const int bin = min(31, (int)(__uint_as_float((uint32_t)(v >> 32)) * scale));
+        const int bin = bins(__uint_as_float((uint32_t)(v >> 32)));
         const int at = atomicAdd(&wb.fill[bin], 1);
         wb.tmp[at] = v;
         wb.tpos[at] = wb.spos[s];
@@ -367,7 +397,7 @@ __device__ float rank_and_write(WarpBuf &wb, int S, float scale, int k, int lane
     for (int p = lane; p < S; p += 32) {
         const unsigned long long v = wb.tmp[p];
         const float key = __uint_as_float((uint32_t)(v >> 32));
-        const int bin = min(31, (int)(key * scale));
+        const int bin = bins(key);
         const int end = wb.fill[bin], beg = end - wb.hist[bin];
         int rank = beg;
         for (int t = beg; t < end; ++t) rank += wb.tmp[t] < v;
@@ -454,7 +484,7 @@ __device__ float insertion_fallback(const GridView &g, const Cube &cb, WarpBuf &
                                     float *__restrict__ out_key) {
     TopK<KPL> top;
     top.init();
-    for_each_point(cell_geom(g, cb), cb, wb, q, lim2, lane, [&](float4 p, bool valid, int pos) {
+    for_each_point<1>(cell_geom(g, cb), cb, wb, q, lim2, lane, [&](float4 p, bool valid, int pos) {
         const float key = rank_key(p, q.x, q.y, q.z);
         top.offer(valid && key <= tau ? pack(key, p) : ~0ull, pos, k, lane);
     });
@@ -533,11 +563,16 @@ __device__ __forceinline__ float neighbour_bound(const GridView &g, const WarpBu
 // bound (from the 5x5x5 cube of the finest level holding k points) unless a
 // finite tau_in is given, then the cube search with culling, tightening and,
 // as a last resort, the sorted insertion list.  Returns the k-th key.
-template <int KPL>
+template <int KPL, int U>
 __device__ __forceinline__ float solve_query(const GridView &g, WarpBuf &wb, Cube &cb, float4 q, int32_t qi,
                                              const uint32_t c0[3], float tau, int k, int lane, bool may_defer,
                                              int32_t *__restrict__ out_idx, float *__restrict__ out_key) {
     const float eps2 = 2.0f * g.frame.eps;
+    // fewer than k points have a key below lo (known from a histogram of
+    // every key <= tau): later histograms split [lo, tau] only
+    float lo = 0.f;
+    int bstar = -1;
+    bool full_hist = false;
     if (!(tau < INFINITY)) {
         // fresh bound: coarsen until the cube holds k points, then take the
         // cells nearest to the query that hold 2k of them
@@ -572,10 +607,14 @@ __device__ __forceinline__ float solve_query(const GridView &g, WarpBuf &wb, Cub
         // within 3 sqrt(3) S < 5.2 S): bucket all their keys over [0, hi]
         const float far = ((all ? 5.2f * S : lim) + 1.7320509f * S + eps2) * kGrow * kGrow;
         const float hi = far * far * kGrow;
-        scan_keep(cell_geom(g, cb), cb, wb, q, lim2, INFINITY, hi > 0.f ? 32.0f / hi : 0.f, lane, true);
-        tau = tighten(wb, k, lane, hi);
+        const Bins fb{0.f, hi > 0.f ? 32.0f / hi : 0.f};
+        scan_keep<U>(cell_geom(g, cb), cb, wb, q, lim2, INFINITY, fb, lane, true);
+        int below = 0;
+        tau = tighten(wb, k, lane, hi, nullptr, &below);
+        // the visited points alone put more than 2 kCap keys at or below tau:
+        // a plain search would overflow, so the first one takes the histogram
+        full_hist = below > 2 * kCap;
     }
-    bool full_hist = false;
     for (int iter = 0;; ++iter) {
         // finest level whose cube (radius two cells) holds the search ball
         const float reach = sqrtf(tau) * kGrow * kGrow + eps2;
@@ -584,9 +623,11 @@ __device__ __forceinline__ float solve_query(const GridView &g, WarpBuf &wb, Cub
         load_cube(g, lev, c0, cb, lane);
         const float lim = (reach + eps2) * kGrow;
         const float lim2 = lim * lim;
-        const float scale = tau > 0.f ? 32.0f / tau : 0.f;
-        const int S = scan_keep(cell_geom(g, cb), cb, wb, q, lim2, tau, scale, lane, full_hist);
-        if (S >= k && S <= kCap) return rank_and_write(wb, S, scale, k, lane, qi, out_idx, out_key);
+        // ranking buckets over [0, tau]; tightening buckets over [lo, tau]
+        const Bins rb{0.f, tau > 0.f ? 32.0f / tau : 0.f};
+        const Bins tb = lo > 0.f ? Bins{lo, tau > lo ? 31.0f / (tau - lo) : 0.f} : rb;
+        const int S = scan_keep<U>(cell_geom(g, cb), cb, wb, q, lim2, tau, tb, lane, full_hist);
+        if (S >= k && S <= kCap) return rank_and_write(wb, S, rb, k, lane, qi, out_idx, out_key);
         if (S < k) {            // cannot happen for a valid bound: search everything
             tau = INFINITY;
             full_hist = false;
@@ -594,11 +635,15 @@ __device__ __forceinline__ float solve_query(const GridView &g, WarpBuf &wb, Cub
         }
         if (iter >= 8) return insertion_fallback<KPL>(g, cb, wb, q, lim2, tau, k, lane, qi, out_idx, out_key);
         if (full_hist) {        // buckets over every kept word: each round cuts ~32x
-            tau = tighten(wb, k, lane, tau);
+            tau = tighten(wb, k, lane, tau, &bstar);
+            // the buckets before the k-th key's hold fewer than k keys
+            const int first = lo > 0.f ? 1 : 0;     // first bucket of [lo, tau]
+            if (bstar > first && tb.scale > 0.f) lo = tb.lo + (float)(bstar - first) / tb.scale;
+            if (!(lo < tau)) lo = 0.f;              // a rounding tie at the edge: start over from 0
             full_hist = false;
         } else if (S <= 2 * kCap) {
             // a mild overflow: the first kCap kept words (real points) bound it
-            bucket_hist(wb, S, scale, lane);
+            bucket_hist(wb, S, rb, lane);
             tau = tighten(wb, k, lane, tau);
         } else {
             full_hist = true;   // rescan with buckets over all kept words
@@ -680,7 +725,7 @@ __global__ void __launch_bounds__(kChainThreads, kChainBlocksPerSm) k_knn_chain(
             // base cells, would search a large region: start afresh instead
             if (n_prev == 0 || tau > 9.0f * k1 || tau > big) tau = INFINITY;
             const float kth =
-                solve_query<KPL>(g, wb, cb, q, __float_as_int(q.w), c0, tau, k, lane, true, out_idx, out_key);
+                solve_query<KPL, 1>(g, wb, cb, q, __float_as_int(q.w), c0, tau, k, lane, true, out_idx, out_key);
             if (isnan(kth)) {
                 if (lane == 0) work[8 + atomicAdd(&work[1], 1)] = (int)sp;
                 n_prev = 0;
@@ -694,6 +739,11 @@ __global__ void __launch_bounds__(kChainThreads, kChainBlocksPerSm) k_knn_chain(
         }
     }
 }
+
+// The sparse queries scan many candidates each, with few warps left to hide
+// memory latency at the end of the pass: their candidate loads go four
+// rounds of 32 at a time.
+constexpr int kSparseRounds = 4;
 
 template <int KPL>
 __global__ void __launch_bounds__(kChainThreads) k_knn_sparse(GridView g, int k, int *__restrict__ work,
@@ -711,7 +761,7 @@ __global__ void __launch_bounds__(kChainThreads) k_knn_sparse(GridView g, int k,
         const float4 q = __ldg(g.pts + sp);
         const uint64_t key0 = __ldg(g.keys + sp);
         const uint32_t c0[3] = {compact3(key0), compact3(key0 >> 1), compact3(key0 >> 2)};
-        solve_query<KPL>(g, wb, cb, q, __float_as_int(q.w), c0, INFINITY, k, lane, false, out_idx, out_key);
+        solve_query<KPL, kSparseRounds>(g, wb, cb, q, __float_as_int(q.w), c0, INFINITY, k, lane, false, out_idx, out_key);
     }
 }
 
@@ -738,7 +788,7 @@ __global__ void __launch_bounds__(kChainThreads) k_radius(GridView g, float R2, 
     while (lev < g.top_level && !(2.0f * g.side[lev] > reach)) ++lev;
     const float lim = (reach + eps2) * kGrow;
     const float lim2 = lim * lim;
-    const float scale = R2 > 0.f ? 32.0f / R2 : 0.f;
+    const Bins bins{0.f, R2 > 0.f ? 32.0f / R2 : 0.f};
     const int64_t n_warps = (int64_t)gridDim.x * kChainWarps;
     Cube cb;
     cb.st = wb.cube_start + lane;
@@ -750,14 +800,14 @@ __global__ void __launch_bounds__(kChainThreads) k_radius(GridView g, float R2, 
             const uint64_t key0 = __ldg(g.keys + sp);
             const uint32_t c0[3] = {compact3(key0), compact3(key0 >> 1), compact3(key0 >> 2)};
             load_cube(g, lev, c0, cb, lane);
-            const int S = scan_keep(cell_geom(g, cb), cb, wb, q, lim2, R2, scale, lane, false);
+            const int S = scan_keep<1>(cell_geom(g, cb), cb, wb, q, lim2, R2, bins, lane, false);
             const int64_t qi = (int64_t)__float_as_int(q.w);
             if (!ROWS) {
                 if (lane == 0) count[qi] = S;
             } else if (S > kCap) {
                 if (lane == 0) atomicMax(overflow, S);
             } else {
-                rank_and_write(wb, S, scale, S, lane, 0, rows + offsets[qi], keys ? keys + offsets[qi] : nullptr);
+                rank_and_write(wb, S, bins, S, lane, 0, rows + offsets[qi], keys ? keys + offsets[qi] : nullptr);
             }
         }
     }

@@ -742,11 +742,11 @@ __global__ void __launch_bounds__(kChainThreads, kChainBlocksPerSm) k_knn_chain(
 
 // The sparse queries scan many candidates each, with few warps left to hide
 // memory latency at the end of the pass: their candidate loads go four
-// rounds of 32 at a time.
+// rounds of 32 at a time, and four blocks per SM stay resident (64 registers).
 constexpr int kSparseRounds = 4;
 
 template <int KPL>
-__global__ void __launch_bounds__(kChainThreads) k_knn_sparse(GridView g, int k, int *__restrict__ work,
+__global__ void __launch_bounds__(kChainThreads, 4) k_knn_sparse(GridView g, int k, int *__restrict__ work,
                                                              int32_t *__restrict__ out_idx,
                                                              float *__restrict__ out_key) {
     __shared__ WarpBuf bufs[kChainWarps];

@@ -313,8 +313,8 @@ struct Bins {
 // inlined into the kernels, and a single body keeps the code they share in
 // the instruction cache.
 template <int U>
-__device__ __noinline__ int scan_keep(const CellGeom g, const Cube &cb, WarpBuf &wb, float4 q, float lim2,
-                                      float tau, Bins bins, int lane, bool hist) {
+__device__ __forceinline__ int scan_keep_body(const CellGeom &g, const Cube &cb, WarpBuf &wb, float4 q, float lim2,
+                                              float tau, Bins bins, int lane, bool hist) {
     if (hist) {
         __syncwarp();
         wb.hist[lane] = 0;
@@ -342,6 +342,12 @@ __device__ __noinline__ int scan_keep(const CellGeom g, const Cube &cb, WarpBuf 
     });
     __syncwarp();
     return S;
+}
+
+template <int U>
+__device__ __noinline__ int scan_keep(const CellGeom g, const Cube &cb, WarpBuf &wb, float4 q, float lim2,
+                                      float tau, Bins bins, int lane, bool hist) {
+    return scan_keep_body<U>(g, cb, wb, q, lim2, tau, bins, lane, hist);
 }
 
 // Histogram (count and largest key) of the first min(S, kCap) kept words in
@@ -800,7 +806,9 @@ __global__ void __launch_bounds__(kChainThreads) k_radius(GridView g, float R2, 
             const uint64_t key0 = __ldg(g.keys + sp);
             const uint32_t c0[3] = {compact3(key0), compact3(key0 >> 1), compact3(key0 >> 2)};
             load_cube(g, lev, c0, cb, lane);
-            const int S = scan_keep<1>(cell_geom(g, cb), cb, wb, q, lim2, R2, bins, lane, false);
+            // inlined here: the radius kernel has no other large body to share
+            // the instruction cache with
+            const int S = scan_keep_body<1>(cell_geom(g, cb), cb, wb, q, lim2, R2, bins, lane, false);
             const int64_t qi = (int64_t)__float_as_int(q.w);
             if (!ROWS) {
                 if (lane == 0) count[qi] = S;

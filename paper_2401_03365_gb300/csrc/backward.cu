@@ -369,6 +369,40 @@ __global__ void k_count(const int32_t *__restrict__ idx, int64_t ne, const int32
     }
 }
 
+// The same counts with a processing order: a block takes the rows of
+// kCountSlots consecutive sorted positions, whose neighbours mostly lie within
+// a window of kCountWindow sorted positions around them; those are counted in
+// shared memory and added to the global counts once per block, the rest
+// directly.
+constexpr int kCountSlots = 256;
+constexpr int kCountWindow = 4096;
+
+__global__ void __launch_bounds__(256) k_count_window(const int32_t *__restrict__ idx, int64_t n, int k,
+                                                      const int32_t *__restrict__ order,
+                                                      const int32_t *__restrict__ pos, int32_t *__restrict__ cnt) {
+    __shared__ int32_t win[kCountWindow];
+    const int64_t s0 = (int64_t)blockIdx.x * kCountSlots;
+    const int64_t lo = s0 + kCountSlots / 2 - kCountWindow / 2;
+    for (int w = threadIdx.x; w < kCountWindow; w += blockDim.x) win[w] = 0;
+    __syncthreads();
+    const int edges = (int)(min(n, s0 + kCountSlots) - s0) * k;
+    for (int e = threadIdx.x; e < edges; e += blockDim.x) {
+        const int64_t slot = s0 + e / k;
+        const int64_t i = __ldg(order + slot);
+        const int32_t t = __ldg(pos + __ldg(idx + i * k + e % k));
+        const int64_t w = (int64_t)t - lo;
+        if (w >= 0 && w < kCountWindow)
+            atomicAdd(win + w, 1);
+        else
+            atomicAdd(cnt + t, 1);
+    }
+    __syncthreads();
+    for (int w = threadIdx.x; w < kCountWindow; w += blockDim.x) {
+        const int32_t c = win[w];
+        if (c) atomicAdd(cnt + (lo + w), c);      // c > 0 only for positions in [0, n)
+    }
+}
+
 // 2^e as a float, e in [-126, 127].
 __device__ __forceinline__ float pow2f(int e) { return __int_as_float((e + 127) << 23); }
 
@@ -531,7 +565,10 @@ int launch_backward(const float *xyz, int64_t n, const int32_t *idx, int k, floa
         k_inverse<<<grid_n, 256, 0, st>>>(order, n, pos);
         ++launches;
     }
-    k_count<<<(int)std::min<int64_t>((ne + 255) / 256, 152 * 32), 256, 0, st>>>(idx, ne, pos, cnt);
+    if (order)
+        k_count_window<<<(int)((n + kCountSlots - 1) / kCountSlots), 256, 0, st>>>(idx, n, k, order, pos, cnt);
+    else
+        k_count<<<(int)std::min<int64_t>((ne + 255) / 256, 152 * 32), 256, 0, st>>>(idx, ne, pos, cnt);
     int rc = device_exclusive_scan(cnt, off, n + 1, st);
     if (rc != MLS_OK) return rc;
     switch (degree) {

@@ -60,13 +60,27 @@ __global__ void k_bbox(const float *__restrict__ xyz, int64_t n, Misc *m) {
         }
     }
     bad = __any_sync(0xffffffffu, bad);
+    // the block's warps meet in shared memory: one set of global atomics per block
+    __shared__ int sb[7];
+    if (threadIdx.x < 3) {
+        sb[threadIdx.x] = 0x7fffffff;
+        sb[3 + threadIdx.x] = (int)0x80000000;
+    }
+    if (threadIdx.x == 0) sb[6] = 0;
+    __syncthreads();
     if ((threadIdx.x & 31) == 0) {
         for (int a = 0; a < 3; ++a) {
-            atomicMin(&m->bbox[a], float_to_ordered(lo[a]));
-            atomicMax(&m->bbox[3 + a], float_to_ordered(hi[a]));
+            atomicMin(&sb[a], float_to_ordered(lo[a]));
+            atomicMax(&sb[3 + a], float_to_ordered(hi[a]));
         }
-        if (bad) atomicOr(&m->nonfinite, 1);
+        if (bad) sb[6] = 1;
     }
+    __syncthreads();
+    if (threadIdx.x < 3) {
+        atomicMin(&m->bbox[threadIdx.x], sb[threadIdx.x]);
+        atomicMax(&m->bbox[3 + threadIdx.x], sb[3 + threadIdx.x]);
+    }
+    if (threadIdx.x == 0 && sb[6]) atomicOr(&m->nonfinite, 1);
 }
 
 // The level-0 frame: cell side s0 = a power of two with 2^21 cells spanning
@@ -262,10 +276,13 @@ __global__ void k_level_hist(const uint64_t *__restrict__ keys, int64_t n, Misc 
     __shared__ unsigned long long hist[kMaxLevels];
     if (threadIdx.x < kMaxLevels) hist[threadIdx.x] = 0;
     __syncthreads();
-    for (int64_t s = 1 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n;
-         s += (int64_t)gridDim.x * blockDim.x) {
-        int l = split_level(keys, s);
-        if (l >= 0) atomicAdd(&hist[l], 1ull);
+    // one shared atomic per distinct level among a warp's points
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t s0 = blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31); s0 < n; s0 += stride) {
+        const int64_t s = s0 + (threadIdx.x & 31) + 1;
+        const int l = s < n ? split_level(keys, s) : -1;
+        const unsigned peers = __match_any_sync(0xffffffffu, l);
+        if (l >= 0 && (threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&hist[l], (unsigned long long)__popc(peers));
     }
     __syncthreads();
     if (threadIdx.x < kMaxLevels && hist[threadIdx.x]) atomicAdd(&m->level_hist[threadIdx.x], hist[threadIdx.x]);

@@ -618,8 +618,10 @@ __device__ __forceinline__ float solve_query(const GridView &g, WarpBuf &wb, Cub
         int below = 0;
         tau = tighten(wb, k, lane, hi, nullptr, &below);
         // the visited points alone put more than 2 kCap keys at or below tau:
-        // a plain search would overflow, so the first one takes the histogram
-        full_hist = below > 2 * kCap;
+        // a plain search would overflow, so the first one takes the histogram;
+        // so does every deferred (sparse) query, whose first search usually
+        // overflows and costs tens of thousands of candidates
+        full_hist = below > 2 * kCap || !may_defer;
     }
     for (int iter = 0;; ++iter) {
         // finest level whose cube (radius two cells) holds the search ball

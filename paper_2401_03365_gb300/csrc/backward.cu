@@ -406,6 +406,28 @@ __global__ void __launch_bounds__(256) k_count_window(const int32_t *__restrict_
 // 2^e as a float, e in [-126, 127].
 __device__ __forceinline__ float pow2f(int e) { return __int_as_float((e + 127) << 23); }
 
+// v 2^s rounded to the nearest integer, ties to even, |v| 2^s < 2^62: the
+// same integer as converting the (exact) product v 2^s to a 64-bit integer,
+// computed from the float's bits with integer instructions (the conversion
+// itself runs on the FP64 pipe).
+__device__ __forceinline__ long long to_fixed(float v, int s) {
+    const uint32_t bits = __float_as_uint(v);
+    const uint32_t ex = (bits >> 23) & 0xffu, frac = bits & 0x7fffffu;
+    const uint32_t mant = ex ? (frac | 0x800000u) : frac;     // v = mant 2^(e2)
+    const int sh = (ex ? (int)ex - 150 : -149) + s;
+    long long q;
+    if (sh >= 0) {
+        q = (long long)mant << sh;
+    } else if (sh > -25) {
+        const int r = -sh;
+        const uint32_t t = mant >> r, rem = mant & ((1u << r) - 1u), half = 1u << (r - 1);
+        q = (long long)(t + ((rem > half || (rem == half && (t & 1u))) ? 1u : 0u));
+    } else {
+        q = 0;                                                // below one half
+    }
+    return (bits >> 31) ? -q : q;
+}
+
 // The integer q 2^-s, rounded once to float.
 __device__ __forceinline__ float from_fixed(long long q, int s) {
     float x = __ll2float_rn(q);
@@ -467,21 +489,17 @@ __global__ void __launch_bounds__(256) k_bucket_sum(int64_t n, const int32_t *__
         }
         const bool finite = mb[0] < kInf && mb[1] < kInf && mb[2] < kInf;
         if (finite) {
-            // scale 2^s = f1 f2, both factors powers of two (two steps past 2^120)
-            float f1[3], f2[3];
             int sh[3];
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
                 const int E = max((int)(mb[a] >> 23) - 127, -126);
                 sh[a] = 61 - E - lc;
-                f1[a] = sh[a] > 120 ? pow2f(120) : 1.f;
-                f2[a] = pow2f(sh[a] > 120 ? sh[a] - 120 : sh[a]);
             }
             long long q[3] = {0, 0, 0};
             auto add = [&](float4 a) {
-                q[0] += __float2ll_rn(a.x * f1[0] * f2[0]);
-                q[1] += __float2ll_rn(a.y * f1[1] * f2[1]);
-                q[2] += __float2ll_rn(a.z * f1[2] * f2[2]);
+                q[0] += to_fixed(a.x, sh[0]);
+                q[1] += to_fixed(a.y, sh[1]);
+                q[2] += to_fixed(a.z, sh[2]);
             };
 #pragma unroll
             for (int r = 0; r < V; ++r) add(v[r]);

@@ -221,7 +221,7 @@ def run_ours(args):
     capi.mls_knn(grid, K, out_idx=idx)
     h = 2.0 * float(capi.mls_mean_knn_dist(x, idx).item())
 
-    def step(xin, ev=None, after_forward=None):
+    def step(xin, ev=None, before_forward_out=None, after_forward=None, before_backward=None):
         nonlocal grid
         if ev: ev[0].record(stream)
         grid = capi.mls_build_grid(xin, 0.0, K, grid=grid)
@@ -229,9 +229,11 @@ def run_ours(args):
         capi.mls_knn(grid, K, out_idx=idx)
         if ev: ev[2].record(stream)
         order = capi.mls_grid_order(grid)
+        if before_forward_out: before_forward_out()
         capi.mls_project(xin, idx, h, 2, "mixed", order=order, out_xyz=out_xyz, out_normal=out_n, out_status=out_st)
         if ev: ev[3].record(stream)
         if after_forward: after_forward()
+        if before_backward: before_backward()
         capi.mls_project_backward(xin, idx, h, gp, gn, 2, "mixed", order=order, out_grad_xyz=grad,
                                   out_grad_h=grad_h)
         if ev: ev[4].record(stream)
@@ -262,43 +264,78 @@ def run_ours(args):
     value = job_throughput(world, n_pts, step_ms)
 
     # end to end through the public API with host buffers: every step copies
-    # the points in from pinned memory, runs the four calls, and copies the
-    # projected points, normals, status and gradient back
+    # its points in from pinned memory, runs the four calls, and copies the
+    # projected points, normals, status and gradient back.  The copies run on
+    # two side streams, ordered by events: the next step's points go into the
+    # other of two device buffers while this step computes, the projected
+    # points, normals and status go back while the adjoint runs, the gradient
+    # while the next step runs.  One timed region over all the steps, from the
+    # first copy in to the last copy out (the L2 flush between steps included).
     host_in = torch.from_numpy(cloud.xyz).pin_memory()
     host_xyz = torch.empty((n_pts, 3), dtype=torch.float32).pin_memory()
     host_n = torch.empty((n_pts, 3), dtype=torch.float32).pin_memory()
     host_st = torch.empty(n_pts, dtype=torch.uint8).pin_memory()
     host_g = torch.empty((n_pts, 3), dtype=torch.float32).pin_memory()
-    x_e2e = torch.empty_like(x)
-    e2e_ms = []
-    # the projected points, normals and status go back on a second stream
-    # while the adjoint runs; the gradient follows the adjoint
-    copy_stream = torch.cuda.Stream(device=dev)
+    x_bufs = [torch.empty_like(x), torch.empty_like(x)]
+    copy_in = torch.cuda.Stream(device=dev)
+    copy_out = torch.cuda.Stream(device=dev)
 
-    def copy_forward_out():
-        fwd_done = torch.cuda.Event()
-        fwd_done.record(stream)
-        copy_stream.wait_event(fwd_done)
-        with torch.cuda.stream(copy_stream):
-            host_xyz.copy_(out_xyz, non_blocking=True)
-            host_n.copy_(out_n, non_blocking=True)
-            host_st.copy_(out_st, non_blocking=True)
-
-    for s in range(min(max(args.steps, 3), 10) + 1):
-        flush.zero_()
+    def e2e_run(n_steps):
+        in_ready = [torch.cuda.Event(), torch.cuda.Event()]
+        step_done = [None] * n_steps
+        fwd_copied = [None] * n_steps
+        grad_copied = [None] * n_steps
+        start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        x_e2e.copy_(host_in, non_blocking=True)
-        step(x_e2e, after_forward=copy_forward_out)
-        host_g.copy_(grad, non_blocking=True)
-        copies_done = torch.cuda.Event()
-        copies_done.record(copy_stream)
-        stream.wait_event(copies_done)
-        b.record(stream)
-        b.synchronize()
-        if s > 0:                      # the first one warms the copy path
-            e2e_ms.append(a.elapsed_time(b))
+        start.record(stream)
+        copy_in.wait_event(start)
+        with torch.cuda.stream(copy_in):
+            x_bufs[0].copy_(host_in, non_blocking=True)
+        in_ready[0].record(copy_in)
+        for s in range(n_steps):
+            if s > 0:
+                flush.zero_()
+            stream.wait_event(in_ready[s % 2])
+            if s + 1 < n_steps:
+                if s > 0:                   # the other buffer is free once the previous step is done
+                    copy_in.wait_event(step_done[s - 1])
+                with torch.cuda.stream(copy_in):
+                    x_bufs[(s + 1) % 2].copy_(host_in, non_blocking=True)
+                in_ready[(s + 1) % 2].record(copy_in)
+
+            def wait_fwd_copy(s=s):
+                if s > 0: stream.wait_event(fwd_copied[s - 1])
+
+            def copy_fwd(s=s):
+                ev = torch.cuda.Event()
+                ev.record(stream)
+                copy_out.wait_event(ev)
+                with torch.cuda.stream(copy_out):
+                    host_xyz.copy_(out_xyz, non_blocking=True)
+                    host_n.copy_(out_n, non_blocking=True)
+                    host_st.copy_(out_st, non_blocking=True)
+                fwd_copied[s] = torch.cuda.Event()
+                fwd_copied[s].record(copy_out)
+
+            def wait_grad_copy(s=s):
+                if s > 0: stream.wait_event(grad_copied[s - 1])
+
+            step(x_bufs[s % 2], before_forward_out=wait_fwd_copy, after_forward=copy_fwd,
+                 before_backward=wait_grad_copy)
+            step_done[s] = torch.cuda.Event()
+            step_done[s].record(stream)
+            copy_out.wait_event(step_done[s])
+            with torch.cuda.stream(copy_out):
+                host_g.copy_(grad, non_blocking=True)
+            grad_copied[s] = torch.cuda.Event()
+            grad_copied[s].record(copy_out)
+        stream.wait_event(grad_copied[n_steps - 1])
+        end.record(stream)
+        end.synchronize()
+        return start.elapsed_time(end) / n_steps
+
+    e2e_run(2)                                  # warms the copy path
+    e2e_ms = [e2e_run(min(max(args.steps, 3), 10))]
     (e2e_step_ms,) = max_over_ranks([float(np.mean(e2e_ms))], dev)
     e2e_value = job_throughput(world, n_pts, e2e_step_ms)
 

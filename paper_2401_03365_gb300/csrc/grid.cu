@@ -431,13 +431,20 @@ int build_grid(mls_grid *g, const float *xyz, int64_t n, float cell_size, int k_
     k_keys<<<blocks_for(n, T), T, 0, st>>>(xyz, n, m, g->keys, g->perm);
     MLS_CUDA_TRY(cudaGetLastError());
 
-    // radix sort, 8 passes of 8 bits over the 63-bit keys
+    // radix sort of the keys' bits from level sort_level up, 8 bits a pass
+    // (all 63 bits, 8 passes, on a first build; the search never uses the
+    // cells below the base level, so later builds of the handle skip the bits
+    // below one level under the last base: points within such a cell keep
+    // their input order)
+    const int sort_level = cell_size > 0.0f ? 0 : g->sort_level;
     int nblocks = (int)((n + kSortTile - 1) / kSortTile);
     int rc = grow(&g->block_hist, (size_t)nblocks * kDigits, &g->block_hist_cap);
     if (rc) return rc;
     rc = grow(&g->scan_tmp, (size_t)kDigits + 64, &g->scan_tmp_cap);
     if (rc) return rc;
-    for (int shift = 0; shift < kKeyBits; shift += kDigitBits) {
+    int passes = 0;
+    for (int shift = 3 * sort_level; shift < kKeyBits; shift += kDigitBits) {
+        ++passes;
         k_radix_hist<<<nblocks, kSortThreads, 0, st>>>(g->keys, n, shift, nblocks, g->block_hist);
         k_radix_scan<<<kDigits, 1024, 0, st>>>(g->block_hist, nblocks, g->scan_tmp);
         k_radix_scatter<<<nblocks, kSortThreads, 0, st>>>(g->keys, g->perm, n, shift, nblocks, g->block_hist,
@@ -449,7 +456,7 @@ int build_grid(mls_grid *g, const float *xyz, int64_t n, float cell_size, int k_
         g->perm = g->perm_alt;
         g->perm_alt = tp;
     }
-    count_launches(4 + 3 * ((kKeyBits + kDigitBits - 1) / kDigitBits));
+    count_launches(4 + 3 * passes);
     k_gather_pts<<<blocks_for(n, T), T, 0, st>>>(xyz, g->perm, n, g->pts);
     k_level_hist<<<blocks_for(n, T), T, 0, st>>>(g->keys, n, m);
     MLS_CUDA_TRY(cudaGetLastError());
@@ -473,9 +480,10 @@ int build_grid(mls_grid *g, const float *xyz, int64_t n, float cell_size, int k_
         if (base < 0) base = 0;
         if (base > top) base = top;
     } else {
-        // finest level whose mean occupancy reaches k_hint / 6
+        // finest level whose mean occupancy reaches k_hint / 6 (the cell
+        // counts are exact from the sorted level up)
         double target = k_hint / 6.0 > 1.0 ? k_hint / 6.0 : 1.0;
-        for (int l = 0; l <= top; ++l)
+        for (int l = sort_level; l <= top; ++l)
             if ((double)n / (double)cells[l] >= target) {
                 base = l;
                 break;
@@ -487,6 +495,7 @@ int build_grid(mls_grid *g, const float *xyz, int64_t n, float cell_size, int k_
     v.frame = hm->frame;
     v.n = (int32_t)n;
     v.base_level = base;
+    g->sort_level = base > 0 ? base - 1 : 0;
     v.top_level = top;
     for (int l = 0; l < kMaxLevels; ++l) v.side[l] = std::ldexp(hm->frame.s0, l);
     int nlev = top - base + 1;

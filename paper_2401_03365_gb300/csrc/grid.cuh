@@ -82,4 +82,8 @@ struct mls_grid {
     size_t hcap[mls::kMaxLevels] = {};
     size_t ccap[mls::kMaxLevels] = {};
     mls::GridView view{};
+    // The next build orders the keys only by their bits at and above this
+    // level (the cells finer than it are never searched): one level below
+    // the base level of the last build; 0 (the whole key) at first.
+    int sort_level = 0;
 };

@@ -54,21 +54,35 @@ def test_knn_full_size_torus_sampled(capi):
 
 
 def test_knn_deterministic_and_grid_reuse(capi):
+    """A rebuilt handle orders the keys only from one level below its last
+    base level: rows stay exact when it is rebuilt on another cloud (whose
+    base level may be finer), on the first again, and with another k."""
     xyz, k = knn_case("torus100k_k32")
     x = torch.from_numpy(xyz).cuda()
     grid = capi.mls_build_grid(x, 0.0, k)
     a, _ = capi.mls_knn(grid, k)
     a = a.clone()
     # rebuild in place on another cloud, then on the first again
-    y = torch.from_numpy(knn_case("sphere20k_k20")[0]).cuda()
+    ys, _ = knn_case("sphere20k_k20")
+    y = torch.from_numpy(ys).cuda()
     grid = capi.mls_build_grid(y, 0.0, k, grid=grid)
     b, _ = capi.mls_knn(grid, k)
-    assert b.shape[0] == y.shape[0]
+    b = b.clone()
     grid = capi.mls_build_grid(x, 0.0, k, grid=grid)
     c, _ = capi.mls_knn(grid, k)
+    c = c.clone()
+    grid = capi.mls_build_grid(x, 0.0, 8, grid=grid)
+    d, _ = capi.mls_knn(grid, 8)
+    grid = capi.mls_build_grid(x, 0.0, 8, grid=grid)
+    e, _ = capi.mls_knn(grid, 8)
     torch.cuda.synchronize()
     grid.close()
     assert torch.equal(a, c)
+    assert np.array_equal(a.cpu().numpy(), oracle_knn(xyz, k)[0])
+    assert np.array_equal(b.cpu().numpy(), oracle_knn(ys, k)[0])
+    idx8 = oracle_knn(xyz, 8)[0]
+    assert np.array_equal(d.cpu().numpy(), idx8)
+    assert np.array_equal(e.cpu().numpy(), idx8)
 
 
 @pytest.mark.parametrize("cell_size", [0.002, 0.05, 1.0])

@@ -30,13 +30,18 @@ __global__ void k_pack_xyz4(const float *__restrict__ xyz, int64_t n, float4 *__
 // project_point on its own point.  Eight blocks per SM (64 registers): the
 // kernel waits on its neighbour gathers, and the extra warps hide that
 // latency (measured 11 % faster than five blocks at 88 registers).
-template <int DEG, int PREC, bool LEVIN = false>
+// With DEFER (the mixed form with scratch available), a point that needs an
+// FP64 step is not finished here: its slot goes to deferred[] (count in
+// *n_deferred) for k_project_deferred, so that the warps of this kernel never
+// wait on FP64 arithmetic (GB300's FP64 rate is a small fraction of FP32).
+template <int DEG, int PREC, bool LEVIN = false, bool DEFER = false>
 __global__ void __launch_bounds__(kProjThreads, LEVIN ? 5 : 8) k_project(const float4 *__restrict__ xyz4, int64_t n,
                                                           const int32_t *__restrict__ idx, int k, float h,
                                                           const int32_t *__restrict__ order,
                                                           float *__restrict__ out_xyz, float *__restrict__ out_n,
                                                           uint8_t *__restrict__ status, int max_iter,
-                                                          float tol) {
+                                                          float tol, int32_t *__restrict__ deferred,
+                                                          int32_t *__restrict__ n_deferred) {
     extern __shared__ int32_t rows[];
     const int lane = threadIdx.x & 31;
     int32_t *my_rows = rows + (threadIdx.x >> 5) * k * 32;
@@ -54,8 +59,12 @@ __global__ void __launch_bounds__(kProjThreads, LEVIN ? 5 : 8) k_project(const f
     if (slot >= n) return;
     const float4 r4 = __ldg(xyz4 + i);
     float out[3], nf[3];
-    const uint8_t st = project_point<DEG, PREC, LEVIN>(
+    const uint8_t st = project_point<DEG, PREC, LEVIN, DEFER>(
         xyz4, [&](int j) { return my_rows[j * 32 + lane]; }, k, 0, 1, h, r4.x, r4.y, r4.z, out, nf, max_iter, tol);
+    if (DEFER && st == kDeferFP64) {
+        deferred[atomicAdd(n_deferred, 1)] = (int32_t)slot;
+        return;
+    }
     out_xyz[3 * i] = out[0];
     out_xyz[3 * i + 1] = out[1];
     out_xyz[3 * i + 2] = out[2];
@@ -65,6 +74,39 @@ __global__ void __launch_bounds__(kProjThreads, LEVIN ? 5 : 8) k_project(const f
         out_n[3 * i + 2] = nf[2];
     }
     if (status) status[i] = st;
+}
+
+// The deferred points of the mixed form, one thread each: the same routine
+// with its FP64 steps, rows read from global memory (same values and order
+// as the first pass, so the results are those of a single pass).
+template <int DEG>
+__global__ void __launch_bounds__(kProjThreads) k_project_deferred(const float4 *__restrict__ xyz4, int64_t n,
+                                                                  const int32_t *__restrict__ idx, int k, float h,
+                                                                  const int32_t *__restrict__ order,
+                                                                  const int32_t *__restrict__ deferred,
+                                                                  const int32_t *__restrict__ n_deferred,
+                                                                  float *__restrict__ out_xyz,
+                                                                  float *__restrict__ out_n,
+                                                                  uint8_t *__restrict__ status) {
+    const int count = *n_deferred;
+    for (int d = blockIdx.x * blockDim.x + threadIdx.x; d < count; d += gridDim.x * blockDim.x) {
+        const int64_t slot = deferred[d];
+        const int64_t i = order ? (int64_t)__ldg(order + slot) : slot;
+        const int32_t *row = idx + i * k;
+        const float4 r4 = __ldg(xyz4 + i);
+        float out[3], nf[3];
+        const uint8_t st = project_point<DEG, MLS_PREC_MIXED>(
+            xyz4, [&](int j) { return __ldg(row + j); }, k, 0, 1, h, r4.x, r4.y, r4.z, out, nf);
+        out_xyz[3 * i] = out[0];
+        out_xyz[3 * i + 1] = out[1];
+        out_xyz[3 * i + 2] = out[2];
+        if (out_n) {
+            out_n[3 * i] = nf[0];
+            out_n[3 * i + 1] = nf[1];
+            out_n[3 * i + 2] = nf[2];
+        }
+        if (status) status[i] = st;
+    }
 }
 
 // Variable neighbourhoods (CSR rows, e.g. the radius-R sets of Sec. 1.4),
@@ -206,15 +248,26 @@ int launch_deg(const float *xyz, int64_t n, const int32_t *idx, int k, float h, 
         k_pack_xyz4<<<(int)std::min<int64_t>((n + 255) / 256, 152 * 16), 256, 0, st>>>(xyz, n, xyz4);
         const size_t smem = (size_t)k * 32 * sizeof(int32_t) * (kProjThreads / 32);
         if (precision == MLS_PREC_MIXED) {
-            auto kern = k_project<DEG, MLS_PREC_MIXED>;
+            // FP64 points deferred to a second, compact pass
+            int32_t *deferred = nullptr;
+            MLS_CUDA_TRY(scratch_alloc((void **)&deferred, (size_t)(n + 1) * sizeof(int32_t), st));
+            int32_t *n_deferred = deferred + n;
+            MLS_CUDA_TRY(cudaMemsetAsync(n_deferred, 0, sizeof(int32_t), st));
+            auto kern = k_project<DEG, MLS_PREC_MIXED, false, true>;
             MLS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            kern<<<blocks, kProjThreads, smem, st>>>(xyz4, n, idx, k, h, order, out_xyz, out_n, status, 1, 0.f);
+            kern<<<blocks, kProjThreads, smem, st>>>(xyz4, n, idx, k, h, order, out_xyz, out_n, status, 1, 0.f,
+                                                     deferred, n_deferred);
+            k_project_deferred<DEG><<<152 * 2, kProjThreads, 0, st>>>(xyz4, n, idx, k, h, order, deferred, n_deferred,
+                                                                     out_xyz, out_n, status);
+            count_launches(3);
+            MLS_CUDA_TRY(cudaFreeAsync(deferred, st));
         } else {
             auto kern = k_project<DEG, MLS_PREC_FP32>;
             MLS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            kern<<<blocks, kProjThreads, smem, st>>>(xyz4, n, idx, k, h, order, out_xyz, out_n, status, 1, 0.f);
+            kern<<<blocks, kProjThreads, smem, st>>>(xyz4, n, idx, k, h, order, out_xyz, out_n, status, 1, 0.f,
+                                                     nullptr, nullptr);
+            count_launches(2);
         }
-        count_launches(2);
         MLS_CUDA_TRY(cudaFreeAsync(xyz4, st));
     }
     MLS_CUDA_TRY(cudaGetLastError());
@@ -278,11 +331,13 @@ int launch_levin_deg(const float *xyz, int64_t n, const int32_t *idx, int k, flo
     if (precision == MLS_PREC_MIXED) {
         auto kern = k_project<DEG, MLS_PREC_MIXED, true>;
         MLS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        kern<<<blocks, kProjThreads, smem, st>>>(xyz4, n, idx, k, h, order, out_xyz, out_n, status, max_iter, tol);
+        kern<<<blocks, kProjThreads, smem, st>>>(xyz4, n, idx, k, h, order, out_xyz, out_n, status, max_iter, tol,
+                                                 nullptr, nullptr);
     } else {
         auto kern = k_project<DEG, MLS_PREC_FP32, true>;
         MLS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        kern<<<blocks, kProjThreads, smem, st>>>(xyz4, n, idx, k, h, order, out_xyz, out_n, status, max_iter, tol);
+        kern<<<blocks, kProjThreads, smem, st>>>(xyz4, n, idx, k, h, order, out_xyz, out_n, status, max_iter, tol,
+                                                 nullptr, nullptr);
     }
     count_launches(2);
     MLS_CUDA_TRY(cudaFreeAsync(xyz4, st));
@@ -350,11 +405,13 @@ int launch_noalloc(const float *xyz, int64_t n, const int32_t *idx, int k, float
         if (precision == MLS_PREC_MIXED) {
             auto kern = k_project<DEG, MLS_PREC_MIXED>;
             MLS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            kern<<<blocks, kProjThreads, smem, st>>>(xyz4, n, idx, k, h, order, out_xyz, out_n, status, 1, 0.f);
+            kern<<<blocks, kProjThreads, smem, st>>>(xyz4, n, idx, k, h, order, out_xyz, out_n, status, 1, 0.f,
+                                                     nullptr, nullptr);
         } else {
             auto kern = k_project<DEG, MLS_PREC_FP32>;
             MLS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            kern<<<blocks, kProjThreads, smem, st>>>(xyz4, n, idx, k, h, order, out_xyz, out_n, status, 1, 0.f);
+            kern<<<blocks, kProjThreads, smem, st>>>(xyz4, n, idx, k, h, order, out_xyz, out_n, status, 1, 0.f,
+                                                     nullptr, nullptr);
         }
         count_launches(2);
     }

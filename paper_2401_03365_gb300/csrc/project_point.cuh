@@ -24,6 +24,9 @@ namespace mls {
 
 constexpr float kMixedGapFlag = 1e-3f;     // FP32 eigensolve trusted above this gap ratio
 constexpr float kMixedCondFlag = 1e5f;     // FP32 Cholesky trusted below this condition estimate
+// Returned instead of a status when DEFER is set and the point needs an FP64
+// step: nothing is computed for it, a later pass runs it without DEFER.
+constexpr uint8_t kDeferFP64 = 0x80;
 
 // Row: callable, Row(j) = index of the point's neighbour j.  All 32 lanes of
 // the warp must call this together when G > 1 (the merges are warp shuffles,
@@ -37,7 +40,7 @@ constexpr float kMixedCondFlag = 1e5f;     // FP32 Cholesky trusted below this c
 // max_iter passes, else status bit MLS_PT_NOT_CONVERGED); the height fit
 // then uses the weights about the final q.  Points stop after different
 // numbers of passes, so LEVIN takes one lane per point (G = 1).
-template <int DEG, int PREC, bool LEVIN = false, class Row>
+template <int DEG, int PREC, bool LEVIN = false, bool DEFER = false, class Row>
 __device__ __forceinline__ uint8_t project_point(const float4 *__restrict__ xyz4, const Row &row, int k, int sub,
                                                  int G, float h, float rx, float ry, float rz, float out[3],
                                                  float nf[3], int max_iter = 1, float tol = 0.f) {
@@ -118,6 +121,7 @@ __device__ __forceinline__ uint8_t project_point(const float4 *__restrict__ xyz4
             // the FP32 eigenvector error grows like eps * l2 / (l1 - l0): in the
             // mixed form, narrow gaps are solved again in FP64 from the same moments
             if (PREC == MLS_PREC_MIXED && (!(lam[2] > 0.f) || (lam[1] - lam[0]) < kMixedGapFlag * lam[2])) {
+                if (DEFER) return kDeferFP64;
                 double Cd[6], nd[3], e1d[3], e2d[3], ld[3];
 #pragma unroll
                 for (int c = 0; c < 6; ++c) Cd[c] = (double)C[c];
@@ -219,6 +223,7 @@ __device__ __forceinline__ uint8_t project_point(const float4 *__restrict__ xyz4
     float cond;
     float a0 = solve_a0<float, DEG>(mom, rhs, true, singular, cond);
     if (PREC == MLS_PREC_MIXED && (singular || !(cond < kMixedCondFlag))) {
+        if (DEFER) return kDeferFP64;
         double condd;
         a0 = (float)solve_a0<double, DEG>(mom, rhs, false, singular, condd);
         st |= MLS_PT_FP64_USED;

@@ -61,6 +61,26 @@ def test_noalloc_matches_mls_project_on_consecutive_calls(capi, precision):
         grid.close()
 
 
+def test_deferred_fp64_pass_is_bit_identical_to_inline(capi):
+    """mls_project (mixed) finishes the points that need FP64 in a second,
+    compact pass; the no-alloc form finishes them inline.  Same arithmetic:
+    bit-identical outputs, and the cloud (1 % outliers) has such points."""
+    c = workloads.torus(n=150_000, seed=23)
+    x = torch.from_numpy(c.xyz).cuda()
+    grid = capi.mls_build_grid(x, 0.0, c.k)
+    idx, _ = capi.mls_knn(grid, c.k)
+    order = capi.mls_grid_order(grid)
+    h = 2.0 * float(capi.mls_mean_knn_dist(x, idx).item())
+    for o in (order, None):
+        ref_xyz, ref_n, ref_st = capi.mls_project(x, idx, h, 2, "mixed", order=o)
+        rc, out, nrm, st = _noalloc(capi, x, idx, h, 2, "mixed", o)
+        torch.cuda.synchronize()
+        assert rc == 0, capi.mls_last_error()
+        assert int(((ref_st & capi.MLS_PT_FP64_USED) != 0).sum()) > 0
+        assert torch.equal(out, ref_xyz) and torch.equal(nrm, ref_n) and torch.equal(st, ref_st)
+    grid.close()
+
+
 def test_noalloc_rejects_clouds_beyond_its_scratch(capi):
     n = capi.MLS_NOALLOC_MAX_POINTS + 1
     x = torch.zeros((n, 3), device="cuda")

@@ -116,11 +116,13 @@ int64_t mls_grid_size(const mls_grid *g);
 
 /* Device pointer to the grid's order of the points: order[s] is the index of
  * the point at sorted position s (n int32, owned by the grid, valid until the
- * grid is rebuilt or destroyed).  The order is the Morton order of the cells
- * down to one level below the base level of the handle's previous build (the
- * whole 63-bit key on a handle's first build); points within one such cell
- * keep their input order.  Passing it to mls_project as d_order makes
- * neighbouring threads work on neighbouring points. */
+ * grid is rebuilt or destroyed).  The order is the Hilbert-curve order of the
+ * level-0 cells (Skilling's index), resolved down to about one level below
+ * the base level of the handle's previous build (the whole 63-bit index on a
+ * handle's first build); points within one unresolved cell keep their input
+ * order.  Every cell of every level searched is a run of consecutive
+ * positions.  Passing it to mls_project as d_order makes neighbouring threads
+ * work on neighbouring points. */
 const int32_t *mls_grid_order(const mls_grid *g);
 
 /*

@@ -1,7 +1,14 @@
-// Grid build (the spatial index of Sec. 2.2, with Morton ordering as the paper
-// suggests for unordered clouds): bounding box, level-0 Morton keys, an LSD
-// radix sort of (key, point index), the sorted float4 points, and one hash
-// table of occupied cells per level from the base level up.
+// Grid build (the spatial index of Sec. 2.2, with a space-filling-curve order
+// as the paper suggests for unordered clouds): bounding box, level-0 cell
+// keys, an LSD radix sort of (key, point index), the sorted float4 points with
+// their Morton cell keys, and one hash table of occupied cells per level from
+// the base level up.  The sort key is the cell's index along the Hilbert
+// curve: like the Morton key it lists every cell of every level as one run of
+// consecutive positions (its top 3 l bits name the level-l cell), and
+// consecutive cells along it are always face neighbours, so consecutive
+// points are closer than in Morton order (the kNN bounds each query from the
+// one before it).  The hash tables and the search keep Morton keys.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -113,6 +120,35 @@ __global__ void k_frame(Misc *m) {
     m->frame = f;
 }
 
+// Index of the level-0 cell (x, y, z) along the 3-D Hilbert curve of
+// kMortonBits levels, by Skilling's transform ("Programming the Hilbert
+// curve", AIP Conf. Proc. 707, 2004): the coordinates are turned in place into
+// the transposed index (undo the curve's rotations and reflections from the
+// top bit down, then Gray-decode), whose bits, interleaved with the first
+// coordinate most significant in every triple, give the index.
+__device__ __forceinline__ uint64_t hilbert3(uint32_t x, uint32_t y, uint32_t z) {
+    uint32_t X[3] = {x, y, z};
+    for (uint32_t Q = 1u << (kMortonBits - 1); Q > 1; Q >>= 1) {
+        const uint32_t P = Q - 1;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            if (X[i] & Q) {
+                X[0] ^= P;                              // reflect
+            } else {
+                const uint32_t t = (X[0] ^ X[i]) & P;   // swap the low bits of X[0] and X[i]
+                X[0] ^= t;
+                X[i] ^= t;
+            }
+        }
+    }
+    X[1] ^= X[0];
+    X[2] ^= X[1];
+    uint32_t t = 0;
+    for (uint32_t Q = 1u << (kMortonBits - 1); Q > 1; Q >>= 1)
+        if (X[2] & Q) t ^= Q - 1;
+    return morton3(X[2] ^ t, X[1] ^ t, X[0] ^ t);
+}
+
 __global__ void k_keys(const float *__restrict__ xyz, int64_t n, const Misc *__restrict__ m,
                        uint64_t *__restrict__ keys, int32_t *__restrict__ perm) {
     GridFrame f = m->frame;
@@ -121,7 +157,7 @@ __global__ void k_keys(const float *__restrict__ xyz, int64_t n, const Misc *__r
         uint32_t c[3];
 #pragma unroll
         for (int a = 0; a < 3; ++a) c[a] = cell_coord(xyz[3 * i + a], f.origin[a], f.inv_s0);
-        keys[i] = morton3(c[0], c[1], c[2]);
+        keys[i] = hilbert3(c[0], c[1], c[2]);
         perm[i] = (int32_t)i;
     }
 }
@@ -254,12 +290,16 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(
 }
 
 __global__ void k_gather_pts(const float *__restrict__ xyz, const int32_t *__restrict__ perm,
-                             int64_t n, float4 *__restrict__ pts) {
+                             int64_t n, const Misc *__restrict__ m, float4 *__restrict__ pts,
+                             uint64_t *__restrict__ mkeys) {
+    GridFrame f = m->frame;
     for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n;
          s += (int64_t)gridDim.x * blockDim.x) {
         int32_t i = perm[s];
-        pts[s] = make_float4(xyz[3 * (int64_t)i], xyz[3 * (int64_t)i + 1], xyz[3 * (int64_t)i + 2],
-                             __int_as_float(i));
+        const float p[3] = {xyz[3 * (int64_t)i], xyz[3 * (int64_t)i + 1], xyz[3 * (int64_t)i + 2]};
+        pts[s] = make_float4(p[0], p[1], p[2], __int_as_float(i));
+        mkeys[s] = morton3(cell_coord(p[0], f.origin[0], f.inv_s0), cell_coord(p[1], f.origin[1], f.inv_s0),
+                           cell_coord(p[2], f.origin[2], f.inv_s0));
     }
 }
 
@@ -310,6 +350,7 @@ __global__ void __launch_bounds__(kHeadThreads) k_head_count(const uint64_t *__r
 }
 
 __global__ void __launch_bounds__(kHeadThreads) k_head_write(const uint64_t *__restrict__ keys,
+                                                              const uint64_t *__restrict__ mkeys,
                                                               int64_t n, int base, int top, int nblocks,
                                                               const int32_t *__restrict__ offsets,
                                                               GridView view, uint64_t **cell_key) {
@@ -317,7 +358,7 @@ __global__ void __launch_bounds__(kHeadThreads) k_head_write(const uint64_t *__r
     int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     int64_t s = (int64_t)blockIdx.x * kHeadThreads + threadIdx.x;
     int l = s < n ? split_level(keys, s) : -1;
-    uint64_t key = s < n ? keys[s] : 0;
+    uint64_t key = s < n ? mkeys[s] : 0;          // the cell's Morton key, for the hash tables
     for (int lev = base; lev <= top; ++lev) {
         unsigned b = __ballot_sync(0xffffffffu, l >= lev);
         if (lane == 0) wsum[warp] = __popc(b);
@@ -375,6 +416,7 @@ int blocks_for(int64_t n, int threads, int cap = 152 * 16) {
 }  // namespace
 
 void free_grid_buffers(mls_grid *g) {
+    cudaFree(g->mkeys);
     cudaFree(g->keys);
     cudaFree(g->keys_alt);
     cudaFree(g->perm);
@@ -401,15 +443,17 @@ int build_grid(mls_grid *g, const float *xyz, int64_t n, float cell_size, int k_
     if (g->cap < n) {
         cudaFree(g->keys);
         cudaFree(g->keys_alt);
+        cudaFree(g->mkeys);
         cudaFree(g->perm);
         cudaFree(g->perm_alt);
         cudaFree(g->pts);
-        g->keys = g->keys_alt = nullptr;
+        g->keys = g->keys_alt = g->mkeys = nullptr;
         g->perm = g->perm_alt = nullptr;
         g->pts = nullptr;
         g->cap = 0;
         MLS_CUDA_TRY(cudaMalloc(&g->keys, n * sizeof(uint64_t)));
         MLS_CUDA_TRY(cudaMalloc(&g->keys_alt, n * sizeof(uint64_t)));
+        MLS_CUDA_TRY(cudaMalloc(&g->mkeys, n * sizeof(uint64_t)));
         MLS_CUDA_TRY(cudaMalloc(&g->perm, n * sizeof(int32_t)));
         MLS_CUDA_TRY(cudaMalloc(&g->perm_alt, n * sizeof(int32_t)));
         MLS_CUDA_TRY(cudaMalloc(&g->pts, n * sizeof(float4)));
@@ -442,9 +486,11 @@ int build_grid(mls_grid *g, const float *xyz, int64_t n, float cell_size, int k_
     if (rc) return rc;
     rc = grow(&g->scan_tmp, (size_t)kDigits + 64, &g->scan_tmp_cap);
     if (rc) return rc;
-    int passes = 0;
-    for (int shift = 3 * sort_level; shift < kKeyBits; shift += kDigitBits) {
-        ++passes;
+    // (the passes that cover the bits from 3 sort_level up start as low as
+    // their width allows: the extra low bits order points within the cells
+    // more finely at no cost)
+    const int passes = (kKeyBits - 3 * sort_level + kDigitBits - 1) / kDigitBits;
+    for (int shift = std::max(0, kKeyBits - kDigitBits * passes); shift < kKeyBits; shift += kDigitBits) {
         k_radix_hist<<<nblocks, kSortThreads, 0, st>>>(g->keys, n, shift, nblocks, g->block_hist);
         k_radix_scan<<<kDigits, 1024, 0, st>>>(g->block_hist, nblocks, g->scan_tmp);
         k_radix_scatter<<<nblocks, kSortThreads, 0, st>>>(g->keys, g->perm, n, shift, nblocks, g->block_hist,
@@ -457,7 +503,7 @@ int build_grid(mls_grid *g, const float *xyz, int64_t n, float cell_size, int k_
         g->perm_alt = tp;
     }
     count_launches(4 + 3 * passes);
-    k_gather_pts<<<blocks_for(n, T), T, 0, st>>>(xyz, g->perm, n, g->pts);
+    k_gather_pts<<<blocks_for(n, T), T, 0, st>>>(xyz, g->perm, n, m, g->pts, g->mkeys);
     k_level_hist<<<blocks_for(n, T), T, 0, st>>>(g->keys, n, m);
     MLS_CUDA_TRY(cudaGetLastError());
     MLS_CUDA_TRY(cudaMemcpyAsync(g->misc_host, m, sizeof(Misc), cudaMemcpyDeviceToHost, st));
@@ -491,7 +537,7 @@ int build_grid(mls_grid *g, const float *xyz, int64_t n, float cell_size, int k_
     }
     GridView &v = g->view;
     v.pts = g->pts;
-    v.keys = g->keys;
+    v.keys = g->mkeys;
     v.frame = hm->frame;
     v.n = (int32_t)n;
     v.base_level = base;
@@ -543,7 +589,8 @@ int build_grid(mls_grid *g, const float *xyz, int64_t n, float cell_size, int k_
     MLS_CUDA_TRY(cudaMemcpyAsync(dev_ptrs, host_ptrs, sizeof(host_ptrs), cudaMemcpyHostToDevice, st));
     k_head_count<<<hblocks, kHeadThreads, 0, st>>>(g->keys, n, base, top, hblocks, g->block_hist);
     k_radix_scan<<<nlev, 1024, 0, st>>>(g->block_hist, hblocks, g->scan_tmp);
-    k_head_write<<<hblocks, kHeadThreads, 0, st>>>(g->keys, n, base, top, hblocks, g->block_hist, v, dev_ptrs);
+    k_head_write<<<hblocks, kHeadThreads, 0, st>>>(g->keys, g->mkeys, n, base, top, hblocks, g->block_hist, v,
+                                                   dev_ptrs);
     dim3 hg(blocks_for(cells[base], T), nlev);
     k_hash_insert<<<hg, T, 0, st>>>(v, dev_ptrs, base, (int)n);
     count_launches(6);

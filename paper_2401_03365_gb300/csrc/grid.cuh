@@ -61,7 +61,8 @@ struct mls_grid {
     int k_hint = 0;
     const float *xyz = nullptr;
     // sort buffers and sorted data
-    uint64_t *keys = nullptr, *keys_alt = nullptr;
+    uint64_t *keys = nullptr, *keys_alt = nullptr;   // sort keys (Hilbert order of the level-0 cells)
+    uint64_t *mkeys = nullptr;                       // Morton keys of the cells, in sorted order
     int32_t *perm = nullptr, *perm_alt = nullptr;
     float4 *pts = nullptr;
     int32_t *block_hist = nullptr;

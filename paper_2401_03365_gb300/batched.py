@@ -66,7 +66,7 @@ class TuneCache:
 
 
 def neighbours(xyz: torch.Tensor, k: int):
-    """(rows (n, k) int32, Morton order (n,) int32, h) of one cloud."""
+    """(rows (n, k) int32, grid order (n,) int32, h) of one cloud."""
     grid = capi.mls_build_grid(xyz, 0.0, k)
     try:
         idx, _ = capi.mls_knn(grid, k)

@@ -200,7 +200,7 @@ class _DeviceArray:
 
 
 def mls_grid_order(grid: Grid) -> torch.Tensor:
-    """The grid's Morton order (order[s] = point at sorted position s) as an
+    """The grid's order (Hilbert order of the cells; order[s] = point at sorted position s) as an
     int32 CUDA tensor viewing the grid's own buffer: valid until the grid is
     rebuilt or destroyed."""
     p = lib().mls_grid_order(grid.handle)

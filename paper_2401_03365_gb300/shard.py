@@ -1,7 +1,9 @@
-"""One cloud split over ranks: contiguous Morton ranges plus one halo exchange.
+"""One cloud split over ranks: contiguous ranges of a space-filling-curve order
+plus one halo exchange.
 
 The per-point projection (Algorithm 1) is independent from point to point,
-so a cloud can be cut into contiguous ranges of its Morton order, one per
+so a cloud can be cut into contiguous ranges of a locality-preserving order
+(the grid's Hilbert order on a GPU, a Morton order in the CPU tests), one per
 rank (the paper's contiguous segments, Sec. 2.1).  A rank's queries need the
 points of other ranks that lie within their k-th neighbour distance, so one
 exchange step precedes the exact search:
@@ -39,7 +41,8 @@ def _world(group):
 
 
 def morton_partition(order: np.ndarray, world: int):
-    """Contiguous ranges of the Morton order, one per rank: index arrays."""
+    """Contiguous ranges of a space-filling-curve order (any permutation is
+    exact; locality only keeps the halo small), one per rank: index arrays."""
     n = order.shape[0]
     cuts = [(n * r) // world for r in range(world + 1)]
     return [np.asarray(order[cuts[r]:cuts[r + 1]]) for r in range(world)]
@@ -110,7 +113,7 @@ class ShardResult:
 def sharded_project(own_xyz: np.ndarray, own_ids: np.ndarray, k: int, h: float, ops, degree: int = 2,
                     precision: str = "mixed", group=None, block: int = 256, device="cpu") -> ShardResult:
     """Exact kNN rows and projection of this rank's points (own_xyz, float32,
-    with global ids own_ids, a contiguous Morton range) within a cloud spread
+    with global ids own_ids, a contiguous range of the order) within a cloud spread
     over the ranks of `group`."""
     world, rank = _world(group)
     own_xyz = np.ascontiguousarray(own_xyz, np.float32)

@@ -95,7 +95,7 @@ def test_backward_deterministic(capi):
 def test_backward_independent_of_processing_order(capi):
     """Each gradient is the exact (fixed-point) sum of its terms, rounded
     once: a random processing order gives bit-identical coordinates' gradients
-    to the Morton order; dL/dh (double partial sums per block) agrees to
+    to the grid order; dL/dh (double partial sums per block) agrees to
     rounding."""
     c = workloads.bumpy_sphere(n=60_000, seed=19)
     x = torch.from_numpy(c.xyz).cuda()
@@ -137,7 +137,7 @@ def test_autograd_function(capi):
 
 
 def test_backward_full_size_torus_sampled(capi):
-    """The benchmark workload (2M points with outliers, k = 32, mixed, Morton
+    """The benchmark workload (2M points with outliers, k = 32, mixed, grid
     order): the gradient at a seeded sample of points j equals the sum over
     the queries whose rows hold j (and j itself); the oracle's adjoint over
     exactly those queries gives it in FP64."""

@@ -40,7 +40,7 @@ def test_knn_bit_exact(capi, case):
 
 def test_knn_full_size_torus_sampled(capi):
     """2M-point torus with outliers (the benchmark workload): the GPU rows of a
-    seeded sample of queries, the first and last points of the Morton order
+    seeded sample of queries, the first and last points of the grid order
     and every outlier-region point in the sample, against the oracle's k-d
     tree over the whole cloud."""
     from paper_2401_03365_gb300 import workloads

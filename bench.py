@@ -53,8 +53,8 @@ GRID_BYTES_PER_POINT = 12 + 16 + 8 + 4
 # taken on are unchanged (SHA-256 of each file).
 STAGE_TRAFFIC = {
     "knn": (186.8, {
-        "paper_2401_03365_gb300/csrc/knn.cu": "4af19aa2d1f33f82d49c9d47ce40eb7bb02ea37eb978aff9feb351a89fea8357",
-        "paper_2401_03365_gb300/csrc/grid.cuh": "9e3837acff7dc08603daeb50044c89a462ce1961944495d3ec580b7146e378d8",
+        "paper_2401_03365_gb300/csrc/knn.cu": "85e9eeb72078c384ae3cc684fa0f6fe31baae9c424621a2441f95778f00a4de1",
+        "paper_2401_03365_gb300/csrc/grid.cuh": "1f26e02fc594d9667d1acb7d9b1153e77edb4a67bdf77bef51e92a978080535d",
         "paper_2401_03365_gb300/csrc/common.cuh": "7b38534e66794f357776ff2b9cc5e1458033c61ab520f00b7a3834258d7b0233",
     }),
 }

@@ -85,9 +85,10 @@ enum mls_point_status {
  * mls_build_grid -- spatial index for the neighbour search that precedes each
  * fit (Sec. 2.2; the paper builds a k-d tree and mentions Morton reordering of
  * unordered clouds, Sec. 2 introduction).  Here: a uniform grid whose cells are
- * numbered by 63-bit Morton keys, points sorted by key with an LSD radix sort,
- * and one hash table per coarsening level (cell side doubling per level) from
- * a base level chosen from the cell occupancy.
+ * numbered by 63-bit Morton keys, points sorted along the Hilbert curve of the
+ * cells with an LSD radix sort (see mls_grid_order), and one hash table per
+ * coarsening level (cell side doubling per level) from a base level chosen
+ * from the cell occupancy.
  *
  *   d_xyz      device, n x 3 floats; must stay valid and unchanged until the
  *              grid is rebuilt or destroyed (mls_knn reads it through the grid)

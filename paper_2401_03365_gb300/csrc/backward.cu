@@ -20,7 +20,7 @@
 // order in which the records reached the bucket, so results do not depend on
 // scheduling or on the processing order.
 //
-// Everything is indexed by sorted (Morton) position when a processing order
+// Everything is indexed by sorted (grid order) position when a processing order
 // is given: point slot s of the order sends its records to the sorted
 // positions of its neighbours.  Neighbours are close in that order, so the
 // bucket writes of a block touch a narrow window of memory at a time.

@@ -3,7 +3,7 @@
 // union of the clouds), its CUDA-graph capture, and the autotuner that picks
 // the launch shape.
 //
-// Work is cut into tiles of tile_pts consecutive (Morton-ordered) points of
+// Work is cut into tiles of tile_pts consecutive (grid-ordered) points of
 // one cloud.  A persistent grid (SMs x resident blocks) takes tiles from one
 // atomic counter; tiles are numbered cloud by cloud in decreasing order of k
 // (then of size), so the most expensive tiles start first and the cheap ones

@@ -30,7 +30,7 @@ struct LevelTable {
 // Everything a query kernel needs, passed by value.
 struct GridView {
     const float4 *pts;         // sorted points: x, y, z, original index (int bits)
-    const uint64_t *keys;      // sorted level-0 Morton keys
+    const uint64_t *keys;      // level-0 Morton cell keys of the sorted points
     GridFrame frame;
     int32_t n;
     int32_t base_level;        // first level with a table

@@ -8,8 +8,9 @@
 // result is the unique first k words.
 //
 // Work layout.  One warp per query; each warp walks runs of consecutive
-// queries in Morton order.  For every query the warp first gets a key bound
-// tau with at least k points at or below it:
+// queries in the grid's order (the Hilbert order of the cells).  For every
+// query the warp first gets a key bound tau with at least k points at or
+// below it:
 //   - chained: from each of the two previous queries, with k-th key kappa at
 //     distance d, tau = (sqrt(kappa) + d)^2 (triangle inequality), inflated by
 //     relative margins of 2^-20 per step, which cover float rounding; the
@@ -28,7 +29,7 @@
 // sorted insertion list finishes the query.
 //
 // The cube's 125 cell ranges (four per lane) are cached in the warp's shared
-// memory: queries that follow each other in Morton order mostly share them.
+// memory: queries that follow each other in the grid order mostly share them.
 #include <algorithm>
 
 #include "grid.cuh"
@@ -775,7 +776,7 @@ __global__ void __launch_bounds__(kChainThreads, 4) k_knn_sparse(GridView g, int
 
 // ---- radius neighbourhoods (Sec. 1.4: the points within radius R) --------
 //
-// One warp per query, runs of 32 consecutive queries in Morton order per
+// One warp per query, runs of 32 consecutive queries in the grid order per
 // warp (the cube of cells stays cached between them).  Every point with key
 // <= R2 is kept, the same cube search and culling as the kNN with the fixed
 // bound R2; ROWS = false counts them, ROWS = true ranks them by (key, index)

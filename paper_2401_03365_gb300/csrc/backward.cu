@@ -27,6 +27,7 @@
 #include <algorithm>
 #include <climits>
 
+#include "fixed_point.cuh"
 #include "solve.cuh"
 
 namespace mls {
@@ -405,28 +406,6 @@ __global__ void __launch_bounds__(256) k_count_window(const int32_t *__restrict_
 
 // 2^e as a float, e in [-126, 127].
 __device__ __forceinline__ float pow2f(int e) { return __int_as_float((e + 127) << 23); }
-
-// v 2^s rounded to the nearest integer, ties to even, |v| 2^s < 2^62: the
-// same integer as converting the (exact) product v 2^s to a 64-bit integer,
-// computed from the float's bits with integer instructions (the conversion
-// itself runs on the FP64 pipe).
-__device__ __forceinline__ long long to_fixed(float v, int s) {
-    const uint32_t bits = __float_as_uint(v);
-    const uint32_t ex = (bits >> 23) & 0xffu, frac = bits & 0x7fffffu;
-    const uint32_t mant = ex ? (frac | 0x800000u) : frac;     // v = mant 2^(e2)
-    const int sh = (ex ? (int)ex - 150 : -149) + s;
-    long long q;
-    if (sh >= 0) {
-        q = (long long)mant << sh;
-    } else if (sh > -25) {
-        const int r = -sh;
-        const uint32_t t = mant >> r, rem = mant & ((1u << r) - 1u), half = 1u << (r - 1);
-        q = (long long)(t + ((rem > half || (rem == half && (t & 1u))) ? 1u : 0u));
-    } else {
-        q = 0;                                                // below one half
-    }
-    return (bits >> 31) ? -q : q;
-}
 
 // The integer q 2^-s, rounded once to float.
 __device__ __forceinline__ float from_fixed(long long q, int s) {

@@ -479,61 +479,69 @@ int build_grid(mls_grid *g, const float *xyz, int64_t n, float cell_size, int k_
     // (all 63 bits, 8 passes, on a first build; the search never uses the
     // cells below the base level, so later builds of the handle skip the bits
     // below one level under the last base: points within such a cell keep
-    // their input order)
-    const int sort_level = cell_size > 0.0f ? 0 : g->sort_level;
+    // their input order).  If the cloud turns out to want a finer base than
+    // the partial sort resolves (its coarsest allowed level already holds 4x
+    // the target occupancy), the keys are sorted again in full.
+    int sort_level = cell_size > 0.0f ? 0 : g->sort_level;
     int nblocks = (int)((n + kSortTile - 1) / kSortTile);
     int rc = grow(&g->block_hist, (size_t)nblocks * kDigits, &g->block_hist_cap);
     if (rc) return rc;
     rc = grow(&g->scan_tmp, (size_t)kDigits + 64, &g->scan_tmp_cap);
     if (rc) return rc;
-    // (the passes that cover the bits from 3 sort_level up start as low as
-    // their width allows: the extra low bits order points within the cells
-    // more finely at no cost)
-    const int passes = (kKeyBits - 3 * sort_level + kDigitBits - 1) / kDigitBits;
-    for (int shift = std::max(0, kKeyBits - kDigitBits * passes); shift < kKeyBits; shift += kDigitBits) {
-        k_radix_hist<<<nblocks, kSortThreads, 0, st>>>(g->keys, n, shift, nblocks, g->block_hist);
-        k_radix_scan<<<kDigits, 1024, 0, st>>>(g->block_hist, nblocks, g->scan_tmp);
-        k_radix_scatter<<<nblocks, kSortThreads, 0, st>>>(g->keys, g->perm, n, shift, nblocks, g->block_hist,
-                                                          g->scan_tmp, g->keys_alt, g->perm_alt);
-        uint64_t *tk = g->keys;
-        g->keys = g->keys_alt;
-        g->keys_alt = tk;
-        int32_t *tp = g->perm;
-        g->perm = g->perm_alt;
-        g->perm_alt = tp;
-    }
-    count_launches(4 + 3 * passes);
-    k_gather_pts<<<blocks_for(n, T), T, 0, st>>>(xyz, g->perm, n, m, g->pts, g->mkeys);
-    k_level_hist<<<blocks_for(n, T), T, 0, st>>>(g->keys, n, m);
-    MLS_CUDA_TRY(cudaGetLastError());
-    MLS_CUDA_TRY(cudaMemcpyAsync(g->misc_host, m, sizeof(Misc), cudaMemcpyDeviceToHost, st));
-    MLS_CUDA_TRY(cudaStreamSynchronize(st));
     const Misc *hm = (const Misc *)g->misc_host;
-    if (hm->nonfinite) return set_error(MLS_ERR_NONFINITE, "mls_build_grid: a coordinate is NaN or infinite");
-
-    // unique cells per level: 1 + number of sorted neighbours split at or above it
     int64_t cells[kMaxLevels];
-    unsigned long long above = 0;
-    for (int l = kMaxLevels - 1; l >= 0; --l) {
-        above += hm->level_hist[l];
-        cells[l] = 1 + (int64_t)above;
-    }
     int top = kMaxLevels - 1;
     int base = top;
-    if (cell_size > 0.0f) {
-        double r = std::log2((double)cell_size / (double)hm->frame.s0);
-        base = (int)std::lround(r);
-        if (base < 0) base = 0;
-        if (base > top) base = top;
-    } else {
+    for (;;) {
+        // (the passes that cover the bits from 3 sort_level up start as low as
+        // their width allows: the extra low bits order points within the cells
+        // more finely at no cost)
+        const int passes = (kKeyBits - 3 * sort_level + kDigitBits - 1) / kDigitBits;
+        for (int shift = std::max(0, kKeyBits - kDigitBits * passes); shift < kKeyBits; shift += kDigitBits) {
+            k_radix_hist<<<nblocks, kSortThreads, 0, st>>>(g->keys, n, shift, nblocks, g->block_hist);
+            k_radix_scan<<<kDigits, 1024, 0, st>>>(g->block_hist, nblocks, g->scan_tmp);
+            k_radix_scatter<<<nblocks, kSortThreads, 0, st>>>(g->keys, g->perm, n, shift, nblocks, g->block_hist,
+                                                              g->scan_tmp, g->keys_alt, g->perm_alt);
+            uint64_t *tk = g->keys;
+            g->keys = g->keys_alt;
+            g->keys_alt = tk;
+            int32_t *tp = g->perm;
+            g->perm = g->perm_alt;
+            g->perm_alt = tp;
+        }
+        count_launches(3 * passes + 2);     // the passes, the point gather, the level histogram
+        MLS_CUDA_TRY(cudaMemsetAsync(m->level_hist, 0, sizeof(m->level_hist), st));
+        k_gather_pts<<<blocks_for(n, T), T, 0, st>>>(xyz, g->perm, n, m, g->pts, g->mkeys);
+        k_level_hist<<<blocks_for(n, T), T, 0, st>>>(g->keys, n, m);
+        MLS_CUDA_TRY(cudaGetLastError());
+        MLS_CUDA_TRY(cudaMemcpyAsync(g->misc_host, m, sizeof(Misc), cudaMemcpyDeviceToHost, st));
+        MLS_CUDA_TRY(cudaStreamSynchronize(st));
+        if (hm->nonfinite) return set_error(MLS_ERR_NONFINITE, "mls_build_grid: a coordinate is NaN or infinite");
+
+        // unique cells per level: 1 + number of sorted neighbours split at or above it
+        unsigned long long above = 0;
+        for (int l = kMaxLevels - 1; l >= 0; --l) {
+            above += hm->level_hist[l];
+            cells[l] = 1 + (int64_t)above;
+        }
+        base = top;
+        if (cell_size > 0.0f) {
+            double r = std::log2((double)cell_size / (double)hm->frame.s0);
+            base = (int)std::lround(r);
+            if (base < 0) base = 0;
+            if (base > top) base = top;
+            break;
+        }
         // finest level whose mean occupancy reaches k_hint / 6 (the cell
         // counts are exact from the sorted level up)
-        double target = k_hint / 6.0 > 1.0 ? k_hint / 6.0 : 1.0;
+        const double target = k_hint / 6.0 > 1.0 ? k_hint / 6.0 : 1.0;
         for (int l = sort_level; l <= top; ++l)
             if ((double)n / (double)cells[l] >= target) {
                 base = l;
                 break;
             }
+        if (sort_level == 0 || base > sort_level || (double)n / (double)cells[base] < 4.0 * target) break;
+        sort_level = 0;
     }
     GridView &v = g->view;
     v.pts = g->pts;
@@ -593,7 +601,7 @@ int build_grid(mls_grid *g, const float *xyz, int64_t n, float cell_size, int k_
                                                    dev_ptrs);
     dim3 hg(blocks_for(cells[base], T), nlev);
     k_hash_insert<<<hg, T, 0, st>>>(v, dev_ptrs, base, (int)n);
-    count_launches(6);
+    count_launches(4 + 4);     // init, bbox, frame, keys; head count, scan, head write, hash insert
     MLS_CUDA_TRY(cudaGetLastError());
     return MLS_OK;
 }

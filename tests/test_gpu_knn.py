@@ -85,6 +85,32 @@ def test_knn_deterministic_and_grid_reuse(capi):
     assert np.array_equal(e.cpu().numpy(), idx8)
 
 
+def test_rebuild_from_a_much_sparser_cloud(capi):
+    """A handle built on 2,000 points of a torus, then rebuilt on 100,000
+    points of the same torus: the partial sort (from one level below the
+    sparse cloud's base) cannot resolve the dense cloud's base level, so the
+    build sorts again in full; rows exact either way."""
+    from paper_2401_03365_gb300 import workloads
+    sparse = workloads.torus(n=2_000, seed=31, outlier_frac=0.0).xyz
+    dense = workloads.torus(n=100_000, seed=32, outlier_frac=0.0).xyz
+    k = 16
+    grid = capi.mls_build_grid(torch.from_numpy(sparse).cuda(), 0.0, k)
+    a, _ = capi.mls_knn(grid, k)
+    a = a.clone()
+    xd = torch.from_numpy(dense).cuda()
+    grid = capi.mls_build_grid(xd, 0.0, k, grid=grid)
+    b, _ = capi.mls_knn(grid, k)
+    b = b.clone()
+    grid = capi.mls_build_grid(xd, 0.0, k, grid=grid)
+    c, _ = capi.mls_knn(grid, k)
+    torch.cuda.synchronize()
+    grid.close()
+    assert np.array_equal(a.cpu().numpy(), oracle_knn(sparse, k)[0])
+    idx_d = oracle_knn(dense, k)[0]
+    assert np.array_equal(b.cpu().numpy(), idx_d)
+    assert np.array_equal(c.cpu().numpy(), idx_d)
+
+
 @pytest.mark.parametrize("cell_size", [0.002, 0.05, 1.0])
 def test_knn_independent_of_cell_size(capi, cell_size):
     xyz, k = knn_case("sphere20k_k20")

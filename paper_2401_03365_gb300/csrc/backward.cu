@@ -42,9 +42,15 @@ constexpr int kSumCached = 9;       // values per lane held in registers there
 constexpr float kBwdGapFlag = 1e-3f;
 constexpr float kBwdCondFlag = 1e5f;
 
-__global__ void k_pack4(const float *__restrict__ xyz, int64_t n, float4 *__restrict__ xyz4) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        xyz4[i] = make_float4(xyz[3 * i], xyz[3 * i + 1], xyz[3 * i + 2], 0.f);
+// The points as float4, in processing order when one is given (xyz4[s] is
+// point order[s]): the neighbours of nearby points then lie close together in
+// memory, which the neighbour gathers' caches reward.
+__global__ void k_pack4(const float *__restrict__ xyz, int64_t n, const int32_t *__restrict__ order,
+                        float4 *__restrict__ xyz4) {
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n; s += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = order ? (int64_t)__ldg(order + s) : s;
+        xyz4[s] = make_float4(xyz[3 * i], xyz[3 * i + 1], xyz[3 * i + 2], 0.f);
+    }
 }
 
 template <typename T, int M>
@@ -96,12 +102,16 @@ __global__ void __launch_bounds__(kBwdThreads, 6) k_backward_point(
     for (int r = 0; r < 32; ++r) {
         const int64_t i_r = __shfl_sync(0xffffffffu, i, r);
         if (r < nrows)
-            for (int c = lane; c < k; c += 32) my_rows[c * 32 + r] = __ldg(idx + i_r * k + c);
+            for (int c = lane; c < k; c += 32) {
+                // the rows as sorted positions (xyz4 is in processing order)
+                const int32_t p = __ldg(idx + i_r * k + c);
+                my_rows[c * 32 + r] = pos ? __ldg(pos + p) : p;
+            }
     }
     __syncwarp();
     float hbar = 0.f;
     if (slot < n) {
-        const float4 r4 = __ldg(xyz4 + i);
+        const float4 r4 = __ldg(xyz4 + slot);
         const float rx = r4.x, ry = r4.y, rz = r4.z;
         const float h2 = h * h, ih = 1.f / h;
         const float neg_scale = -1.4426950408889634f / h2;
@@ -147,8 +157,7 @@ __global__ void __launch_bounds__(kBwdThreads, 6) k_backward_point(
         float rbar[3] = {gp[0], gp[1], gp[2]};
         // a free place in the bucket of neighbour j (its sorted position)
         auto bucket_slot = [&](int j) {
-            const int32_t p = my_rows[j * 32 + lane];
-            const int32_t t = pos ? __ldg(pos + p) : p;
+            const int32_t t = my_rows[j * 32 + lane];
             return __ldg(off + t) + atomicAdd(fill + t, 1);
         };
         if (flag & MLS_PT_PLANE_DEGENERATE) {
@@ -556,9 +565,10 @@ int launch_backward(const float *xyz, int64_t n, const int32_t *idx, int k, floa
     int32_t *fill = cnt + n + 1;
     const int grid_n = (int)std::min<int64_t>((n + 255) / 256, 152 * 16);
     MLS_CUDA_TRY(cudaMemsetAsync(cnt, 0, (size_t)(2 * n + 2) * sizeof(int32_t), st));
-    k_pack4<<<grid_n, 256, 0, st>>>(xyz, n, xyz4);
+    k_pack4<<<grid_n, 256, 0, st>>>(xyz, n, order, xyz4);
     int launches = 1;
     if (order) {
+        MLS_CUDA_TRY(cudaMemsetAsync(pos, 0, (size_t)n * sizeof(int32_t), st));   // in range for any order
         k_inverse<<<grid_n, 256, 0, st>>>(order, n, pos);
         ++launches;
     }

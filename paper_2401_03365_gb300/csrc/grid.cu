@@ -14,6 +14,7 @@
 #include <cstring>
 
 #include "grid.cuh"
+#include "hilbert.cuh"
 
 namespace mls {
 
@@ -120,35 +121,6 @@ __global__ void k_frame(Misc *m) {
     m->frame = f;
 }
 
-// Index of the level-0 cell (x, y, z) along the 3-D Hilbert curve of
-// kMortonBits levels, by Skilling's transform ("Programming the Hilbert
-// curve", AIP Conf. Proc. 707, 2004): the coordinates are turned in place into
-// the transposed index (undo the curve's rotations and reflections from the
-// top bit down, then Gray-decode), whose bits, interleaved with the first
-// coordinate most significant in every triple, give the index.
-__device__ __forceinline__ uint64_t hilbert3(uint32_t x, uint32_t y, uint32_t z) {
-    uint32_t X[3] = {x, y, z};
-    for (uint32_t Q = 1u << (kMortonBits - 1); Q > 1; Q >>= 1) {
-        const uint32_t P = Q - 1;
-#pragma unroll
-        for (int i = 0; i < 3; ++i) {
-            if (X[i] & Q) {
-                X[0] ^= P;                              // reflect
-            } else {
-                const uint32_t t = (X[0] ^ X[i]) & P;   // swap the low bits of X[0] and X[i]
-                X[0] ^= t;
-                X[i] ^= t;
-            }
-        }
-    }
-    X[1] ^= X[0];
-    X[2] ^= X[1];
-    uint32_t t = 0;
-    for (uint32_t Q = 1u << (kMortonBits - 1); Q > 1; Q >>= 1)
-        if (X[2] & Q) t ^= Q - 1;
-    return morton3(X[2] ^ t, X[1] ^ t, X[0] ^ t);
-}
-
 __global__ void k_keys(const float *__restrict__ xyz, int64_t n, const Misc *__restrict__ m,
                        uint64_t *__restrict__ keys, int32_t *__restrict__ perm) {
     GridFrame f = m->frame;
@@ -157,7 +129,7 @@ __global__ void k_keys(const float *__restrict__ xyz, int64_t n, const Misc *__r
         uint32_t c[3];
 #pragma unroll
         for (int a = 0; a < 3; ++a) c[a] = cell_coord(xyz[3 * i + a], f.origin[a], f.inv_s0);
-        keys[i] = hilbert3(c[0], c[1], c[2]);
+        keys[i] = hilbert3(c[0], c[1], c[2], kMortonBits);
         perm[i] = (int32_t)i;
     }
 }

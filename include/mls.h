@@ -99,6 +99,10 @@ enum mls_point_status {
  *   stream     stream for all work
  *   inout      *inout == NULL: a new grid is created and returned;
  *              otherwise the grid is rebuilt in place, reusing its memory.
+ *              A rebuilt grid sorts only the key bits from about one level
+ *              below its previous base level (fewer radix passes); if the new
+ *              cloud needs a finer base than that resolves, it sorts the whole
+ *              key again.  Results never depend on it.
  *
  * Synchronises `stream` once (level sizes are read back to size the tables),
  * so it cannot be captured in a CUDA graph.  Returns MLS_ERR_NONFINITE if any
@@ -152,7 +156,10 @@ int mls_knn(const mls_grid *g, int k, int32_t *d_idx, float *d_key, mls_stream s
  *   d_out_xyz    device, n x 3 floats: projected points p'
  *   d_out_normal device, n x 3 floats or NULL: plane normals n
  *   d_status     device, n bytes or NULL: enum mls_point_status bits
- * Outputs must not alias inputs.
+ * Outputs must not alias inputs.  Uses stream-ordered scratch (the library's
+ * pool): the points as float4 (16 n bytes) and, in MLS_PREC_MIXED, a list of
+ * the points that need an FP64 step (4 n bytes), finished by a second, compact
+ * pass with the same arithmetic as in line.
  */
 int mls_project(const float *d_xyz, int64_t n, const int32_t *d_idx, int k, float h, int degree,
                 int precision, const int32_t *d_order, float *d_out_xyz, float *d_out_normal,

@@ -58,7 +58,10 @@ enum mls_status_code {
     MLS_ERR_OOM = -5,                /* device allocation failed */
     MLS_ERR_TIMEOUT = -6,            /* a bounded device-side wait gave up */
     MLS_ERR_NONFINITE = -7,          /* a coordinate is NaN or infinite */
-    MLS_ERR_TOO_LARGE = -8           /* n beyond the 2^31 - 1 index range */
+    MLS_ERR_TOO_LARGE = -8           /* n beyond the entry point's limit: the 2^31 - 1 index
+                                        range, MLS_NOALLOC_MAX_POINTS for
+                                        mls_project_noalloc, (2^31 - 1) / MLS_MAX_K for
+                                        mls_project_backward */
 };
 
 /* Precision of mls_project / mls_project_backward. */
@@ -232,8 +235,11 @@ int mls_compact(const uint8_t *d_status, int64_t n, int mask, int32_t *d_kept, i
  *
  * Arguments, outputs and results are those of mls_project.
  * Returns MLS_ERR_TOO_LARGE when n > MLS_NOALLOC_MAX_POINTS.
- * The first call on a device looks the array's device address up (with that
- * device current); make that first call before any stream capture.
+ * Every call made outside a stream capture looks the array's device address
+ * up (with the device current), so a cudaDeviceReset between calls leaves
+ * no stale address behind; a call made during a capture uses the address
+ * found by the last call on that device, so make a first call on each device
+ * before any stream capture.
  * All calls share the one array: calls that overlap on the GPU (other
  * streams, other threads) race and corrupt each other's scratch; serialise
  * them.  Every call overwrites the part it uses, so no state carries over.
@@ -361,7 +367,9 @@ int mls_batch_tune_results(const mls_batch *b, int capacity, int32_t *shapes, fl
  * own (one per device) that keeps freed memory mapped for the next call
  * instead of returning it to the system at every synchronisation.  This call
  * synchronises every device that has such a pool and returns its unused
- * memory to the system. */
+ * memory to the system.  A cudaDeviceReset destroys a device's pool with the
+ * rest of its context: do not reset a device that this library has used while
+ * the process still calls it. */
 int mls_release_scratch(void);
 
 /* Number of CUDA kernels this library has launched in the process so far

@@ -72,9 +72,9 @@ def _load():
     lib.oracle_project.argtypes = [_f32p, _i64, _i32p, _int, _dbl, _int, _i64p, _i64, _f64p, _f64p,
                                    _u8p, _f64p]
     lib.oracle_project_grad.argtypes = [_f32p, _i64, _i32p, _int, _dbl, _int, _f64p, _f64p, _i64p, _i64,
-                                        _f64p, _f64p]
+                                        _f64p, _f64p, _f64p]
     lib.oracle_project_levin.argtypes = [_f32p, _i64, _i32p, _int, _dbl, _int, _int, _dbl, _i64p, _i64, _f64p,
-                                         _f64p, _u8p, _i32p]
+                                         _f64p, _u8p, _i32p, _f64p]
     lib.oracle_radius_kdtree.argtypes = [_f32p, _i64, ctypes.c_float, _i64p, _i32p, _i32p]
     lib.oracle_project_rows.argtypes = [_f32p, _i64, _i64p, _i32p, _dbl, _int, _int, _f64p, _f64p, _u8p, _f64p]
     _lib = lib
@@ -157,10 +157,13 @@ def project(xyz, idx, h, degree=2, queries=None):
     return out, nrm, st, diag
 
 
-def project_levin(xyz, idx, h, degree=2, max_iter=100, tol=1e-12, queries=None):
+def project_levin(xyz, idx, h, degree=2, max_iter=100, tol=1e-12, queries=None, with_diag=False):
     """The projection with weights about q (Sec. 1.4, Eq. 1), by the fixed
     point iteration from q = r.  Returns (xyz', normal, status, iterations);
-    status bit 8 marks points that did not converge within max_iter."""
+    status bit 8 marks points that did not converge within max_iter.  With
+    `with_diag`, a fifth array (m x 5) holds this operator's own diagnostics:
+    the last plane's eigenvalues, the final fit's condition number and the
+    last plane's total weight (columns as in `project`)."""
     xyz = _xyz(xyz)
     idx = np.ascontiguousarray(idx, np.int32)
     n, k = xyz.shape[0], idx.shape[1]
@@ -171,12 +174,13 @@ def project_levin(xyz, idx, h, degree=2, max_iter=100, tol=1e-12, queries=None):
     nrm = np.empty((m, 3), np.float64)
     st = np.empty(m, np.uint8)
     it = np.empty(m, np.int32)
+    diag = np.empty((m, 5), np.float64) if with_diag else None
     rc = _load().oracle_project_levin(_p(xyz, _f32p), n, _p(idx, _i32p), k, float(h), int(degree), int(max_iter),
                                       float(tol), _p(q, _i64p), m, _p(out, _f64p), _p(nrm, _f64p), _p(st, _u8p),
-                                      _p(it, _i32p))
+                                      _p(it, _i32p), _p(diag, _f64p))
     if rc != 0:
         raise ValueError(f"oracle_project_levin failed ({rc})")
-    return out, nrm, st, it
+    return (out, nrm, st, it, diag) if with_diag else (out, nrm, st, it)
 
 
 def radius_neighbors(xyz, R):
@@ -218,9 +222,11 @@ def project_rows(xyz, offsets, rows, h, degree=2, min_neighbors=3):
     return out, nrm, st, diag
 
 
-def project_grad(xyz, idx, h, degree, gout_xyz, gout_normal=None, queries=None):
+def project_grad(xyz, idx, h, degree, gout_xyz, gout_normal=None, queries=None, with_abs=False):
     """(dL/dxyz, dL/dh).  With `queries`, only those points' terms (idx: one
-    row per query) are summed."""
+    row per query) are summed.  With `with_abs`, a third array (n) holds per
+    point the sum of the norms of the terms added into its gradient (the
+    scale of its rounding error when the terms cancel)."""
     xyz = _xyz(xyz)
     idx = np.ascontiguousarray(idx, np.int32)
     n, k = xyz.shape[0], idx.shape[1]
@@ -231,12 +237,13 @@ def project_grad(xyz, idx, h, degree, gout_xyz, gout_normal=None, queries=None):
     gn = None if gout_normal is None else np.ascontiguousarray(gout_normal, np.float64)
     grad = np.empty((n, 3), np.float64)
     gh = np.zeros(1, np.float64)
+    gabs = np.empty(n, np.float64) if with_abs else None
     rc = _load().oracle_project_grad(_p(xyz, _f32p), n, _p(idx, _i32p), k, float(h), int(degree),
                                      _p(gp, _f64p), _p(gn, _f64p), _p(q, _i64p), m, _p(grad, _f64p),
-                                     _p(gh, _f64p))
+                                     _p(gh, _f64p), _p(gabs, _f64p))
     if rc != 0:
         raise ValueError(f"oracle_project_grad failed ({rc})")
-    return grad, float(gh[0])
+    return (grad, float(gh[0]), gabs) if with_abs else (grad, float(gh[0]))
 
 
 def fit_height(P, w, nrm, e1, e2, q, h, degree=2):

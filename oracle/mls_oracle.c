@@ -643,12 +643,14 @@ static double dot3(const double *a, const double *b)
  * output is r) and none through the normal.  With a singular polynomial
  * system the polynomial value is 0 and only the plane part is differentiated. */
 static void adjoint_point(const point_state *st, const int32_t *row, int64_t i,
-                          const double *gp, const double *gn, double *grad, double *grad_h)
+                          const double *gp, const double *gn, double *grad, double *grad_h,
+                          double *grad_abs)
 {
     int k = st->k, nb = n_basis(st->degree);
     double h = st->h;
     if (st->status & ST_PLANE_DEGENERATE) {
         for (int a = 0; a < 3; ++a) grad[3 * i + a] += gp[a];
+        if (grad_abs) grad_abs[i] += sqrt(dot3(gp, gp));
         return;
     }
     double *dbar = (double *)calloc(3 * (size_t)k, sizeof(double));
@@ -773,8 +775,10 @@ static void adjoint_point(const point_state *st, const int32_t *row, int64_t i,
             grad[3 * p + a] += dbar[3 * j + a];
             rbar[a] -= dbar[3 * j + a];
         }
+        if (grad_abs) grad_abs[p] += sqrt(dot3(dbar + 3 * j, dbar + 3 * j));
     }
     for (int a = 0; a < 3; ++a) grad[3 * i + a] += rbar[a];
+    if (grad_abs) grad_abs[i] += sqrt(dot3(rbar, rbar));
     *grad_h += hbar;
     free(dbar);
     free(wbar);
@@ -784,10 +788,15 @@ static void adjoint_point(const point_state *st, const int32_t *row, int64_t i,
  * and *grad_h (overwritten) for the cotangents gout_xyz (n x 3) and
  * gout_normal (n x 3, or NULL for zero).  With queries != NULL only the
  * listed points' terms are summed (their rows are idx rows s, in order):
- * the full product is the sum over all points. */
+ * the full product is the sum over all points.
+ * grad_abs (optional, n, overwritten): per point, the sum of the Euclidean
+ * norms of the terms added into its gradient (one per projected point whose
+ * row holds it, plus its own); a scale for the rounding error of the sum,
+ * which can be far above the norm of the sum when the terms cancel. */
 int oracle_project_grad(const float *xyz, int64_t n, const int32_t *idx, int k, double h,
                         int degree, const double *gout_xyz, const double *gout_normal,
-                        const int64_t *queries, int64_t nq, double *grad_xyz, double *grad_h)
+                        const int64_t *queries, int64_t nq, double *grad_xyz, double *grad_h,
+                        double *grad_abs)
 {
     if (k < 1 || k > n || !(h > 0.0) || degree < 0 || degree > 2) return -1;
     point_state st;
@@ -796,13 +805,14 @@ int oracle_project_grad(const float *xyz, int64_t n, const int32_t *idx, int k, 
         return -2;
     }
     memset(grad_xyz, 0, sizeof(double) * 3 * (size_t)n);
+    if (grad_abs) memset(grad_abs, 0, sizeof(double) * (size_t)n);
     *grad_h = 0.0;
     int64_t m = queries ? nq : n;
     for (int64_t s = 0; s < m; ++s) {
         int64_t i = queries ? queries[s] : s;
         project_point(xyz, idx + s * k, k, h, degree, i, &st);
         adjoint_point(&st, idx + s * k, i, gout_xyz + 3 * i, gout_normal ? gout_normal + 3 * i : NULL,
-                      grad_xyz, grad_h);
+                      grad_xyz, grad_h, grad_abs);
     }
     free_state(&st);
     return 0;
@@ -826,10 +836,13 @@ int oracle_project_grad(const float *xyz, int64_t n, const int32_t *idx, int k, 
  * status bit 8).  The polynomial is then fitted in the frame at the final q
  * with the weights about that q, and the result is q + g(0, 0) n.
  * Status, degenerate and singular rules as in oracle_project.
- * out_iter (optional): iterations used per point. */
+ * out_iter (optional): iterations used per point.
+ * out_diag (optional, 5 per row, as oracle_project's): eigenvalues of the
+ * last plane's covariance, condition number of the final height fit's normal
+ * matrix (0 when not fitted), and the last plane's total weight. */
 int oracle_project_levin(const float *xyz, int64_t n, const int32_t *idx, int k, double h, int degree,
                          int max_iter, double tol, const int64_t *queries, int64_t nq, double *out_xyz,
-                         double *out_normal, uint8_t *out_status, int32_t *out_iter)
+                         double *out_normal, uint8_t *out_status, int32_t *out_iter, double *out_diag)
 {
     if (k < 1 || k > n || !(h > 0.0) || degree < 0 || degree > 2 || max_iter < 1) return -1;
     double *P = (double *)malloc(sizeof(double) * 3 * (size_t)k);
@@ -848,7 +861,7 @@ int oracle_project_levin(const float *xyz, int64_t n, const int32_t *idx, int k,
         for (int j = 0; j < k; ++j)
             for (int a = 0; a < 3; ++a) P[3 * j + a] = (double)xyz[3 * (int64_t)row[j] + a];
         int status = ST_NOT_CONVERGED, iters = 0;
-        double t = 0.0;
+        double t = 0.0, last_lam[3] = {0, 0, 0}, last_W = 0.0, cond = 0.0;
         for (int it = 0; it < max_iter; ++it) {
             iters = it + 1;
             /* weights about q */
@@ -879,6 +892,8 @@ int oracle_project_levin(const float *xyz, int64_t n, const int32_t *idx, int k,
             e2[0] = nrm[1] * e1[2] - nrm[2] * e1[1];
             e2[1] = nrm[2] * e1[0] - nrm[0] * e1[2];
             e2[2] = nrm[0] * e1[1] - nrm[1] * e1[0];
+            for (int a = 0; a < 3; ++a) last_lam[a] = lam[a];
+            last_W = W;
             if (!(lam[2] > 0.0) || (lam[1] - lam[0]) <= 1e-6 * lam[2]) {
                 status = ST_PLANE_DEGENERATE;
                 break;
@@ -902,7 +917,7 @@ int oracle_project_levin(const float *xyz, int64_t n, const int32_t *idx, int k,
                 w[j] = exp(-d2 / (h * h));
             }
             double coef[6] = {0, 0, 0, 0, 0, 0};
-            if (!oracle_fit_height(k, P, w, nrm, e1, e2, q, h, degree, coef, NULL)) {
+            if (!oracle_fit_height(k, P, w, nrm, e1, e2, q, h, degree, coef, out_diag ? &cond : NULL)) {
                 status |= ST_POLY_SINGULAR;
                 coef[0] = 0.0;
             }
@@ -914,6 +929,11 @@ int oracle_project_levin(const float *xyz, int64_t n, const int32_t *idx, int k,
         }
         if (out_status) out_status[s] = (uint8_t)status;
         if (out_iter) out_iter[s] = iters;
+        if (out_diag) {
+            for (int a = 0; a < 3; ++a) out_diag[5 * s + a] = last_lam[a];
+            out_diag[5 * s + 3] = cond;
+            out_diag[5 * s + 4] = last_W;
+        }
     }
     free(P);
     free(w);

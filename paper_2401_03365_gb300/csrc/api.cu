@@ -34,8 +34,10 @@ std::atomic<int64_t> g_launches{0};
 
 // Mean neighbour distance excluding self, accumulated in FP64 in a fixed
 // order (a grid-stride loop of a fixed grid, then fixed trees), so the
-// result does not change from run to run.
-constexpr int kMeanBlocks = 152 * 8;
+// result does not change from run to run.  The grid is a constant, not a
+// multiple of the device's SM count, so that the summation order, and with
+// it the result, is also the same on every device.
+constexpr int kMeanBlocks = 1216;
 constexpr int kMeanThreads = 256;
 
 __global__ void __launch_bounds__(kMeanThreads) k_mean_dist(const float *__restrict__ xyz, int64_t n,
@@ -106,6 +108,8 @@ __global__ void __launch_bounds__(1024) k_mean_finish(const double *__restrict__
 }  // namespace
 
 void count_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+void clear_error() { g_last_error[0] = 0; }
 
 int set_error(int code, const char *fmt, ...) {
     va_list ap;
@@ -237,8 +241,9 @@ int mls_radius_rows(const mls_grid *g, float R, const int64_t *d_offsets, int32_
     if (rc != MLS_OK) return rc;
     if (!d_offsets || !d_rows) return set_error(MLS_ERR_INVALID_ARG, "mls_radius_rows: null pointer");
     cudaStream_t st = (cudaStream_t)stream;
+    mls::ScratchSet scratch(st);
     int *overflow = nullptr;
-    MLS_CUDA_TRY(mls::scratch_alloc((void **)&overflow, sizeof(int), st));
+    MLS_CUDA_TRY(scratch.alloc(&overflow, sizeof(int)));
     MLS_CUDA_TRY(cudaMemsetAsync(overflow, 0, sizeof(int), st));
     rc = mls::launch_radius(g, R * R, nullptr, d_offsets, d_rows, d_keys, overflow, st);
     int worst = 0;
@@ -247,7 +252,6 @@ int mls_radius_rows(const mls_grid *g, float R, const int64_t *d_offsets, int32_
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) rc = set_error(MLS_ERR_CUDA, "mls_radius_rows: %s", cudaGetErrorString(e));
     }
-    cudaFreeAsync(overflow, st);
     if (rc != MLS_OK) return rc;
     if (worst > 0)
         return set_error(MLS_ERR_K_TOO_LARGE, "mls_radius_rows: a neighbourhood holds %d points, more than %d",
@@ -338,13 +342,13 @@ int mls_mean_knn_dist(const float *d_xyz, int64_t n, const int32_t *d_idx, int k
     if (!d_xyz || !d_idx || !d_out) return set_error(MLS_ERR_INVALID_ARG, "mls_mean_knn_dist: null pointer");
     if (n < 1 || k < 1 || k > MLS_MAX_K) return set_error(MLS_ERR_INVALID_ARG, "mls_mean_knn_dist: n or k");
     cudaStream_t st = (cudaStream_t)stream;
+    mls::ScratchSet scratch(st);
     double *part = nullptr;
-    MLS_CUDA_TRY(mls::scratch_alloc((void **)&part, 2 * mls::kMeanBlocks * sizeof(double), st));
+    MLS_CUDA_TRY(scratch.alloc(&part, 2 * mls::kMeanBlocks * sizeof(double)));
     unsigned long long *cnt = reinterpret_cast<unsigned long long *>(part + mls::kMeanBlocks);
     mls::k_mean_dist<<<mls::kMeanBlocks, mls::kMeanThreads, 0, st>>>(d_xyz, n, d_idx, k, part, cnt);
     mls::k_mean_finish<<<1, 1024, 0, st>>>(part, cnt, d_out);
     mls::count_launches(2);
-    MLS_CUDA_TRY(cudaFreeAsync(part, st));
     MLS_CUDA_TRY(cudaGetLastError());
     return MLS_OK;
 }

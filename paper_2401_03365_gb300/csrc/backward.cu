@@ -555,15 +555,17 @@ int launch_backward(const float *xyz, int64_t n, const int32_t *idx, int k, floa
     float4 *xyz4 = nullptr, *rec = nullptr, *self4 = nullptr;
     double *hp = nullptr;
     int32_t *cnt = nullptr, *off = nullptr, *pos = nullptr;
-    MLS_CUDA_TRY(scratch_alloc((void **)&xyz4, (size_t)n * sizeof(float4), st));
-    MLS_CUDA_TRY(scratch_alloc((void **)&rec, (size_t)ne * sizeof(float4), st));
-    MLS_CUDA_TRY(scratch_alloc((void **)&self4, (size_t)n * sizeof(float4), st));
-    MLS_CUDA_TRY(scratch_alloc((void **)&hp, (size_t)blocks * sizeof(double), st));
-    MLS_CUDA_TRY(scratch_alloc((void **)&cnt, (size_t)(2 * n + 2) * sizeof(int32_t), st));
-    MLS_CUDA_TRY(scratch_alloc((void **)&off, (size_t)(n + 1) * sizeof(int32_t), st));
-    if (order) MLS_CUDA_TRY(scratch_alloc((void **)&pos, (size_t)n * sizeof(int32_t), st));
+    ScratchSet scratch(st);     // every buffer freed on every return below
+    MLS_CUDA_TRY(scratch.alloc(&xyz4, (size_t)n * sizeof(float4)));
+    MLS_CUDA_TRY(scratch.alloc(&rec, (size_t)ne * sizeof(float4)));
+    MLS_CUDA_TRY(scratch.alloc(&self4, (size_t)n * sizeof(float4)));
+    MLS_CUDA_TRY(scratch.alloc(&hp, (size_t)blocks * sizeof(double)));
+    MLS_CUDA_TRY(scratch.alloc(&cnt, (size_t)(2 * n + 2) * sizeof(int32_t)));
+    MLS_CUDA_TRY(scratch.alloc(&off, (size_t)(n + 1) * sizeof(int32_t)));
+    if (order) MLS_CUDA_TRY(scratch.alloc(&pos, (size_t)n * sizeof(int32_t)));
     int32_t *fill = cnt + n + 1;
-    const int grid_n = (int)std::min<int64_t>((n + 255) / 256, 152 * 16);
+    const int sms = sm_count();
+    const int grid_n = (int)std::min<int64_t>((n + 255) / 256, (int64_t)sms * 16);
     MLS_CUDA_TRY(cudaMemsetAsync(cnt, 0, (size_t)(2 * n + 2) * sizeof(int32_t), st));
     k_pack4<<<grid_n, 256, 0, st>>>(xyz, n, order, xyz4);
     int launches = 1;
@@ -575,7 +577,7 @@ int launch_backward(const float *xyz, int64_t n, const int32_t *idx, int k, floa
     if (order)
         k_count_window<<<(int)((n + kCountSlots - 1) / kCountSlots), 256, 0, st>>>(idx, n, k, order, pos, cnt);
     else
-        k_count<<<(int)std::min<int64_t>((ne + 255) / 256, 152 * 32), 256, 0, st>>>(idx, ne, pos, cnt);
+        k_count<<<(int)std::min<int64_t>((ne + 255) / 256, (int64_t)sms * 32), 256, 0, st>>>(idx, ne, pos, cnt);
     int rc = device_exclusive_scan(cnt, off, n + 1, st);
     if (rc != MLS_OK) return rc;
     switch (degree) {
@@ -583,18 +585,11 @@ int launch_backward(const float *xyz, int64_t n, const int32_t *idx, int k, floa
         case 1: launch_point<1>(xyz4, n, idx, k, h, precision, order, pos, gp, gn, off, fill, rec, self4, hp, blocks, st); break;
         default: launch_point<2>(xyz4, n, idx, k, h, precision, order, pos, gp, gn, off, fill, rec, self4, hp, blocks, st); break;
     }
-    k_bucket_sum<kSumLanes, kSumCached><<<(int)std::min<int64_t>((n * kSumLanes + 255) / 256, 152 * 32), 256, 0, st>>>(
+    k_bucket_sum<kSumLanes, kSumCached><<<(int)std::min<int64_t>((n * kSumLanes + 255) / 256, (int64_t)sms * 32), 256, 0, st>>>(
         n, order, off, rec, self4, grad_xyz);
     k_sum_h<<<1, 1024, 0, st>>>(hp, blocks, grad_h);
     count_launches(launches + 4);   // + count, point, bucket sum, sum_h (the scan counts its own)
     MLS_CUDA_TRY(cudaGetLastError());
-    cudaFreeAsync(xyz4, st);
-    cudaFreeAsync(rec, st);
-    cudaFreeAsync(self4, st);
-    cudaFreeAsync(hp, st);
-    cudaFreeAsync(cnt, st);
-    cudaFreeAsync(off, st);
-    if (pos) cudaFreeAsync(pos, st);
     return MLS_OK;
 }
 

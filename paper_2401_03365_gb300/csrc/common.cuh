@@ -16,12 +16,48 @@ constexpr int kMaxLevels = kMortonBits + 1;      // level L: cell side s0 * 2^L,
 // Records the thread's last error message; returns `code`.
 int set_error(int code, const char *fmt, ...);
 
+// Clears the thread's last error message (every entry point starts so).
+void clear_error();
+
 // Adds to the process-wide count of kernel launches.
 void count_launches(int n);
 
 // Stream-ordered scratch from the library's per-device pool (scratch.cu);
 // release with cudaFreeAsync on the same stream.
 cudaError_t scratch_alloc(void **p, size_t bytes, cudaStream_t st);
+
+// Number of SMs of the current device (queried once per device); grids of
+// grid-stride kernels are sized as multiples of it.
+int sm_count();
+
+// Scratch buffers of one call, freed together (cudaFreeAsync on the call's
+// stream) when the set goes out of scope, on every exit path.
+class ScratchSet {
+  public:
+    explicit ScratchSet(cudaStream_t st) : st_(st) {}
+    ScratchSet(const ScratchSet &) = delete;
+    ScratchSet &operator=(const ScratchSet &) = delete;
+    ~ScratchSet() {
+        for (int i = 0; i < n_; ++i) cudaFreeAsync(p_[i], st_);
+    }
+    template <class T>
+    cudaError_t alloc(T **out, size_t bytes) {
+        *out = nullptr;
+        if (n_ == kMax) return cudaErrorInvalidValue;
+        void *q = nullptr;
+        const cudaError_t e = scratch_alloc(&q, bytes, st_);
+        if (e != cudaSuccess) return e;
+        p_[n_++] = q;
+        *out = static_cast<T *>(q);
+        return cudaSuccess;
+    }
+
+  private:
+    static constexpr int kMax = 16;
+    cudaStream_t st_;
+    void *p_[kMax] = {};
+    int n_ = 0;
+};
 
 #define MLS_CUDA_TRY(expr)                                                              \
     do {                                                                                \

@@ -378,7 +378,8 @@ int grow(T **p, size_t count, size_t *cap) {
     return MLS_OK;
 }
 
-int blocks_for(int64_t n, int threads, int cap = 152 * 16) {
+int blocks_for(int64_t n, int threads, int per_sm = 16) {
+    const int64_t cap = (int64_t)sm_count() * per_sm;
     int64_t b = (n + threads - 1) / threads;
     if (b < 1) b = 1;
     if (b > cap) b = cap;

@@ -828,9 +828,7 @@ __global__ void __launch_bounds__(kChainThreads) k_radius(GridView g, float R2, 
 
 int launch_knn(const mls_grid *grid, int k, int32_t *idx, float *key, cudaStream_t st) {
     const int64_t n = grid->n;
-    int dev = 0, sms = 152;
-    MLS_CUDA_TRY(cudaGetDevice(&dev));
-    MLS_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int sms = sm_count();
     auto chain = k <= 32 ? k_knn_chain<1> : k_knn_chain<2>;
     auto sparse = k <= 32 ? k_knn_sparse<1> : k_knn_sparse<2>;
     // all shared memory to the carveout, so that every block the registers
@@ -859,9 +857,7 @@ namespace mls {
 
 int launch_radius(const mls_grid *grid, float R2, int32_t *count, const int64_t *offsets, int32_t *rows,
                   float *keys, int *overflow, cudaStream_t st) {
-    int dev = 0, sms = 152;
-    MLS_CUDA_TRY(cudaGetDevice(&dev));
-    MLS_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int sms = sm_count();
     const int64_t runs = (grid->n + 31) / 32;
     const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)sms * 4, (runs + kChainWarps - 1) / kChainWarps));
     if (rows) {

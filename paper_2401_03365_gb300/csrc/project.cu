@@ -243,24 +243,24 @@ int launch_deg(const float *xyz, int64_t n, const int32_t *idx, int k, float h, 
         count_launches(1);
     } else {
         // a stream-ordered scratch copy of the points as float4
+        ScratchSet scratch(st);
         float4 *xyz4 = nullptr;
-        MLS_CUDA_TRY(scratch_alloc((void **)&xyz4, (size_t)n * sizeof(float4), st));
-        k_pack_xyz4<<<(int)std::min<int64_t>((n + 255) / 256, 152 * 16), 256, 0, st>>>(xyz, n, xyz4);
+        MLS_CUDA_TRY(scratch.alloc(&xyz4, (size_t)n * sizeof(float4)));
+        k_pack_xyz4<<<(int)std::min<int64_t>((n + 255) / 256, (int64_t)sm_count() * 16), 256, 0, st>>>(xyz, n, xyz4);
         const size_t smem = (size_t)k * 32 * sizeof(int32_t) * (kProjThreads / 32);
         if (precision == MLS_PREC_MIXED) {
             // FP64 points deferred to a second, compact pass
             int32_t *deferred = nullptr;
-            MLS_CUDA_TRY(scratch_alloc((void **)&deferred, (size_t)(n + 1) * sizeof(int32_t), st));
+            MLS_CUDA_TRY(scratch.alloc(&deferred, (size_t)(n + 1) * sizeof(int32_t)));
             int32_t *n_deferred = deferred + n;
             MLS_CUDA_TRY(cudaMemsetAsync(n_deferred, 0, sizeof(int32_t), st));
             auto kern = k_project<DEG, MLS_PREC_MIXED, false, true>;
             MLS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
             kern<<<blocks, kProjThreads, smem, st>>>(xyz4, n, idx, k, h, order, out_xyz, out_n, status, 1, 0.f,
                                                      deferred, n_deferred);
-            k_project_deferred<DEG><<<152 * 2, kProjThreads, 0, st>>>(xyz4, n, idx, k, h, order, deferred, n_deferred,
+            k_project_deferred<DEG><<<sm_count() * 2, kProjThreads, 0, st>>>(xyz4, n, idx, k, h, order, deferred, n_deferred,
                                                                      out_xyz, out_n, status);
             count_launches(3);
-            MLS_CUDA_TRY(cudaFreeAsync(deferred, st));
         } else {
             auto kern = k_project<DEG, MLS_PREC_FP32>;
             MLS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -268,7 +268,6 @@ int launch_deg(const float *xyz, int64_t n, const int32_t *idx, int k, float h, 
                                                      nullptr, nullptr);
             count_launches(2);
         }
-        MLS_CUDA_TRY(cudaFreeAsync(xyz4, st));
     }
     MLS_CUDA_TRY(cudaGetLastError());
     return MLS_OK;
@@ -291,9 +290,10 @@ int launch_project(const float *xyz, int64_t n, const int32_t *idx, int k, float
 int launch_project_rows(const float *xyz, int64_t n, const int64_t *off, const int32_t *rows, float h, int degree,
                         int precision, int min_nb, const int32_t *order, float *out_xyz, float *out_n,
                         uint8_t *status, cudaStream_t st) {
+    ScratchSet scratch(st);
     float4 *xyz4 = nullptr;
-    MLS_CUDA_TRY(scratch_alloc((void **)&xyz4, (size_t)n * sizeof(float4), st));
-    k_pack_xyz4<<<(int)std::min<int64_t>((n + 255) / 256, 152 * 16), 256, 0, st>>>(xyz, n, xyz4);
+    MLS_CUDA_TRY(scratch.alloc(&xyz4, (size_t)n * sizeof(float4)));
+    k_pack_xyz4<<<(int)std::min<int64_t>((n + 255) / 256, (int64_t)sm_count() * 16), 256, 0, st>>>(xyz, n, xyz4);
     const int blocks = (int)((n + kProjThreads - 1) / kProjThreads);
     const bool mixed = precision == MLS_PREC_MIXED;
     switch (degree) {
@@ -311,7 +311,6 @@ int launch_project_rows(const float *xyz, int64_t n, const int64_t *off, const i
             break;
     }
     count_launches(2);
-    MLS_CUDA_TRY(cudaFreeAsync(xyz4, st));
     MLS_CUDA_TRY(cudaGetLastError());
     return MLS_OK;
 }
@@ -324,9 +323,10 @@ int launch_levin_deg(const float *xyz, int64_t n, const int32_t *idx, int k, flo
                      float tol, const int32_t *order, float *out_xyz, float *out_n, uint8_t *status,
                      cudaStream_t st) {
     const int blocks = (int)((n + kProjThreads - 1) / kProjThreads);
+    ScratchSet scratch(st);
     float4 *xyz4 = nullptr;
-    MLS_CUDA_TRY(scratch_alloc((void **)&xyz4, (size_t)n * sizeof(float4), st));
-    k_pack_xyz4<<<(int)std::min<int64_t>((n + 255) / 256, 152 * 16), 256, 0, st>>>(xyz, n, xyz4);
+    MLS_CUDA_TRY(scratch.alloc(&xyz4, (size_t)n * sizeof(float4)));
+    k_pack_xyz4<<<(int)std::min<int64_t>((n + 255) / 256, (int64_t)sm_count() * 16), 256, 0, st>>>(xyz, n, xyz4);
     const size_t smem = (size_t)k * 32 * sizeof(int32_t) * (kProjThreads / 32);
     if (precision == MLS_PREC_MIXED) {
         auto kern = k_project<DEG, MLS_PREC_MIXED, true>;
@@ -340,7 +340,6 @@ int launch_levin_deg(const float *xyz, int64_t n, const int32_t *idx, int k, flo
                                                  nullptr, nullptr);
     }
     count_launches(2);
-    MLS_CUDA_TRY(cudaFreeAsync(xyz4, st));
     MLS_CUDA_TRY(cudaGetLastError());
     return MLS_OK;
 }
@@ -364,8 +363,10 @@ int launch_project_levin(const float *xyz, int64_t n, const int32_t *idx, int k,
 //
 // The same kernels as mls_project, with the float4 copy of the points kept in
 // a file-scope device array instead of stream-ordered scratch.  The array is
-// a host-side stand-in in host code: its device address is looked up once per
-// device (with that device current) and passed to the kernels.
+// a host-side stand-in in host code: its device address is looked up with the
+// device current and passed to the kernels -- on every call made outside a
+// stream capture (so a device reset in between cannot leave a stale address),
+// from the per-device cache of the last look-up during a capture.
 
 namespace {
 
@@ -375,12 +376,14 @@ constexpr int kMaxDevices = 64;
 float4 *g_noalloc_addr[kMaxDevices] = {};
 std::mutex g_noalloc_mutex;
 
-int noalloc_scratch(float4 **out) {
+int noalloc_scratch(cudaStream_t st, float4 **out) {
     int dev = 0;
     MLS_CUDA_TRY(cudaGetDevice(&dev));
     if (dev < 0 || dev >= kMaxDevices) return set_error(MLS_ERR_CUDA, "mls_project_noalloc: device %d", dev);
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    MLS_CUDA_TRY(cudaStreamIsCapturing(st, &cap));
     std::lock_guard<std::mutex> lock(g_noalloc_mutex);
-    if (!g_noalloc_addr[dev]) {
+    if (!g_noalloc_addr[dev] || cap == cudaStreamCaptureStatusNone) {
         void *p = nullptr;
         MLS_CUDA_TRY(cudaGetSymbolAddress(&p, g_noalloc_xyz4));
         g_noalloc_addr[dev] = (float4 *)p;
@@ -398,9 +401,9 @@ int launch_noalloc(const float *xyz, int64_t n, const int32_t *idx, int k, float
         count_launches(1);
     } else {
         float4 *xyz4 = nullptr;
-        int rc = noalloc_scratch(&xyz4);
+        int rc = noalloc_scratch(st, &xyz4);
         if (rc != MLS_OK) return rc;
-        k_pack_xyz4<<<(int)std::min<int64_t>((n + 255) / 256, 152 * 16), 256, 0, st>>>(xyz, n, xyz4);
+        k_pack_xyz4<<<(int)std::min<int64_t>((n + 255) / 256, (int64_t)sm_count() * 16), 256, 0, st>>>(xyz, n, xyz4);
         const size_t smem = (size_t)k * 32 * sizeof(int32_t) * (kProjThreads / 32);
         if (precision == MLS_PREC_MIXED) {
             auto kern = k_project<DEG, MLS_PREC_MIXED>;
@@ -427,6 +430,7 @@ extern "C" int mls_project_noalloc(const float *d_xyz, int64_t n, const int32_t 
                                    int precision, const int32_t *d_order, float *d_out_xyz, float *d_out_normal,
                                    uint8_t *d_status, mls_stream stream) {
     using mls::set_error;
+    mls::clear_error();
     if (!d_xyz || !d_idx || !d_out_xyz) return set_error(MLS_ERR_INVALID_ARG, "mls_project_noalloc: null pointer");
     if (n < 1) return set_error(MLS_ERR_INVALID_ARG, "mls_project_noalloc: n = %lld < 1", (long long)n);
     if (n > MLS_NOALLOC_MAX_POINTS)

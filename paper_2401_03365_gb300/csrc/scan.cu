@@ -87,14 +87,14 @@ __global__ void k_keep_scatter(const int32_t *__restrict__ flag, const int32_t *
 template <typename TI, typename T>
 int scan_impl(const TI *in, int64_t n_in, T *out, int64_t n, cudaStream_t st) {
     const int64_t blocks = (n + kScanThreads - 1) / kScanThreads;
+    ScratchSet scratch(st);
     T *sums = nullptr;
-    MLS_CUDA_TRY(scratch_alloc((void **)&sums, (size_t)blocks * sizeof(T), st));
+    MLS_CUDA_TRY(scratch.alloc(&sums, (size_t)blocks * sizeof(T)));
     k_scan_blocks<TI, T><<<(unsigned)blocks, kScanThreads, 0, st>>>(in, n_in, out, n, sums);
     k_scan_sums<T><<<1, kScanThreads, 0, st>>>(sums, blocks);
     k_scan_add<T><<<(unsigned)blocks, kScanThreads, 0, st>>>(out, n, sums);
     count_launches(3);
     MLS_CUDA_TRY(cudaGetLastError());
-    MLS_CUDA_TRY(cudaFreeAsync(sums, st));
     return MLS_OK;
 }
 
@@ -110,17 +110,17 @@ int device_exclusive_scan64(const int32_t *in, int64_t *out, int64_t n, cudaStre
 }
 
 int device_compact(const uint8_t *status, int64_t n, int mask, int32_t *kept, int64_t *num, cudaStream_t st) {
+    ScratchSet scratch(st);
     int32_t *flag = nullptr;
-    MLS_CUDA_TRY(scratch_alloc((void **)&flag, (size_t)(2 * n) * sizeof(int32_t), st));
+    MLS_CUDA_TRY(scratch.alloc(&flag, (size_t)(2 * n) * sizeof(int32_t)));
     int32_t *pos = flag + n;
-    const int grid = (int)std::min<int64_t>((n + 255) / 256, 152 * 16);
+    const int grid = (int)std::min<int64_t>((n + 255) / 256, (int64_t)sm_count() * 16);
     k_keep_flags<<<grid, 256, 0, st>>>(status, n, mask, flag);
     int rc = device_exclusive_scan(flag, pos, n, st);
     if (rc != MLS_OK) return rc;
     k_keep_scatter<<<grid, 256, 0, st>>>(flag, pos, n, kept, num);
     count_launches(2);
     MLS_CUDA_TRY(cudaGetLastError());
-    MLS_CUDA_TRY(cudaFreeAsync(flag, st));
     return MLS_OK;
 }
 

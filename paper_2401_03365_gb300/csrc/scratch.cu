@@ -7,6 +7,7 @@
 // would hand it back to the system at every synchronisation and map it again
 // on the next allocation, which costs milliseconds per call on large clouds.
 // mls_release_scratch() returns the unused part to the system.
+#include <atomic>
 #include <cstdint>
 #include <mutex>
 
@@ -45,6 +46,18 @@ cudaError_t pool_for_current(cudaMemPool_t *out) {
     return cudaSuccess;
 }
 }  // namespace
+
+int sm_count() {
+    static std::atomic<int> counts[kMaxDevices];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return 1;
+    int c = counts[dev].load(std::memory_order_relaxed);
+    if (c == 0) {
+        if (cudaDeviceGetAttribute(&c, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || c < 1) return 1;
+        counts[dev].store(c, std::memory_order_relaxed);
+    }
+    return c;
+}
 
 cudaError_t scratch_alloc(void **p, size_t bytes, cudaStream_t st) {
     cudaMemPool_t pool = nullptr;

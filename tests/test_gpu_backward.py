@@ -1,11 +1,15 @@
 """GPU adjoint (mls_project_backward through the C ABI) against the FP64
-oracle's adjoint, itself pinned to central differences on the CPU."""
+oracle's adjoint, itself pinned to central differences on the CPU.  Every
+point whose gradient takes terms only from well-posed neighbourhoods must be
+within 1e-3 of the oracle's gradient, relative in norm; the rest are counted
+and their worst error reported."""
 import numpy as np
 import pytest
 import torch
 
 import oracle
 from paper_2401_03365_gb300 import workloads
+from tests.gpu_cases import GRAD_TOL, clean_targets, compare_gradient
 
 pytestmark = pytest.mark.gpu
 
@@ -42,12 +46,12 @@ def test_backward_matches_oracle_adjoint(capi, degree, precision):
                                        degree, precision, order=order)
     torch.cuda.synchronize()
     g_o, gh_o = oracle.project_grad(c.xyz, idx_o, h, degree, gp.astype(np.float64), gn.astype(np.float64))
-    g = gx.cpu().numpy().astype(np.float64)
-    err = np.linalg.norm(g - g_o, axis=1)
-    scale = np.linalg.norm(g_o, axis=1)
-    ref = np.median(scale)
-    assert np.all(err <= 2e-3 * scale + 2e-4 * ref), (err / (scale + 1e-30)).max()
-    assert abs(float(gh.item()) - gh_o) <= 2e-3 * abs(gh_o) + 1e-6 * ref * np.sqrt(c.n)
+    diag = oracle.project(c.xyz, idx_o, h, degree)[3]
+    clean = clean_targets(idx_o, diag, c.n)
+    rep = compare_gradient(gx.cpu().numpy(), g_o, clean, min_clean=0.99)
+    print(rep)
+    # dL/dh sums every point's term: held to the same relative bound
+    assert abs(float(gh.item()) - gh_o) <= GRAD_TOL * abs(gh_o)
 
 
 def test_backward_with_outliers_matches_on_well_posed_neighbourhoods(capi):
@@ -61,20 +65,25 @@ def test_backward_with_outliers_matches_on_well_posed_neighbourhoods(capi):
     torch.cuda.synchronize()
     g_o, _ = oracle.project_grad(c.xyz, idx_o, h, 2, gp.astype(np.float64), gn.astype(np.float64))
     _, _, _, diag = oracle.project(c.xyz, idx_o, h, 2)
-    gap = (diag[:, 1] - diag[:, 0]) / np.maximum(diag[:, 2], 1e-300)
-    good = (gap >= 1e-2) & (diag[:, 3] <= 1e6)
-    # a target is clean when every source that lists it is good
-    bad_src = ~good
-    tainted = np.zeros(c.n, bool)
-    tainted[idx_o[bad_src].ravel()] = True
-    tainted |= bad_src
-    clean = ~tainted
-    assert clean.mean() > 0.5
-    g = gx.cpu().numpy().astype(np.float64)
-    err = np.linalg.norm(g - g_o, axis=1)
-    scale = np.linalg.norm(g_o, axis=1)
-    ref = np.median(scale[clean])
-    assert np.all(err[clean] <= 2e-3 * scale[clean] + 2e-4 * ref), (err[clean] / (scale[clean] + 1e-30)).max()
+    # a target is clean when every source that lists it is well-posed
+    clean = clean_targets(idx_o, diag, c.n)
+    rep = compare_gradient(gx.cpu().numpy(), g_o, clean, min_clean=0.9)
+    print(rep)
+
+
+@pytest.mark.parametrize("precision", ["fp32", "mixed"])
+def test_backward_torus_all_points(capi, precision):
+    """200,000 torus points with outliers, every point compared (FP32 and
+    mixed): the clean mask holds ~99 %."""
+    c = workloads.torus(n=200_000, seed=21)
+    x, idx, order, idx_o, h, gp, gn = _setup(capi, c, 32, 2, 9)
+    gx, _ = capi.mls_project_backward(x, idx, h, torch.from_numpy(gp).cuda(), torch.from_numpy(gn).cuda(),
+                                      2, precision, order=order)
+    torch.cuda.synchronize()
+    g_o, _ = oracle.project_grad(c.xyz, idx_o, h, 2, gp.astype(np.float64), gn.astype(np.float64))
+    diag = oracle.project(c.xyz, idx_o, h, 2)[3]
+    rep = compare_gradient(gx.cpu().numpy(), g_o, clean_targets(idx_o, diag, c.n), min_clean=0.95)
+    print(rep)
 
 
 def test_backward_deterministic(capi):
@@ -163,12 +172,11 @@ def test_backward_full_size_torus_sampled(capi):
     # the sampled rows must be the oracle's own rows
     rows_o, _ = oracle.knn_kdtree(c.xyz, c.k, queries=queries)
     assert np.array_equal(rows_o, rows[queries])
-    g_o, _ = oracle.project_grad(c.xyz, rows_o, float(np.float32(h)), 2, gp.astype(np.float64),
-                                 gn.astype(np.float64), queries=queries)
-    err = np.linalg.norm(g[targets] - g_o[targets], axis=1)
-    scale = np.linalg.norm(g_o[targets], axis=1)
-    ref = np.median(scale)
-    # points near ill-posed neighbourhoods (outliers) carry gradients that
-    # FP32 cannot resolve: the bound holds for all but a stated few
-    ok = err <= 2e-3 * scale + 2e-4 * ref
-    assert ok.mean() >= 0.98, (np.sort(err / (scale + 1e-30))[-10:])
+    hf = float(np.float32(h))
+    g_o, _ = oracle.project_grad(c.xyz, rows_o, hf, 2, gp.astype(np.float64), gn.astype(np.float64),
+                                 queries=queries)
+    # clean targets: every query whose row holds them is well-posed
+    diag = oracle.project(c.xyz, rows_o, hf, 2, queries=queries)[3]
+    clean = clean_targets(rows_o, diag, c.n, queries=queries)[targets]
+    rep = compare_gradient(g[targets], g_o[targets], clean, min_clean=0.9)
+    print(rep)

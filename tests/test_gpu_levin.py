@@ -1,13 +1,15 @@
 """mls_project_levin (weights about q, Sec. 1.4, Eq. 1) against the oracle's
-fixed-point form, element by element on the well-posed mask (taken from the
-oracle's weights-about-r diagnostics: eigen-gap and fit condition)."""
+fixed-point form, element by element on the well-posed mask taken from that
+operator's own diagnostics (eigen-gap of its last plane, condition of its
+final fit).  Only the points the oracle leaves unconverged are left out, and
+on every other well-posed point the GPU must have converged too."""
 import numpy as np
 import pytest
 import torch
 
 import oracle
 from paper_2401_03365_gb300 import workloads
-from tests.gpu_cases import compare_projection, diag_len
+from tests.gpu_cases import compare_projection, diag_len, well_posed
 
 pytestmark = pytest.mark.gpu
 
@@ -30,22 +32,20 @@ def _case(c, k):
 def test_sphere(capi, precision, degree):
     c = workloads.sphere()
     rows, h = _case(c, c.k)
-    o_xyz, o_n, o_st, o_it = oracle.project_levin(c.xyz, rows, h, degree)
+    o_xyz, o_n, o_st, o_it, diag = oracle.project_levin(c.xyz, rows, h, degree, with_diag=True)
     assert np.all((o_st & oracle.STATUS_NOT_CONVERGED) == 0)
-    diag = oracle.project(c.xyz, rows, h, degree)[3]
     x = torch.from_numpy(c.xyz).cuda()
     idx = torch.from_numpy(rows.astype(np.int32)).cuda()
     g_xyz, g_n, g_st = capi.mls_project_levin(x, idx, h, degree, precision, max_iter=32, tol=1e-6)
     g_st = g_st.cpu().numpy()
-    assert np.mean((g_st & capi.MLS_PT_NOT_CONVERGED) != 0) < 1e-3
+    assert np.all((g_st & capi.MLS_PT_NOT_CONVERGED)[well_posed(diag)] == 0)
     compare_projection(g_xyz.cpu().numpy(), g_n.cpu().numpy(), g_st, o_xyz, o_n, o_st & 3, diag, diag_len(c.xyz))
 
 
 def test_torus_with_outliers_in_morton_order(capi):
     c = workloads.torus(n=100_000, seed=12)
     rows, h = _case(c, c.k)
-    o_xyz, o_n, o_st, _ = oracle.project_levin(c.xyz, rows, h, 2)
-    diag = oracle.project(c.xyz, rows, h, 2)[3]
+    o_xyz, o_n, o_st, _, diag = oracle.project_levin(c.xyz, rows, h, 2, with_diag=True)
     x = torch.from_numpy(c.xyz).cuda()
     grid = capi.mls_build_grid(x, 0.0, c.k)
     idx, _ = capi.mls_knn(grid, c.k)
@@ -55,12 +55,14 @@ def test_torus_with_outliers_in_morton_order(capi):
     torch.cuda.synchronize()
     grid.close()
     g_conv = (g[2].cpu().numpy() & capi.MLS_PT_NOT_CONVERGED) == 0
-    assert g_conv.mean() > 0.999
-    # points either side stopped before converging carry the flag and are
-    # left out (a slowly contracting iteration is still moving there)
-    ok = ((o_st & oracle.STATUS_NOT_CONVERGED) == 0) & g_conv
-    compare_projection(*(t.cpu().numpy()[ok] for t in g), o_xyz[ok], o_n[ok], o_st[ok] & 3, diag[ok],
-                       diag_len(c.xyz), min_well_posed=0.3)
+    # only the points the oracle leaves unconverged are left out (a slowly
+    # contracting iteration is still moving there); the GPU must have
+    # converged wherever the oracle did on a well-posed point
+    ok = (o_st & oracle.STATUS_NOT_CONVERGED) == 0
+    assert np.all(g_conv[ok & well_posed(diag)])
+    rep = compare_projection(*(t.cpu().numpy()[ok] for t in g), o_xyz[ok], o_n[ok], o_st[ok] & 3, diag[ok],
+                             diag_len(c.xyz), min_well_posed=0.3)
+    print("oracle unconverged:", int((~ok).sum()), rep)
 
 
 def test_paraboloid_axis_fixed_point(capi):

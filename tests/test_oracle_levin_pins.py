@@ -105,3 +105,44 @@ def test_iteration_limit_sets_the_flag():
     assert np.all((st & oracle.STATUS_NOT_CONVERGED) != 0) and np.all(it == 1)
     _, _, st, it = oracle.project_levin(c.xyz, rows, 0.2, 2)
     assert np.all((st & oracle.STATUS_NOT_CONVERGED) == 0) and it.max() < 100
+
+
+def test_diagnostics_of_the_final_plane_on_the_paraboloid_axis():
+    """The operator's own diagnostics: at the fixed point q = (0, 0, D) (D
+    from brentq, as above) they are the eigenvalues of the weighted
+    covariance with the weights about q, and the condition number of the
+    degree-1 normal matrix over (x, y) / h with those weights, both computed
+    here with numpy."""
+    pts, row, m = _paraboloid_with_axis_query()
+    P = pts[:m].astype(np.float64)
+    h = 0.12
+    r2 = P[:, 0] ** 2 + P[:, 1] ** 2
+
+    def weights(c):
+        return np.exp(-(r2 + (P[:, 2] - c) ** 2) / h ** 2)
+
+    D = brentq(lambda c: (weights(c) * P[:, 2]).sum() / weights(c).sum() - c, -1.0, 1.0, xtol=1e-15)
+    w = weights(D)
+    c = (w[:, None] * P).sum(0) / w.sum()
+    E = P - c
+    C = (w[:, None, None] * E[:, :, None] * E[:, None, :]).sum(0) / w.sum()
+    lam = np.linalg.eigvalsh(C)
+    phi = np.stack([np.ones(m), P[:, 0] / h, P[:, 1] / h], 1)
+    A = (w[:, None, None] * phi[:, :, None] * phi[:, None, :]).sum(0)
+    ev = np.linalg.eigvalsh(A)
+    _, _, st, _, diag = oracle.project_levin(pts, row, h, 1, queries=[m], with_diag=True)
+    assert st[0] == 0
+    assert np.allclose(diag[0, :3], lam, rtol=1e-9, atol=1e-14)
+    assert abs(diag[0, 3] / (ev[-1] / ev[0]) - 1.0) < 1e-9
+    assert abs(diag[0, 4] / w.sum() - 1.0) < 1e-9
+
+
+def test_diagnostics_reduce_to_the_weights_about_r_for_a_wide_bandwidth():
+    c = workloads.sphere(n=2000, seed=5, k=16)
+    rows, _ = oracle.knn_kdtree(c.xyz, 16)
+    _, _, sa, _, da = oracle.project_levin(c.xyz, rows, 1e5, 0, with_diag=True)
+    _, _, sb, db = oracle.project(c.xyz, rows, 1e5, 0)
+    ok = (sa == 0) & (sb == 0)
+    assert ok.mean() > 0.99
+    assert np.allclose(da[ok][:, [0, 1, 2, 4]], db[ok][:, [0, 1, 2, 4]], rtol=1e-6, atol=1e-12)
+    assert np.allclose(da[ok][:, 3], 1.0) and np.allclose(db[ok][:, 3], 1.0)

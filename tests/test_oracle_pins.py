@@ -413,3 +413,32 @@ def test_adjoint_over_query_subsets_sums_to_the_whole():
     g_b, h_b = oracle.project_grad(c.xyz, idx[b], 0.1, 2, gp, queries=b)
     assert np.allclose(g_a + g_b, g_all, rtol=1e-12, atol=1e-12 * np.abs(g_all).max())
     assert h_a + h_b == pytest.approx(h_all, rel=1e-12)
+
+
+def test_adjoint_term_norms():
+    """grad_abs: the sum of the norms of the terms added into each gradient.
+    One query alone gives each of its other neighbours exactly one term,
+    so there it is that gradient's norm; over several queries it adds up
+    query by query, bounds the norm of the sum, and is 0 for points in no
+    row."""
+    c = workloads.sphere(n=1500, seed=54, k=12)
+    idx, _ = oracle.knn_kdtree(c.xyz, 12)
+    rng = np.random.default_rng(55)
+    gp = rng.standard_normal((1500, 3))
+    gn = rng.standard_normal((1500, 3))
+    i = 321
+    g1, _, a1 = oracle.project_grad(c.xyz, idx[[i]], 0.1, 2, gp, gn, queries=[i], with_abs=True)
+    others = idx[i][idx[i] != i]
+    assert np.array_equal(a1[others], np.linalg.norm(g1[others], axis=1))
+    assert a1[i] >= np.linalg.norm(g1[i])
+    untouched = np.setdiff1d(np.arange(1500), idx[i])
+    assert np.all(a1[untouched] == 0) and np.all(g1[untouched] == 0)
+    g_all, _, a_all = oracle.project_grad(c.xyz, idx, 0.1, 2, gp, gn, with_abs=True)
+    perm = rng.permutation(1500)
+    a, b = np.sort(perm[:600]), np.sort(perm[600:])
+    _, _, aa = oracle.project_grad(c.xyz, idx[a], 0.1, 2, gp, gn, queries=a, with_abs=True)
+    _, _, ab = oracle.project_grad(c.xyz, idx[b], 0.1, 2, gp, gn, queries=b, with_abs=True)
+    assert np.allclose(aa + ab, a_all, rtol=1e-12)
+    assert np.all(a_all >= np.linalg.norm(g_all, axis=1) * (1 - 1e-12))
+    g_plain, _ = oracle.project_grad(c.xyz, idx, 0.1, 2, gp, gn)
+    assert np.array_equal(g_plain, g_all)

@@ -88,3 +88,28 @@ def test_noalloc_rejects_clouds_beyond_its_scratch(capi):
     rc, *_ = _noalloc(capi, x, idx, 0.1, 2, "mixed", None)
     assert rc == -8
     assert "scratch" in capi.mls_last_error()
+
+
+@pytest.mark.parametrize("precision", ["mixed", "fp32", "fp64"])
+@pytest.mark.parametrize("degree", [0, 1, 2])
+def test_noalloc_fills_its_whole_scratch(capi, degree, precision):
+    """n = MLS_NOALLOC_MAX_POINTS exactly (the array filled to its last
+    entry), every degree and precision: bit-identical to mls_project, and a
+    successful call leaves no error message behind."""
+    n = capi.MLS_NOALLOC_MAX_POINTS
+    c = workloads.torus(n=n, seed=24)
+    x = torch.from_numpy(c.xyz).cuda()
+    grid = capi.mls_build_grid(x, 0.0, c.k)
+    idx, _ = capi.mls_knn(grid, c.k)
+    order = capi.mls_grid_order(grid)
+    h = 2.0 * float(capi.mls_mean_knn_dist(x, idx).item())
+    # a failed call first: its message must not outlive the next success
+    bad, *_ = _noalloc(capi, x, idx, -1.0, degree, precision, order)
+    assert bad != 0 and capi.mls_last_error()
+    rc, out, nrm, st = _noalloc(capi, x, idx, h, degree, precision, order)
+    assert rc == 0 and capi.mls_last_error() == ""
+    ref_xyz, ref_n, ref_st = capi.mls_project(x, idx, h, degree, precision, order=order)
+    torch.cuda.synchronize()
+    grid.close()
+    # (mixed: the deferred FP64 pass of mls_project = the inline steps here)
+    assert torch.equal(out, ref_xyz) and torch.equal(nrm, ref_n) and torch.equal(st, ref_st)

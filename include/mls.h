@@ -144,6 +144,12 @@ const int32_t *mls_grid_order(const mls_grid *g);
  */
 int mls_knn(const mls_grid *g, int k, int32_t *d_idx, float *d_key, mls_stream stream);
 
+/* Number of queries the last mls_knn call on this grid handed to its second
+ * pass (queries whose first key bound needs a cube above the base level:
+ * outliers, sparse regions); a measure of the work, never of the result.
+ * Synchronises `stream` (the kNN's stream).  Negative: an error code. */
+int64_t mls_knn_deferred(const mls_grid *g, mls_stream stream);
+
 /*
  * mls_project -- the MLS projection of every point (Sec. 1.4, Eq. 1;
  * Algorithm 1: plane, local polynomial, projection onto the polynomial).

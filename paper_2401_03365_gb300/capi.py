@@ -17,7 +17,7 @@ from .build import library_path
 
 __all__ = [
     "MLSError", "Grid", "lib", "mls_build_grid", "mls_grid_destroy", "mls_grid_size", "mls_grid_order",
-    "mls_knn", "mls_project", "mls_project_levin", "mls_project_backward", "mls_radius_neighbors",
+    "mls_knn", "mls_knn_deferred", "mls_project", "mls_project_levin", "mls_project_backward", "mls_radius_neighbors",
     "mls_project_rows", "mls_compact", "mls_mean_knn_dist", "mls_status_str", "mls_last_error", "mls_kernel_launches", "mls_release_scratch",
     "Batch", "mls_batch_create", "mls_batch_destroy", "mls_batch_set_shape", "mls_batch_get_shape",
     "mls_project_batched", "mls_batch_capture", "mls_batch_replay", "mls_batch_autotune", "mls_batch_tune_results",
@@ -45,6 +45,7 @@ _SIGNATURES = [
     ("mls_grid_size", _i64, [_vp]),
     ("mls_grid_order", _vp, [_vp]),
     ("mls_knn", _int, [_vp, _int, _vp, _vp, _vp]),
+    ("mls_knn_deferred", ctypes.c_int64, [_vp, _vp]),
     ("mls_project", _int, [_vp, _i64, _vp, _int, _flt, _int, _int, _vp, _vp, _vp, _vp, _vp]),
     ("mls_project_noalloc", _int, [_vp, _i64, _vp, _int, _flt, _int, _int, _vp, _vp, _vp, _vp, _vp]),
     ("mls_project_levin", _int, [_vp, _i64, _vp, _int, _flt, _int, _int, _int, _flt, _vp, _vp, _vp, _vp, _vp]),
@@ -210,6 +211,8 @@ def mls_grid_order(grid: Grid) -> torch.Tensor:
 
 
 def mls_knn(grid: Grid, k: int, with_key: bool = False, out_idx=None, out_key=None, stream=None):
+    """Exact kNN rows (n, k) int32 in original indexing (and keys with
+    `with_key`)."""
     n = grid.n
     dev = grid.xyz.device
     if out_idx is None:
@@ -221,6 +224,15 @@ def mls_knn(grid: Grid, k: int, with_key: bool = False, out_idx=None, out_key=No
         _need(out_key, "out_key", torch.float32, (n, k))
     _check("mls_knn", lib().mls_knn(grid.handle, int(k), _ptr(out_idx), _ptr(out_key), _stream(stream)))
     return out_idx, out_key
+
+
+def mls_knn_deferred(grid: Grid, stream=None) -> int:
+    """Queries the last kNN call on `grid` handed to its second (sparse)
+    pass (synchronises the stream)."""
+    v = int(lib().mls_knn_deferred(grid.handle, _stream(stream)))
+    if v < 0:
+        _check("mls_knn_deferred", v)
+    return v
 
 
 def mls_project(xyz: torch.Tensor, idx: torch.Tensor, h: float, degree: int = 2, precision: str = "mixed",

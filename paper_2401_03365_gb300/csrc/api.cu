@@ -196,6 +196,16 @@ int mls_knn(const mls_grid *g, int k, int32_t *d_idx, float *d_key, mls_stream s
     return mls::launch_knn(g, k, d_idx, d_key, (cudaStream_t)stream);
 }
 
+int64_t mls_knn_deferred(const mls_grid *g, mls_stream stream) {
+    mls::g_last_error[0] = 0;
+    if (!g || !g->work) return set_error(MLS_ERR_INVALID_ARG, "mls_knn_deferred: no kNN on this grid");
+    int count = 0;
+    cudaStream_t st = (cudaStream_t)stream;
+    MLS_CUDA_TRY(cudaMemcpyAsync(&count, g->work + 1, sizeof(int), cudaMemcpyDeviceToHost, st));
+    MLS_CUDA_TRY(cudaStreamSynchronize(st));
+    return count;
+}
+
 int mls_project(const float *d_xyz, int64_t n, const int32_t *d_idx, int k, float h, int degree, int precision,
                 const int32_t *d_order, float *d_out_xyz, float *d_out_normal, uint8_t *d_status,
                 mls_stream stream) {

@@ -39,41 +39,73 @@ WORKLOAD = ("torus2m_k32: 2,000,000 points on a torus (R=1, r=0.3) with normal n
 N_POINTS = 2_000_000
 K = 32
 
-# Algorithmic work per point: flops of the degree-2
-# projection as the oracle's operation list counts them, and the minimal HBM
-# bytes of the kNN (read the point, write its k indices).
+# Algorithmic work per point of the degree-2 projection, counted from the
+# oracle's operation list (FMA = 2 flops): forward pass A 17, pass B 18,
+# pass C 62 flops per neighbour; per point the 3x3 Jacobi (3 sweeps), the 6x6
+# Cholesky with two solves and one refinement, q and p' (645).  The adjoint
+# (oracle adjoint_point) recomputes the forward and adds per neighbour 190
+# (height-fit reverse 106, covariance 43, centroid 17, weights 18, gather 6)
+# and per point 307 (the solve for z 150, the eigenvector derivative 116,
+# ofs and the rest 41).
 FLOPS_PER_NEIGHBOUR = 97
 FLOPS_PER_POINT = 645
-KNN_BYTES_PER_POINT = 16 + 4 * K
+BWD_FLOPS_PER_NEIGHBOUR = 97 + 190
+BWD_FLOPS_PER_POINT = 645 + 307
+
+
+def proj_flops(k):
+    return FLOPS_PER_NEIGHBOUR * k + FLOPS_PER_POINT
+
+
+def bwd_flops(k):
+    return BWD_FLOPS_PER_NEIGHBOUR * k + BWD_FLOPS_PER_POINT
+
+
+# The kNN's algorithmic HBM bytes per query: read its float4, write its row
+# of sorted positions and its row of original indices (k int32 each).
+def knn_bytes(k):
+    return 16 + 8 * k
+
+
 GRID_BYTES_PER_POINT = 12 + 16 + 8 + 4
 
-# Measured DRAM bytes per point of a stage (dram__bytes_read.sum +
-# dram__bytes_write.sum of its kernels, one ncu capture on a 1,000,000-point
-# torus, scaled by the point count), valid only while the kernel sources it was
-# taken on are unchanged (SHA-256 of each file).
-STAGE_TRAFFIC = {
-    "knn": (186.8, {
-        "paper_2401_03365_gb300/csrc/knn.cu": "85e9eeb72078c384ae3cc684fa0f6fe31baae9c424621a2441f95778f00a4de1",
+# Measured per-query figures of the kNN's two kernels (k_knn_chain +
+# k_knn_sparse, one ncu capture on the 1,000,000-point torus, k = 32):
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) and warp
+# instructions (smsp__inst_executed.sum), each divided by the point count;
+# valid only while the kernel sources they were taken on are unchanged
+# (SHA-256 of each file).
+KNN_MEASURED = {
+    "traffic_bytes_per_query": 338.2,
+    "warp_inst_per_query": 1952.9,
+    "sources": {
+        "paper_2401_03365_gb300/csrc/knn.cu": "ba659bf82c68b49f308525f7fcce2b5156d09f66f4cf882bb5e5bec5f36f775e",
         "paper_2401_03365_gb300/csrc/grid.cuh": "1f26e02fc594d9667d1acb7d9b1153e77edb4a67bdf77bef51e92a978080535d",
-        "paper_2401_03365_gb300/csrc/common.cuh": "7b38534e66794f357776ff2b9cc5e1458033c61ab520f00b7a3834258d7b0233",
-    }),
+        "paper_2401_03365_gb300/csrc/common.cuh": "d77c32eee32ea26b93540c965ff858c429d115e1fc2d5e36a01c004accbad1ae",
+    },
 }
 
 
-def stage_traffic(stage, n_points):
-    """DRAM bytes of one launch of the stage, or None when unmeasured or stale."""
+def knn_measured(field, n_points):
+    """The measured figure for n_points queries, or None when unmeasured or
+    stale."""
     import hashlib
-    if stage not in STAGE_TRAFFIC:
+    v = KNN_MEASURED.get(field)
+    if v is None or not KNN_MEASURED["sources"]:
         return None
-    per_point, sources = STAGE_TRAFFIC[stage]
-    for rel, digest in sources.items():
+    for rel, digest in KNN_MEASURED["sources"].items():
         with open(os.path.join(ROOT, rel), "rb") as f:
             if hashlib.sha256(f.read()).hexdigest() != digest:
                 return None
-    return per_point * n_points
+    return v * n_points
 
 
-def load_peaks():
+def device_sms(dev):
+    import torch
+    return int(torch.cuda.get_device_properties(dev).multi_processor_count)
+
+
+def load_peaks(sms):
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     peaks = {"hbm_gbs": 6800.0, "source": "fallback"}
     if os.path.exists(path):
@@ -82,8 +114,12 @@ def load_peaks():
         peaks.update(p)
         peaks["source"] = "measured"
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    # FP32: 152 SMs x 128 lanes x 2 flops (FMA) x max SM clock
-    peaks["fp32_tflops"] = 152 * 128 * 2 * sm_max * 1e6 / 1e12
+    # FP32: SMs (read from the device) x 128 FP32 lanes x 2 flops (FMA) x
+    # the maximum SM clock; instruction issue: SMs x 4 schedulers x 1 warp
+    # instruction per cycle x the clock
+    peaks["sms"] = sms
+    peaks["fp32_tflops"] = sms * 128 * 2 * sm_max * 1e6 / 1e12
+    peaks["issue_ginst_per_mhz"] = sms * 4 * 1e6 / 1e9
     return peaks
 
 
@@ -200,12 +236,14 @@ def run_ours(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     build.build()
     dev = torch.device("cuda", local)
+    sms = device_sms(dev)
     cloud_seed, cot_seed = rank_seeds(rank)
     cloud = workloads.torus(n=n_pts, seed=cloud_seed, k=K)
     x = torch.from_numpy(cloud.xyz).to(dev)
     stream = torch.cuda.current_stream()
 
     idx = torch.empty((n_pts, K), dtype=torch.int32, device=dev)
+    pos = torch.empty((n_pts, K), dtype=torch.int32, device=dev)
     out_xyz = torch.empty_like(x)
     out_n = torch.empty_like(x)
     out_st = torch.empty(n_pts, dtype=torch.uint8, device=dev)
@@ -221,16 +259,19 @@ def run_ours(args):
     capi.mls_knn(grid, K, out_idx=idx)
     h = 2.0 * float(capi.mls_mean_knn_dist(x, idx).item())
 
+    # one step: grid build, kNN (rows of sorted positions for the projection
+    # in the grid's order, rows of original indices for the adjoint), the
+    # projection, the adjoint with a fixed cotangent
     def step(xin, ev=None, before_forward_out=None, after_forward=None, before_backward=None):
         nonlocal grid
         if ev: ev[0].record(stream)
         grid = capi.mls_build_grid(xin, 0.0, K, grid=grid)
         if ev: ev[1].record(stream)
-        capi.mls_knn(grid, K, out_idx=idx)
+        capi.mls_knn_sorted(grid, K, out_pos=pos, out_idx=idx)
         if ev: ev[2].record(stream)
         order = capi.mls_grid_order(grid)
         if before_forward_out: before_forward_out()
-        capi.mls_project(xin, idx, h, 2, "mixed", order=order, out_xyz=out_xyz, out_normal=out_n, out_status=out_st)
+        capi.mls_project_sorted(grid, pos, h, 2, "mixed", out_xyz=out_xyz, out_normal=out_n, out_status=out_st)
         if ev: ev[3].record(stream)
         if after_forward: after_forward()
         if before_backward: before_backward()
@@ -258,11 +299,12 @@ def run_ours(args):
     if world > 1:
         dist.barrier()
     launches = capi.mls_kernel_launches() - launches0
+    deferred = capi.mls_knn_deferred(grid)
     stage = np.array([[e[i].elapsed_time(e[i + 1]) for i in range(4)] for e in events])  # ms
     build_ms, knn_ms, proj_ms, bwd_ms = (float(v) for v in stage.mean(0))
-    step_ms, fwd_ms = max_over_ranks([stage.sum(1).mean(), stage[:, :3].sum(1).mean()], dev)
+    step_ms, fwd_ms, wall_ms = max_over_ranks([stage.sum(1).mean(), stage[:, :3].sum(1).mean(),
+                                               wall * 1e3 / args.steps], dev)
     value = job_throughput(world, n_pts, step_ms)
-
     # end to end through the public API with host buffers: every step copies
     # its points in from pinned memory, runs the four calls, and copies the
     # projected points, normals, status and gradient back.  The copies run on
@@ -378,40 +420,19 @@ def run_ours(args):
     rd_mean_nb = float(off_r[-1].item()) / n_pts
     rd_kept = int(kept_r.shape[0])
     grid.close()
+    del pos
     if rank != 0:
         if world > 1:
             dist.barrier()
             dist.destroy_process_group()
         return None
 
-    peaks = load_peaks()
-    proj_flops = n_pts * (FLOPS_PER_NEIGHBOUR * K + FLOPS_PER_POINT)
-    knn_gbs = n_pts * KNN_BYTES_PER_POINT / (knn_ms * 1e-3) / 1e9
-    proj_tf = proj_flops / (proj_ms * 1e-3) / 1e12
-    bwd_tf = 3 * proj_flops / (bwd_ms * 1e-3) / 1e12
-    kernels = {
-        "grid_build": {"ms": build_ms, "calls": "mls_build_grid"},
-        "knn": {"ms": knn_ms, "calls": "mls_knn (k_knn_chain + k_knn_sparse)", "bound": "hbm",
-                "achieved_gbs": knn_gbs, "frac": knn_gbs / peaks["hbm_gbs"]},
-        "project": {"ms": proj_ms, "calls": "mls_project (k_pack_xyz4 + k_project)", "bound": "alu",
-                    "achieved_tflops": proj_tf, "frac": proj_tf / peaks["fp32_tflops"]},
-        "backward": {"ms": bwd_ms, "calls": "mls_project_backward (adjoint + gather)", "bound": "alu",
-                     "achieved_tflops": bwd_tf, "frac": bwd_tf / peaks["fp32_tflops"]},
-    }
-    dom = max(kernels, key=lambda n_: kernels[n_]["ms"])
-    if dom == "knn" or dom == "grid_build":
-        ms = kernels[dom]["ms"]
-        bytes_pp = KNN_BYTES_PER_POINT if dom == "knn" else GRID_BYTES_PER_POINT
-        ach = n_pts * bytes_pp / (ms * 1e-3) / 1e9
-        roofline = {"kernel": kernels[dom]["calls"], "bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"],
-                    "unit": "GB/s", "frac": ach / peaks["hbm_gbs"], "traffic": stage_traffic(dom, n_pts),
-                    "peak_source": f"{peaks['source']} hbm_gbs (copy)",
-                    "algorithmic_bytes_per_point": bytes_pp}
-    else:
-        ach = proj_tf if dom == "project" else bwd_tf
-        roofline = {"kernel": kernels[dom]["calls"], "bound": "alu", "achieved": ach, "peak": peaks["fp32_tflops"],
-                    "unit": "TFLOP/s", "frac": ach / peaks["fp32_tflops"], "traffic": stage_traffic(dom, n_pts),
-                    "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 flops x max SM clock"}
+    peaks = load_peaks(sms)
+    clk = clocks.summary()
+    mhz = clk.get("sm_mhz") or float(peaks.get("sm_max_mhz", 2070.0))
+    kernels = stage_kernels(n_pts, K, build_ms, knn_ms, proj_ms, bwd_ms, peaks, mhz)
+    roofline = dict(kernels["knn"]["roofline_hbm"])
+    roofline["issue"] = kernels["knn"]["roofline_issue"]
     line = {
         "metric": METRIC,
         "value": value,
@@ -428,13 +449,19 @@ def run_ours(args):
         "config": {"workload": WORKLOAD if n_pts == N_POINTS else
                    WORKLOAD.replace("2,000,000", f"{n_pts:,}").replace("torus2m", "torus") + " (profiling size)",
                    "points_per_gpu": n_pts, "k": K, "degree": 2, "precision": "mixed",
-                   "h": h, "step": "grid build + exact kNN + MLS projection + backward (fwd+bwd)",
+                   "h": h, "step": ("grid build + exact kNN (rows by sorted position and by original index) + "
+                                    "MLS projection in the grid's order + backward (fwd+bwd)"),
                    "l2": "flushed before every step (256 MB write, outside the timed events)",
                    "parallelism": f"independent clouds per GPU x{world}"},
         "fwd": {"value": job_throughput(world, n_pts, fwd_ms), "unit": "points/s", "ms_per_step": fwd_ms,
                 "step": "grid build + exact kNN + MLS projection"},
+        "wall": {"ms_per_step": wall_ms, "value": job_throughput(world, n_pts, wall_ms), "unit": "points/s",
+                 "note": ("host clock around the timed loop / steps: adds to the events the L2 flush, the "
+                          "Python launch of each step's calls and the host side of mls_build_grid's one "
+                          "stream synchronisation (its level sizes are read back)")},
         "roofline": roofline,
         "kernels": kernels,
+        "knn_deferred_frac": deferred / n_pts,
         "levin": {"ms": float(np.median(lv_ms)), "points_per_s": n_pts / (float(np.median(lv_ms)) * 1e-3),
                   "step": "mls_project_levin (weights about q, fixed point from q = r, tol 1e-6 h, <= 32 passes), "
                           "mixed, degree 2, same rows and h",
@@ -446,18 +473,261 @@ def run_ours(args):
         "e2e": {"value": e2e_value, "unit": "points/s", "h2d_bytes_per_step": n_pts * 12,
                 "d2h_bytes_per_step": n_pts * (12 + 12 + 1 + 12)},
         "gpu_launches": int(launches),
-        "clocks": clocks.summary(),
+        "clocks": clk,
         "wall_s_timed_region": wall,
     }
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(cloud.xyz, h, args.cpu_sample)
         line["cpu_baseline_all_cores"] = cpu_baseline_all_cores(cloud.xyz, h, args.cpu_sample)
+    del cloud, x, idx, out_xyz, out_n, out_st, grad, gp, gn
+    torch.cuda.empty_cache()
+    if world == 1 and not args.no_scan:
+        line["scan50m_k64"] = run_scan(args, dev, peaks, flush)
+    if world == 1 and not args.no_differentiable:
+        line["bumpy1m_k32"] = run_differentiable(args, dev, peaks, flush)
     if world == 1 and not args.no_batched:
         line["batched"] = run_batched(args, dev)
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
     return line
+
+
+def stage_kernels(n, k, build_ms, knn_ms, proj_ms, bwd_ms, peaks, mhz):
+    """Per-stage times and roofline fractions of one step over n points."""
+    knn_gbs = n * knn_bytes(k) / (knn_ms * 1e-3) / 1e9
+    proj_tf = n * proj_flops(k) / (proj_ms * 1e-3) / 1e12
+    bwd_tf = n * bwd_flops(k) / (bwd_ms * 1e-3) / 1e12
+    inst = knn_measured("warp_inst_per_query", n) if k == K else None
+    issue_peak = peaks["issue_ginst_per_mhz"] * mhz          # G warp instructions / s
+    issue = {"bound": "issue", "unit": "G warp-inst/s", "peak": issue_peak,
+             "peak_source": f"derived: {peaks['sms']} SM x 4 schedulers x 1 inst/cycle x {mhz:.0f} MHz "
+                            "(median SM clock sampled in the timed region)",
+             "warp_inst_per_query": None if inst is None else inst / n,
+             "achieved": None if inst is None else inst / (knn_ms * 1e-3) / 1e9}
+    issue["frac"] = None if inst is None else issue["achieved"] / issue_peak
+    return {
+        "grid_build": {"ms": build_ms, "calls": "mls_build_grid",
+                       "achieved_gbs": n * GRID_BYTES_PER_POINT / (build_ms * 1e-3) / 1e9},
+        "knn": {"ms": knn_ms, "calls": "mls_knn_sorted (k_knn_chain + k_knn_sparse)",
+                "roofline_hbm": {"kernel": "mls_knn_sorted (k_knn_chain + k_knn_sparse)", "bound": "hbm",
+                                 "achieved": knn_gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                                 "frac": knn_gbs / peaks["hbm_gbs"],
+                                 "traffic": knn_measured("traffic_bytes_per_query", n) if k == K else None,
+                                 "peak_source": f"{peaks['source']} hbm_gbs (copy)",
+                                 "algorithmic_bytes_per_point": knn_bytes(k)},
+                "roofline_issue": issue},
+        "project": {"ms": proj_ms, "calls": "mls_project_sorted (k_project + k_project_deferred)", "bound": "alu",
+                    "flops_per_point": proj_flops(k), "achieved_tflops": proj_tf,
+                    "frac": proj_tf / peaks["fp32_tflops"]},
+        "backward": {"ms": bwd_ms, "calls": "mls_project_backward (pack, counts, scan, adjoint, bucket sums)",
+                     "bound": "alu", "flops_per_point": bwd_flops(k), "achieved_tflops": bwd_tf,
+                     "frac": bwd_tf / peaks["fp32_tflops"]},
+        "fp32_peak_tflops": peaks["fp32_tflops"],
+        "fp32_peak_source": f"derived: {peaks['sms']} SM (from the device) x 128 FP32 lanes x 2 flops x max SM clock",
+    }
+
+
+def _timed_stages(fns, reps, stream, flush=None):
+    """Runs the stage callables in sequence `reps` times with CUDA events
+    between them; returns the mean ms of each stage."""
+    import torch
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(len(fns) + 1)] for _ in range(reps)]
+    for r in range(reps):
+        if flush is not None:
+            flush.zero_()
+        ev[r][0].record(stream)
+        for i, f in enumerate(fns):
+            f()
+            ev[r][i + 1].record(stream)
+    torch.cuda.synchronize()
+    return [float(np.mean([ev[r][i].elapsed_time(ev[r][i + 1]) for r in range(reps)])) for i in range(len(fns))]
+
+
+def run_scan(args, dev, peaks, flush):
+    """The scan-scale workload: 50M points on the height field of 8 random
+    sinusoids over [0,1]^2 with a 10x sampling-density ramp, noise 0.002,
+    k = 64, mixed precision; one forward step = grid build + exact kNN + the
+    projection in the grid's order."""
+    import torch
+
+    from paper_2401_03365_gb300 import capi, workloads
+    t0 = time.perf_counter()
+    c = workloads.heightfield()
+    t_gen = time.perf_counter() - t0
+    n, k = c.n, c.k
+    stream = torch.cuda.current_stream()
+    x = torch.from_numpy(c.xyz).to(dev)
+    grid = capi.mls_build_grid(x, 0.0, k)
+    idx, _ = capi.mls_knn(grid, k)
+    h = 2.0 * float(capi.mls_mean_knn_dist(x, idx).item())
+    del idx
+    pos = torch.empty((n, k), dtype=torch.int32, device=dev)
+    out = [torch.empty_like(x), torch.empty_like(x), torch.empty(n, dtype=torch.uint8, device=dev)]
+    state = {"grid": grid}
+
+    def build():
+        state["grid"] = capi.mls_build_grid(x, 0.0, k, grid=state["grid"])
+
+    def knn():
+        capi.mls_knn_sorted(state["grid"], k, out_pos=pos)
+
+    def project():
+        capi.mls_project_sorted(state["grid"], pos, h, 2, "mixed", out_xyz=out[0], out_normal=out[1],
+                                out_status=out[2])
+
+    steps = max(3, min(args.steps, 5))
+    _timed_stages([build, knn, project], args.warmup, stream)
+    build_ms, knn_ms, proj_ms = _timed_stages([build, knn, project], steps, stream)
+    deferred = capi.mls_knn_deferred(state["grid"])
+    regular = float(((out[2] & 3) == 0).float().mean().item())
+    state["grid"].close()
+    step_ms = build_ms + knn_ms + proj_ms
+    kernels = stage_kernels(n, k, build_ms, knn_ms, proj_ms, float("nan"), peaks,
+                            float(peaks.get("sm_max_mhz", 2070.0)))
+    kernels.pop("backward")
+    line = {"workload": ("heightfield50m_k64: 50,000,000 points on z = sum of 8 random sinusoids over [0,1]^2, "
+                         "density ramp 1+9x, noise 0.002, k=64, h = 2 x mean kNN distance, degree 2, mixed"),
+            "value": n / (step_ms * 1e-3), "unit": "points/s", "ms_per_step": step_ms, "steps": steps,
+            "step": "grid build + exact kNN (rows by sorted position) + MLS projection in the grid's order",
+            "l2": "inputs far larger than L2 (0.6 GB of points, 12.8 GB of rows); no flush",
+            "h": h, "regular_frac": regular, "knn_deferred_frac": deferred / n, "kernels": kernels,
+            "setup_s": {"generate": t_gen}}
+    del x, pos, out
+    torch.cuda.empty_cache()
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline_scan(c.xyz, k, h)
+    return line
+
+
+def cpu_baseline_scan(xyz, k, h, sub=5_000_000, sample=20_000):
+    """The oracle on a bounded sample of the 50M-point cloud: its k-d tree
+    over a seeded 5M-point subset (time scaled to the whole cloud by n log n)
+    and the kNN + FP64 projection of 20,000 sampled queries against it (time
+    per query scaled to every point)."""
+    import oracle
+    n = xyz.shape[0]
+    rng = np.random.default_rng(77)
+    part = np.ascontiguousarray(xyz[np.sort(rng.choice(n, sub, replace=False))])
+    t0 = time.perf_counter()
+    oracle.knn_kdtree(part, k, queries=np.zeros(0, np.int64))
+    t_build = time.perf_counter() - t0
+    q = np.sort(rng.choice(sub, sample, replace=False))
+    t0 = time.perf_counter()
+    rows, _ = oracle.knn_kdtree(part, k, queries=q)
+    t_knn = time.perf_counter() - t0 - t_build
+    t0 = time.perf_counter()
+    oracle.project(part, rows, h, 2, queries=q)
+    t_proj = time.perf_counter() - t0
+    t_full = t_build * (n * np.log2(n)) / (sub * np.log2(sub)) + (t_knn + t_proj) * n / sample
+    return {"value": n / t_full, "unit": "points/s", "cores": 1, "kind": "oracle",
+            "sample": (f"k-d tree over a seeded {sub:,}-point subset ({t_build:.1f} s, scaled by n log n to the "
+                       f"{n:,} points) + kNN ({t_knn:.2f} s) and FP64 projection ({t_proj:.2f} s) of {sample:,} "
+                       f"sampled queries, scaled to every point"),
+            "seconds": t_build + t_knn + t_proj}
+
+
+def run_differentiable(args, dev, peaks, flush):
+    """The differentiable workload: 1M points on a sphere with 64 Gaussian
+    bumps, k = 32, FP32 forward and backward of the loss
+    L = sum_i (|p'_i| - rho(p'_i / |p'_i|))^2 (the squared radial residual of
+    every projected point to the analytic surface) with respect to the
+    coordinates and h, through the autograd Function.  One step = grid build
+    + kNN + projection + loss + backward (the adjoint kernels and the loss's
+    own gradient)."""
+    import torch
+
+    from paper_2401_03365_gb300 import capi, mls, workloads
+    c = workloads.bumpy_sphere()
+    n, k = c.n, c.k
+    stream = torch.cuda.current_stream()
+    x = torch.from_numpy(c.xyz).to(dev)
+    centres = torch.as_tensor(c.meta["centres"], dtype=torch.float32, device=dev)
+    amps = torch.as_tensor(c.meta["amps"], dtype=torch.float32, device=dev)
+    widths = torch.as_tensor(c.meta["widths"], dtype=torch.float32, device=dev)
+    grid = capi.mls_build_grid(x, 0.0, k)
+    idx = torch.empty((n, k), dtype=torch.int32, device=dev)
+    pos = torch.empty((n, k), dtype=torch.int32, device=dev)
+    capi.mls_knn(grid, k, out_idx=idx)
+    h = 2.0 * float(capi.mls_mean_knn_dist(x, idx).item())
+    state = {"grid": grid}
+
+    def loss_of(p):
+        r = p.norm(dim=1)
+        u = p / r[:, None]
+        rho = 1.0 + (amps[None, :] * torch.exp(-(1.0 - u @ centres.T) / widths[None, :] ** 2)).sum(1)
+        return ((r - rho) ** 2).sum()
+
+    def build():
+        state["grid"] = capi.mls_build_grid(x, 0.0, k, grid=state["grid"])
+
+    def knn():
+        capi.mls_knn_sorted(state["grid"], k, out_pos=pos, out_idx=idx)
+
+    def fwd():
+        state["xg"] = x.detach().requires_grad_(True)
+        state["h"] = torch.tensor(h, dtype=torch.float32, device=dev, requires_grad=True)
+        order = capi.mls_grid_order(state["grid"])
+        out, _, _ = mls.project_differentiable(state["xg"], idx, state["h"], 2, "fp32", order=order,
+                                               grid=state["grid"], pos=pos)
+        state["loss"] = loss_of(out)
+
+    def bwd():
+        state["loss"].backward()
+
+    steps = max(args.steps, 5)
+    _timed_stages([build, knn, fwd, bwd], args.warmup, stream, flush)
+    build_ms, knn_ms, fwd_ms, bwd_ms = _timed_stages([build, knn, fwd, bwd], steps, stream, flush)
+    gx = state["xg"].grad
+    finite = bool(torch.isfinite(gx).all().item()) and bool(torch.isfinite(state["h"].grad).all().item())
+    state["grid"].close()
+    step_ms = build_ms + knn_ms + fwd_ms + bwd_ms
+    kernels = stage_kernels(n, k, build_ms, knn_ms, fwd_ms, bwd_ms, peaks, float(peaks.get("sm_max_mhz", 2070.0)))
+    kernels["project"]["calls"] += " + the loss (torch ops)"
+    kernels["backward"]["calls"] += " + the loss's gradient (torch autograd)"
+    line = {"workload": ("bumpy1m_k32: 1,000,000 points on a sphere with 64 Gaussian bumps, noise 0.005, k=32, "
+                         "h = 2 x mean kNN distance, degree 2, FP32; loss sum (|p'| - rho(p'/|p'|))^2"),
+            "value": n / (step_ms * 1e-3), "unit": "points/s", "ms_per_step": step_ms, "steps": steps,
+            "step": "grid build + kNN + projection (autograd Function) + loss + backward to xyz and h",
+            "l2": "flushed before every step (256 MB write, outside the timed events)",
+            "h": h, "gradients_finite": finite, "kernels": kernels}
+    del x, idx, pos, state
+    torch.cuda.empty_cache()
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline_differentiable(c, h)
+    return line
+
+
+def cpu_baseline_differentiable(c, h, sample=20_000):
+    """The oracle on a bounded sample of the bumpy-sphere workload: its k-d
+    tree over the whole cloud, then kNN, FP64 projection and FP64 adjoint of
+    a seeded 20,000-point sample (with the loss's cotangent at the oracle's
+    own outputs), scaled to every point."""
+    import oracle
+    from paper_2401_03365_gb300 import workloads
+    n, k = c.n, c.k
+    rng = np.random.default_rng(78)
+    q = np.sort(rng.choice(n, sample, replace=False))
+    t0 = time.perf_counter()
+    oracle.knn_kdtree(c.xyz, k, queries=np.zeros(0, np.int64))
+    t_build = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    rows, _ = oracle.knn_kdtree(c.xyz, k, queries=q)
+    o_xyz, _, _, _ = oracle.project(c.xyz, rows, h, 2, queries=q)
+    # the cotangent's radial part 2 (|p'| - rho) p' / |p'| (only timed: the
+    # oracle's cost does not depend on the cotangent's values)
+    r = np.linalg.norm(o_xyz, axis=1)
+    rho = workloads.bumpy_radius(o_xyz / r[:, None], c.meta["centres"], c.meta["amps"], c.meta["widths"])
+    gp = np.zeros((n, 3))
+    gp[q] = (2.0 * (r - rho) / r)[:, None] * o_xyz
+    oracle.project_grad(c.xyz, rows, h, 2, gp, queries=q)
+    t_sample = time.perf_counter() - t0 - t_build
+    t_full = t_build + t_sample * n / sample
+    return {"value": n / t_full, "unit": "points/s", "cores": 1, "kind": "oracle",
+            "sample": (f"k-d tree over all {n:,} points ({t_build:.2f} s) + kNN, FP64 projection, loss cotangent "
+                       f"and FP64 adjoint of a seeded {sample:,}-point sample ({t_sample:.2f} s), scaled to every "
+                       "point"),
+            "seconds": t_build + t_sample}
 
 
 def run_batched(args, dev):
@@ -635,10 +905,12 @@ def run_reference(args):
     for _ in range(args.warmup):
         cpu_baseline(cloud.xyz, h, 1_000)
     times = []
+    measured = []
     info = None
     for _ in range(args.steps):
         info = cpu_baseline(cloud.xyz, h, args.ref_sample)
         times.append(N_POINTS / info["value"])
+        measured.append(info["seconds"])
     step_s = float(np.mean(times))
     value = N_POINTS / step_s
     return {
@@ -648,6 +920,9 @@ def run_reference(args):
         "config": {"workload": WORKLOAD, "points_per_gpu": N_POINTS, "k": K, "degree": 2,
                    "step": "oracle: k-d tree + kNN + FP64 projection + FP64 adjoint, sampled and extrapolated"},
         "cpu_baseline": {"value": value, "unit": "points/s", "cores": 1, "kind": "oracle", "sample": info["sample"]},
+        "measured_s_per_sampled_step": float(np.mean(measured)),
+        "ms_per_step_is": ("the full cloud's time extrapolated from each step's sample (tree over all points, "
+                           f"{args.ref_sample:,} queries); the sampled step itself took measured_s_per_sampled_step"),
         "e2e": {"value": value, "unit": "points/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
         "gpu_launches": 0,
     }
@@ -665,6 +940,8 @@ def main():
                     help="sampled queries per step of --impl reference")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the 256-cloud batched measurement")
+    ap.add_argument("--no-scan", action="store_true", help="skip the 50M-point height-field measurement")
+    ap.add_argument("--no-differentiable", action="store_true", help="skip the 1M-point fwd+bwd loss measurement")
     ap.add_argument("--points", type=int, default=N_POINTS,
                     help="cloud size; smaller than the default only for profiling captures")
     args = ap.parse_args()

@@ -144,6 +144,32 @@ const int32_t *mls_grid_order(const mls_grid *g);
  */
 int mls_knn(const mls_grid *g, int k, int32_t *d_idx, float *d_key, mls_stream stream);
 
+/*
+ * mls_knn_sorted -- the same neighbourhoods in the grid's own order, for
+ * mls_project_sorted: row s (s = a sorted position, see mls_grid_order)
+ * lists the sorted positions of the neighbours of the point at sorted
+ * position s, ascending by (key, index) as in mls_knn.
+ *   d_pos   device, n x k int32, written
+ *   d_idx   device, n x k int32 or NULL: also the rows of mls_knn (original
+ *           indexing, row = original index)
+ *   d_key   device, n x k floats or NULL: the keys, in d_idx's layout
+ */
+int mls_knn_sorted(const mls_grid *g, int k, int32_t *d_pos, int32_t *d_idx, float *d_key, mls_stream stream);
+
+/*
+ * mls_project_sorted -- mls_project over the grid's sorted copy of the points
+ * and rows of sorted positions (from mls_knn_sorted on the same grid, which
+ * must not have been rebuilt since): neighbouring threads read neighbouring
+ * rows and neighbouring points.  Results are those of mls_project on the
+ * matching original-index rows, bit for bit, written in the original order
+ * (point i's result at i).  precision MLS_PREC_FP32 or MLS_PREC_MIXED
+ * (MLS_ERR_INVALID_ARG for MLS_PREC_FP64: use mls_project).  The grid's
+ * points must still be the cloud it was built on.  Scratch: in the mixed form
+ * the list of the points that need an FP64 step (4 n bytes).
+ */
+int mls_project_sorted(const mls_grid *g, const int32_t *d_pos, int k, float h, int degree, int precision,
+                       float *d_out_xyz, float *d_out_normal, uint8_t *d_status, mls_stream stream);
+
 /* Number of queries the last mls_knn call on this grid handed to its second
  * pass (queries whose first key bound needs a cube above the base level:
  * outliers, sparse regions); a measure of the work, never of the result.

@@ -17,7 +17,7 @@ from .build import library_path
 
 __all__ = [
     "MLSError", "Grid", "lib", "mls_build_grid", "mls_grid_destroy", "mls_grid_size", "mls_grid_order",
-    "mls_knn", "mls_knn_deferred", "mls_project", "mls_project_levin", "mls_project_backward", "mls_radius_neighbors",
+    "mls_knn", "mls_knn_sorted", "mls_knn_deferred", "mls_project_sorted", "mls_project", "mls_project_levin", "mls_project_backward", "mls_radius_neighbors",
     "mls_project_rows", "mls_compact", "mls_mean_knn_dist", "mls_status_str", "mls_last_error", "mls_kernel_launches", "mls_release_scratch",
     "Batch", "mls_batch_create", "mls_batch_destroy", "mls_batch_set_shape", "mls_batch_get_shape",
     "mls_project_batched", "mls_batch_capture", "mls_batch_replay", "mls_batch_autotune", "mls_batch_tune_results",
@@ -46,6 +46,8 @@ _SIGNATURES = [
     ("mls_grid_order", _vp, [_vp]),
     ("mls_knn", _int, [_vp, _int, _vp, _vp, _vp]),
     ("mls_knn_deferred", ctypes.c_int64, [_vp, _vp]),
+    ("mls_knn_sorted", _int, [_vp, _int, _vp, _vp, _vp, _vp]),
+    ("mls_project_sorted", _int, [_vp, _vp, _int, ctypes.c_float, _int, _int, _vp, _vp, _vp, _vp]),
     ("mls_project", _int, [_vp, _i64, _vp, _int, _flt, _int, _int, _vp, _vp, _vp, _vp, _vp]),
     ("mls_project_noalloc", _int, [_vp, _i64, _vp, _int, _flt, _int, _int, _vp, _vp, _vp, _vp, _vp]),
     ("mls_project_levin", _int, [_vp, _i64, _vp, _int, _flt, _int, _int, _int, _flt, _vp, _vp, _vp, _vp, _vp]),
@@ -224,6 +226,48 @@ def mls_knn(grid: Grid, k: int, with_key: bool = False, out_idx=None, out_key=No
         _need(out_key, "out_key", torch.float32, (n, k))
     _check("mls_knn", lib().mls_knn(grid.handle, int(k), _ptr(out_idx), _ptr(out_key), _stream(stream)))
     return out_idx, out_key
+
+
+def mls_knn_sorted(grid: Grid, k: int, with_idx: bool = False, with_key: bool = False, out_pos=None,
+                   out_idx=None, out_key=None, stream=None):
+    """Rows of sorted positions by sorted position (n, k) int32, and with
+    `with_idx` / `with_key` also mls_knn's rows and keys: (pos, idx, key)."""
+    n = grid.n
+    dev = grid.xyz.device
+    out_pos = torch.empty((n, k), dtype=torch.int32, device=dev) if out_pos is None else out_pos
+    _need(out_pos, "out_pos", torch.int32, (n, k))
+    if with_idx and out_idx is None:
+        out_idx = torch.empty((n, k), dtype=torch.int32, device=dev)
+    if out_idx is not None:
+        _need(out_idx, "out_idx", torch.int32, (n, k))
+    if with_key and out_key is None:
+        out_key = torch.empty((n, k), dtype=torch.float32, device=dev)
+    if out_key is not None:
+        _need(out_key, "out_key", torch.float32, (n, k))
+    _check("mls_knn_sorted", lib().mls_knn_sorted(grid.handle, int(k), _ptr(out_pos), _ptr(out_idx), _ptr(out_key),
+                                                  _stream(stream)))
+    return out_pos, out_idx, out_key
+
+
+def mls_project_sorted(grid: Grid, pos: torch.Tensor, h: float, degree: int = 2, precision: str = "mixed",
+                       out_xyz=None, out_normal=None, out_status=None, stream=None):
+    """mls_project over the grid's sorted points and mls_knn_sorted's rows;
+    outputs in the original order."""
+    n = grid.n
+    _need(pos, "pos", torch.int32)
+    if pos.dim() != 2 or pos.shape[0] != n:
+        raise ValueError("pos must be (n, k)")
+    dev = grid.xyz.device
+    out_xyz = torch.empty((n, 3), dtype=torch.float32, device=dev) if out_xyz is None else out_xyz
+    out_normal = torch.empty((n, 3), dtype=torch.float32, device=dev) if out_normal is None else out_normal
+    out_status = torch.empty(n, dtype=torch.uint8, device=dev) if out_status is None else out_status
+    _need(out_xyz, "out_xyz", torch.float32, (n, 3))
+    _need(out_normal, "out_normal", torch.float32, (n, 3))
+    _need(out_status, "out_status", torch.uint8, (n,))
+    rc = lib().mls_project_sorted(grid.handle, _ptr(pos), pos.shape[1], float(h), int(degree), PRECISION[precision],
+                                  _ptr(out_xyz), _ptr(out_normal), _ptr(out_status), _stream(stream))
+    _check("mls_project_sorted", rc)
+    return out_xyz, out_normal, out_status
 
 
 def mls_knn_deferred(grid: Grid, stream=None) -> int:

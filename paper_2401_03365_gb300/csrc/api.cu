@@ -11,7 +11,9 @@ namespace mls {
 
 int build_grid(mls_grid *g, const float *xyz, int64_t n, float cell_size, int k_hint, cudaStream_t st);
 void free_grid_buffers(mls_grid *g);
-int launch_knn(const mls_grid *grid, int k, int32_t *idx, float *key, cudaStream_t st);
+int launch_knn(const mls_grid *grid, int k, int32_t *idx, float *key, int32_t *pos, cudaStream_t st);
+int launch_project_sorted(const float4 *pts, int64_t n, const int32_t *pos, int k, float h, int degree,
+                          int precision, float *out_xyz, float *out_n, uint8_t *status, cudaStream_t st);
 int launch_project(const float *xyz, int64_t n, const int32_t *idx, int k, float h, int degree, int precision,
                    const int32_t *order, float *out_xyz, float *out_n, uint8_t *status, cudaStream_t st);
 int launch_radius(const mls_grid *grid, float R2, int32_t *count, const int64_t *offsets, int32_t *rows,
@@ -193,7 +195,36 @@ int mls_knn(const mls_grid *g, int k, int32_t *d_idx, float *d_key, mls_stream s
     if (k < 1 || k > MLS_MAX_K || k > g->n)
         return set_error(MLS_ERR_K_TOO_LARGE, "mls_knn: k = %d not in [1, min(%d, n = %lld)]", k, MLS_MAX_K,
                          (long long)g->n);
-    return mls::launch_knn(g, k, d_idx, d_key, (cudaStream_t)stream);
+    return mls::launch_knn(g, k, d_idx, d_key, nullptr, (cudaStream_t)stream);
+}
+
+int mls_knn_sorted(const mls_grid *g, int k, int32_t *d_pos, int32_t *d_idx, float *d_key, mls_stream stream) {
+    mls::g_last_error[0] = 0;
+    if (!g || !d_pos) return set_error(MLS_ERR_INVALID_ARG, "mls_knn_sorted: null pointer");
+    if (g->n < 1) return set_error(MLS_ERR_INVALID_ARG, "mls_knn_sorted: grid is empty (failed build?)");
+    if (k < 1 || k > MLS_MAX_K || k > g->n)
+        return set_error(MLS_ERR_K_TOO_LARGE, "mls_knn_sorted: k = %d not in [1, min(%d, n = %lld)]", k, MLS_MAX_K,
+                         (long long)g->n);
+    return mls::launch_knn(g, k, d_idx, d_key, d_pos, (cudaStream_t)stream);
+}
+
+int mls_project_sorted(const mls_grid *g, const int32_t *d_pos, int k, float h, int degree, int precision,
+                       float *d_out_xyz, float *d_out_normal, uint8_t *d_status, mls_stream stream) {
+    mls::g_last_error[0] = 0;
+    if (!g || !d_pos || !d_out_xyz) return set_error(MLS_ERR_INVALID_ARG, "mls_project_sorted: null pointer");
+    if (g->n < 1) return set_error(MLS_ERR_INVALID_ARG, "mls_project_sorted: grid is empty (failed build?)");
+    if (k < 1 || k > MLS_MAX_K || k > g->n)
+        return set_error(MLS_ERR_K_TOO_LARGE, "mls_project_sorted: k = %d not in [1, min(%d, n)]", k, MLS_MAX_K);
+    if (!(h > 0.0f) || !std::isfinite(h))
+        return set_error(MLS_ERR_INVALID_ARG, "mls_project_sorted: h = %g must be finite and > 0", (double)h);
+    if (degree < 0 || degree > 2)
+        return set_error(MLS_ERR_UNSUPPORTED_DEGREE, "mls_project_sorted: degree = %d not in {0, 1, 2}", degree);
+    if (precision != MLS_PREC_FP32 && precision != MLS_PREC_MIXED)
+        return set_error(MLS_ERR_INVALID_ARG, "mls_project_sorted: precision = %d (FP32 or mixed)", precision);
+    if ((const void *)d_out_xyz == (const void *)g->xyz)
+        return set_error(MLS_ERR_INVALID_ARG, "mls_project_sorted: output aliases the grid's points");
+    return mls::launch_project_sorted(g->view.pts, g->n, d_pos, k, h, degree, precision, d_out_xyz, d_out_normal,
+                                      d_status, (cudaStream_t)stream);
 }
 
 int64_t mls_knn_deferred(const mls_grid *g, mls_stream stream) {

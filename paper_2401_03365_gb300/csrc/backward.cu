@@ -55,14 +55,14 @@ __global__ void k_pack4(const float *__restrict__ xyz, int64_t n, const int32_t 
 
 template <typename T, int M>
 __device__ bool factor_and_solve(const T A[M][M], const T b[M], const T e0bar, T a[M], T z[M], T &cond) {
-    T L[M][M], pmin, pmax;
-    if (!cholesky<T, M>(A, L, T(1e-12), pmin, pmax)) return false;
+    T L[M][M], invd[M], pmin, pmax;
+    if (!cholesky<T, M>(A, L, invd, T(1e-12), pmin, pmax)) return false;
     cond = (pmax / pmin) * (pmax / pmin);
-    chol_solve<T, M>(L, b, a);
+    chol_solve<T, M>(L, invd, b, a);
     T rhs[M];
 #pragma unroll
     for (int r = 0; r < M; ++r) rhs[r] = r == 0 ? e0bar : T(0);
-    chol_solve<T, M>(L, rhs, z);
+    chol_solve<T, M>(L, invd, rhs, z);
     return true;
 }
 

@@ -384,11 +384,20 @@ __device__ float tighten(const WarpBuf &wb, int k, int lane, float fallback, int
     return __uint_as_float(mx);
 }
 
+// Where a query's row goes: its neighbours' original indices (row = the
+// query's original index) and their keys in the same layout, and their
+// sorted positions (row = the query's sorted position); any may be NULL.
+struct RowOut {
+    int32_t *idx;
+    float *key;
+    int32_t *pos;
+};
+
 // Counting sort of the S <= kCap kept words by bucket, then rank inside the
 // bucket; the first k go to the output row and their sorted positions to
 // wb.nb.  Returns the k-th key.
-__device__ float rank_and_write(WarpBuf &wb, int S, Bins bins, int k, int lane, int32_t qi,
-                                int32_t *__restrict__ out_idx, float *__restrict__ out_key) {
+__device__ float rank_and_write(WarpBuf &wb, int S, Bins bins, int k, int lane, int32_t qi, int64_t sp,
+                                RowOut out) {
     bucket_hist(wb, S, bins, lane);
     const int h = wb.hist[lane];
     wb.fill[lane] = warp_incl_scan(h, lane) - h;
@@ -409,8 +418,9 @@ __device__ float rank_and_write(WarpBuf &wb, int S, Bins bins, int k, int lane, 
         int rank = beg;
         for (int t = beg; t < end; ++t) rank += wb.tmp[t] < v;
         if (rank < k) {
-            out_idx[(int64_t)qi * k + rank] = (int32_t)(uint32_t)v;
-            if (out_key) out_key[(int64_t)qi * k + rank] = key;
+            if (out.idx) out.idx[(int64_t)qi * k + rank] = (int32_t)(uint32_t)v;
+            if (out.key) out.key[(int64_t)qi * k + rank] = key;
+            if (out.pos) out.pos[sp * k + rank] = wb.tpos[p];
             if (rank < 64) wb.nb[rank] = wb.tpos[p];     // the radius rows can be longer than a kNN row
             if (rank == k - 1) wb.kth = key;
         }
@@ -487,8 +497,7 @@ struct TopK {
 
 template <int KPL>
 __device__ float insertion_fallback(const GridView &g, const Cube &cb, WarpBuf &wb, float4 q, float lim2, float tau,
-                                    int k, int lane, int32_t qi, int32_t *__restrict__ out_idx,
-                                    float *__restrict__ out_key) {
+                                    int k, int lane, int32_t qi, int64_t sp, RowOut out) {
     TopK<KPL> top;
     top.init();
     for_each_point<1>(cell_geom(g, cb), cb, wb, q, lim2, lane, [&](float4 p, bool valid, int pos) {
@@ -499,8 +508,9 @@ __device__ float insertion_fallback(const GridView &g, const Cube &cb, WarpBuf &
     for (int r = 0; r < KPL; ++r) {
         const int e = r * 32 + lane;
         if (e < k) {
-            out_idx[(int64_t)qi * k + e] = (int32_t)(uint32_t)top.e[r];
-            if (out_key) out_key[(int64_t)qi * k + e] = __uint_as_float((uint32_t)(top.e[r] >> 32));
+            if (out.idx) out.idx[(int64_t)qi * k + e] = (int32_t)(uint32_t)top.e[r];
+            if (out.key) out.key[(int64_t)qi * k + e] = __uint_as_float((uint32_t)(top.e[r] >> 32));
+            if (out.pos) out.pos[sp * k + e] = top.pos[r];
             wb.nb[e] = top.pos[r];
             wb.tpos[e] = top.pos[r];
         }
@@ -572,8 +582,8 @@ __device__ __forceinline__ float neighbour_bound(const GridView &g, const WarpBu
 // as a last resort, the sorted insertion list.  Returns the k-th key.
 template <int KPL, int U>
 __device__ __forceinline__ float solve_query(const GridView &g, WarpBuf &wb, Cube &cb, float4 q, int32_t qi,
-                                             const uint32_t c0[3], float tau, int k, int lane, bool may_defer,
-                                             int32_t *__restrict__ out_idx, float *__restrict__ out_key) {
+                                             int64_t sp, const uint32_t c0[3], float tau, int k, int lane,
+                                             bool may_defer, RowOut out) {
     const float eps2 = 2.0f * g.frame.eps;
     // fewer than k points have a key below lo (known from a histogram of
     // every key <= tau): later histograms split [lo, tau] only
@@ -636,13 +646,13 @@ __device__ __forceinline__ float solve_query(const GridView &g, WarpBuf &wb, Cub
         const Bins rb{0.f, tau > 0.f ? 32.0f / tau : 0.f};
         const Bins tb = lo > 0.f ? Bins{lo, tau > lo ? 31.0f / (tau - lo) : 0.f} : rb;
         const int S = scan_keep<U>(cell_geom(g, cb), cb, wb, q, lim2, tau, tb, lane, full_hist);
-        if (S >= k && S <= kCap) return rank_and_write(wb, S, rb, k, lane, qi, out_idx, out_key);
+        if (S >= k && S <= kCap) return rank_and_write(wb, S, rb, k, lane, qi, sp, out);
         if (S < k) {            // cannot happen for a valid bound: search everything
             tau = INFINITY;
             full_hist = false;
             continue;
         }
-        if (iter >= 8) return insertion_fallback<KPL>(g, cb, wb, q, lim2, tau, k, lane, qi, out_idx, out_key);
+        if (iter >= 8) return insertion_fallback<KPL>(g, cb, wb, q, lim2, tau, k, lane, qi, sp, out);
         if (full_hist) {        // buckets over every kept word: each round cuts ~32x
             tau = tighten(wb, k, lane, tau, &bstar);
             // the buckets before the k-th key's hold fewer than k keys
@@ -694,8 +704,7 @@ constexpr int kChainBlocksPerSm = 5;
 
 template <int KPL>
 __global__ void __launch_bounds__(kChainThreads, kChainBlocksPerSm) k_knn_chain(GridView g, int k, int *__restrict__ work,
-                                                            int32_t *__restrict__ out_idx,
-                                                            float *__restrict__ out_key) {
+                                                                                RowOut out) {
     __shared__ WarpBuf bufs[kChainWarps];
     const int lane = threadIdx.x & 31;
     WarpBuf &wb = bufs[threadIdx.x >> 5];
@@ -734,7 +743,7 @@ __global__ void __launch_bounds__(kChainThreads, kChainBlocksPerSm) k_knn_chain(
             // base cells, would search a large region: start afresh instead
             if (n_prev == 0 || tau > 9.0f * k1 || tau > big) tau = INFINITY;
             const float kth =
-                solve_query<KPL, 1>(g, wb, cb, q, __float_as_int(q.w), c0, tau, k, lane, true, out_idx, out_key);
+                solve_query<KPL, 1>(g, wb, cb, q, __float_as_int(q.w), sp, c0, tau, k, lane, true, out);
             if (isnan(kth)) {
                 if (lane == 0) work[8 + atomicAdd(&work[1], 1)] = (int)sp;
                 n_prev = 0;
@@ -756,8 +765,7 @@ constexpr int kSparseRounds = 4;
 
 template <int KPL>
 __global__ void __launch_bounds__(kChainThreads, 4) k_knn_sparse(GridView g, int k, int *__restrict__ work,
-                                                             int32_t *__restrict__ out_idx,
-                                                             float *__restrict__ out_key) {
+                                                                 RowOut out) {
     __shared__ WarpBuf bufs[kChainWarps];
     const int lane = threadIdx.x & 31;
     WarpBuf &wb = bufs[threadIdx.x >> 5];
@@ -770,7 +778,7 @@ __global__ void __launch_bounds__(kChainThreads, 4) k_knn_sparse(GridView g, int
         const float4 q = __ldg(g.pts + sp);
         const uint64_t key0 = __ldg(g.keys + sp);
         const uint32_t c0[3] = {compact3(key0), compact3(key0 >> 1), compact3(key0 >> 2)};
-        solve_query<KPL, kSparseRounds>(g, wb, cb, q, __float_as_int(q.w), c0, INFINITY, k, lane, false, out_idx, out_key);
+        solve_query<KPL, kSparseRounds>(g, wb, cb, q, __float_as_int(q.w), sp, c0, INFINITY, k, lane, false, out);
     }
 }
 
@@ -818,7 +826,8 @@ __global__ void __launch_bounds__(kChainThreads) k_radius(GridView g, float R2, 
             } else if (S > kCap) {
                 if (lane == 0) atomicMax(overflow, S);
             } else {
-                rank_and_write(wb, S, bins, S, lane, 0, rows + offsets[qi], keys ? keys + offsets[qi] : nullptr);
+                rank_and_write(wb, S, bins, S, lane, 0, 0,
+                               RowOut{rows + offsets[qi], keys ? keys + offsets[qi] : nullptr, nullptr});
             }
         }
     }
@@ -826,7 +835,7 @@ __global__ void __launch_bounds__(kChainThreads) k_radius(GridView g, float R2, 
 
 }  // namespace
 
-int launch_knn(const mls_grid *grid, int k, int32_t *idx, float *key, cudaStream_t st) {
+int launch_knn(const mls_grid *grid, int k, int32_t *idx, float *key, int32_t *pos, cudaStream_t st) {
     const int64_t n = grid->n;
     const int sms = sm_count();
     auto chain = k <= 32 ? k_knn_chain<1> : k_knn_chain<2>;
@@ -844,8 +853,9 @@ int launch_knn(const mls_grid *grid, int k, int32_t *idx, float *key, cudaStream
     const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)sms * per_sm,
                                                                     (runs + kChainWarps - 1) / kChainWarps));
     MLS_CUDA_TRY(cudaMemsetAsync(grid->work, 0, 8 * sizeof(int), st));
-    chain<<<blocks, kChainThreads, 0, st>>>(grid->view, k, grid->work, idx, key);
-    sparse<<<sms * per_sm, kChainThreads, 0, st>>>(grid->view, k, grid->work, idx, key);
+    const RowOut out{idx, key, pos};
+    chain<<<blocks, kChainThreads, 0, st>>>(grid->view, k, grid->work, out);
+    sparse<<<sms * per_sm, kChainThreads, 0, st>>>(grid->view, k, grid->work, out);
     count_launches(2);
     MLS_CUDA_TRY(cudaGetLastError());
     return MLS_OK;

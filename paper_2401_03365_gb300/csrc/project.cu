@@ -34,7 +34,11 @@ __global__ void k_pack_xyz4(const float *__restrict__ xyz, int64_t n, float4 *__
 // FP64 step is not finished here: its slot goes to deferred[] (count in
 // *n_deferred) for k_project_deferred, so that the warps of this kernel never
 // wait on FP64 arithmetic (GB300's FP64 rate is a small fraction of FP32).
-template <int DEG, int PREC, bool LEVIN = false, bool DEFER = false>
+// With SORTED, xyz4 is the grid's sorted copy of the points (w = the point's
+// original index bits), slot s is sorted position s, idx holds the rows of
+// sorted positions by sorted position, and each result goes to the point's
+// original index.
+template <int DEG, int PREC, bool LEVIN = false, bool DEFER = false, bool SORTED = false>
 __global__ void __launch_bounds__(kProjThreads, LEVIN ? 5 : 8) k_project(const float4 *__restrict__ xyz4, int64_t n,
                                                           const int32_t *__restrict__ idx, int k, float h,
                                                           const int32_t *__restrict__ order,
@@ -65,21 +69,23 @@ __global__ void __launch_bounds__(kProjThreads, LEVIN ? 5 : 8) k_project(const f
         deferred[atomicAdd(n_deferred, 1)] = (int32_t)slot;
         return;
     }
-    out_xyz[3 * i] = out[0];
-    out_xyz[3 * i + 1] = out[1];
-    out_xyz[3 * i + 2] = out[2];
+    const int64_t o = SORTED ? (int64_t)__float_as_int(r4.w) : i;
+    out_xyz[3 * o] = out[0];
+    out_xyz[3 * o + 1] = out[1];
+    out_xyz[3 * o + 2] = out[2];
     if (out_n) {
-        out_n[3 * i] = nf[0];
-        out_n[3 * i + 1] = nf[1];
-        out_n[3 * i + 2] = nf[2];
+        out_n[3 * o] = nf[0];
+        out_n[3 * o + 1] = nf[1];
+        out_n[3 * o + 2] = nf[2];
     }
-    if (status) status[i] = st;
+    if (status) status[o] = st;
 }
 
 // The deferred points of the mixed form, one thread each: the same routine
 // with its FP64 steps, rows read from global memory (same values and order
-// as the first pass, so the results are those of a single pass).
-template <int DEG>
+// as the first pass, so the results are those of a single pass).  SORTED as
+// in k_project.
+template <int DEG, bool SORTED = false>
 __global__ void __launch_bounds__(kProjThreads) k_project_deferred(const float4 *__restrict__ xyz4, int64_t n,
                                                                   const int32_t *__restrict__ idx, int k, float h,
                                                                   const int32_t *__restrict__ order,
@@ -97,15 +103,16 @@ __global__ void __launch_bounds__(kProjThreads) k_project_deferred(const float4 
         float out[3], nf[3];
         const uint8_t st = project_point<DEG, MLS_PREC_MIXED>(
             xyz4, [&](int j) { return __ldg(row + j); }, k, 0, 1, h, r4.x, r4.y, r4.z, out, nf);
-        out_xyz[3 * i] = out[0];
-        out_xyz[3 * i + 1] = out[1];
-        out_xyz[3 * i + 2] = out[2];
+        const int64_t o = SORTED ? (int64_t)__float_as_int(r4.w) : i;
+        out_xyz[3 * o] = out[0];
+        out_xyz[3 * o + 1] = out[1];
+        out_xyz[3 * o + 2] = out[2];
         if (out_n) {
-            out_n[3 * i] = nf[0];
-            out_n[3 * i + 1] = nf[1];
-            out_n[3 * i + 2] = nf[2];
+            out_n[3 * o] = nf[0];
+            out_n[3 * o + 1] = nf[1];
+            out_n[3 * o + 2] = nf[2];
         }
-        if (status) status[i] = st;
+        if (status) status[o] = st;
     }
 }
 
@@ -216,10 +223,10 @@ __global__ void __launch_bounds__(kProjThreads) k_project_fp64(const float *__re
                 for (int c = 0; c < M; ++c) A[a][c] += w * phi[a] * phi[c];
             }
         }
-        double pmin, pmax;
+        double pmin, pmax, invd[M];
         double a0 = 0;
-        if (cholesky<double, M>(A, L, 1e-12, pmin, pmax)) {
-            chol_solve<double, M>(L, b, x);
+        if (cholesky<double, M>(A, L, invd, 1e-12, pmin, pmax)) {
+            chol_solve<double, M>(L, invd, b, x);
             a0 = x[0];
         } else {
             st |= MLS_PT_POLY_SINGULAR;
@@ -284,6 +291,49 @@ int launch_project(const float *xyz, int64_t n, const int32_t *idx, int k, float
             return launch_deg<1>(xyz, n, idx, k, h, precision, order, out_xyz, out_n, status, st);
         default:
             return launch_deg<2>(xyz, n, idx, k, h, precision, order, out_xyz, out_n, status, st);
+    }
+}
+
+namespace {
+
+// The projection over the grid's sorted points and rows of sorted positions.
+template <int DEG>
+int launch_sorted_deg(const float4 *pts, int64_t n, const int32_t *pos, int k, float h, int precision,
+                      float *out_xyz, float *out_n, uint8_t *status, cudaStream_t st) {
+    const int blocks = (int)((n + kProjThreads - 1) / kProjThreads);
+    const size_t smem = (size_t)k * 32 * sizeof(int32_t) * (kProjThreads / 32);
+    if (precision == MLS_PREC_MIXED) {
+        ScratchSet scratch(st);
+        int32_t *deferred = nullptr;
+        MLS_CUDA_TRY(scratch.alloc(&deferred, (size_t)(n + 1) * sizeof(int32_t)));
+        int32_t *n_deferred = deferred + n;
+        MLS_CUDA_TRY(cudaMemsetAsync(n_deferred, 0, sizeof(int32_t), st));
+        auto kern = k_project<DEG, MLS_PREC_MIXED, false, true, true>;
+        MLS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        kern<<<blocks, kProjThreads, smem, st>>>(pts, n, pos, k, h, nullptr, out_xyz, out_n, status, 1, 0.f,
+                                                 deferred, n_deferred);
+        k_project_deferred<DEG, true><<<sm_count() * 2, kProjThreads, 0, st>>>(pts, n, pos, k, h, nullptr, deferred,
+                                                                                n_deferred, out_xyz, out_n, status);
+        count_launches(2);
+    } else {
+        auto kern = k_project<DEG, MLS_PREC_FP32, false, false, true>;
+        MLS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        kern<<<blocks, kProjThreads, smem, st>>>(pts, n, pos, k, h, nullptr, out_xyz, out_n, status, 1, 0.f,
+                                                 nullptr, nullptr);
+        count_launches(1);
+    }
+    MLS_CUDA_TRY(cudaGetLastError());
+    return MLS_OK;
+}
+
+}  // namespace
+
+int launch_project_sorted(const float4 *pts, int64_t n, const int32_t *pos, int k, float h, int degree,
+                          int precision, float *out_xyz, float *out_n, uint8_t *status, cudaStream_t st) {
+    switch (degree) {
+        case 0: return launch_sorted_deg<0>(pts, n, pos, k, h, precision, out_xyz, out_n, status, st);
+        case 1: return launch_sorted_deg<1>(pts, n, pos, k, h, precision, out_xyz, out_n, status, st);
+        default: return launch_sorted_deg<2>(pts, n, pos, k, h, precision, out_xyz, out_n, status, st);
     }
 }
 

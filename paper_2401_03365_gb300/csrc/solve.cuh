@@ -12,6 +12,27 @@ struct Basis {
     static constexpr int M = DEG == 0 ? 1 : (DEG == 1 ? 3 : 6);
 };
 
+// Rotation (c, s) of a Jacobi step with theta = (a_qq - a_pp) / (2 a_pq):
+// t = sign(theta) / (|theta| + sqrt(theta^2 + 1)), c = 1 / sqrt(t^2 + 1),
+// s = t c.  In FP32 with the hardware reciprocal square root and the fast
+// quotient (c^2 + s^2 = 1 to a few ulps; the rotations' rounding is then of
+// the order of the FP32 moments' own); past |theta| = 2^40 the first-order
+// value t = 1 / (2 theta) is exact in float.
+__device__ __forceinline__ void jacobi_rotation(float app, float aqq, float apq, float &c, float &s) {
+    const float theta = __fdividef(aqq - app, 2.0f * apq);
+    const float at = fabsf(theta);
+    float t = at > 0x1p40f ? __fdividef(0.5f, at) : __fdividef(1.0f, at + fmaf(theta, theta, 1.0f) * rsqrtf(fmaf(theta, theta, 1.0f)));
+    t = theta >= 0.f ? t : -t;
+    c = rsqrtf(fmaf(t, t, 1.0f));
+    s = t * c;
+}
+__device__ __forceinline__ void jacobi_rotation(double app, double aqq, double apq, double &c, double &s) {
+    const double theta = (aqq - app) / (2.0 * apq);
+    const double t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+    c = 1.0 / sqrt(t * t + 1.0);
+    s = t * c;
+}
+
 // Cyclic Jacobi on the symmetric 3x3 matrix a (xx, xy, xz, yy, yz, zz).
 // Eigenvalues ascending in lam, eigenvectors as columns of V.
 template <typename T>
@@ -31,9 +52,8 @@ __device__ void jacobi3(const T a6[6], T lam[3], T V[3][3]) {
             const int p = pq == 2 ? 1 : 0, q = pq == 0 ? 1 : 2;
             T apq = A[p][q];
             if (apq == T(0)) continue;
-            T theta = (A[q][q] - A[p][p]) / (T(2) * apq);
-            T t = (theta >= T(0) ? T(1) : T(-1)) / (fabs(theta) + sqrt(theta * theta + T(1)));
-            T c = T(1) / sqrt(t * t + T(1)), s = t * c;
+            T c, s;
+            jacobi_rotation(A[p][p], A[q][q], apq, c, s);
 #pragma unroll
             for (int r = 0; r < 3; ++r) {
                 T arp = A[r][p], arq = A[r][q];
@@ -76,11 +96,23 @@ __device__ void jacobi3(const T a6[6], T lam[3], T V[3][3]) {
     }
 }
 
-// Cholesky A = L L^T of an M x M symmetric matrix (lower triangle used).
-// Returns false when a pivot is <= rel_tol * trace.  min/max pivot (of L)
-// are returned for the conditioning estimate.
+// Square root and its reciprocal of a positive pivot: in FP32 from the
+// hardware reciprocal square root, in FP64 correctly rounded.
+__device__ __forceinline__ void root_and_inverse(float d, float &l, float &inv) {
+    inv = rsqrtf(d);
+    l = d * inv;
+}
+__device__ __forceinline__ void root_and_inverse(double d, double &l, double &inv) {
+    l = sqrt(d);
+    inv = 1.0 / l;
+}
+
+// Cholesky A = L L^T of an M x M symmetric matrix (lower triangle used),
+// with the reciprocals of L's diagonal in invd.  Returns false when a pivot
+// is <= rel_tol * trace.  min/max pivot (of L) are returned for the
+// conditioning estimate.
 template <typename T, int M>
-__device__ bool cholesky(const T A[M][M], T L[M][M], T rel_tol, T &pmin, T &pmax) {
+__device__ bool cholesky(const T A[M][M], T L[M][M], T invd[M], T rel_tol, T &pmin, T &pmax) {
     T tr = T(0);
 #pragma unroll
     for (int i = 0; i < M; ++i) tr += A[i][i];
@@ -96,11 +128,12 @@ __device__ bool cholesky(const T A[M][M], T L[M][M], T rel_tol, T &pmin, T &pmax
             ok = false;
             d = T(1);
         }
-        T l = sqrt(d);
+        T l, inv;
+        root_and_inverse(d, l, inv);
         L[j][j] = l;
+        invd[j] = inv;
         pmin = fmin(pmin, l);
         pmax = fmax(pmax, l);
-        T inv = T(1) / l;
 #pragma unroll
         for (int i = j + 1; i < M; ++i) {
             T s = A[i][j];
@@ -113,21 +146,21 @@ __device__ bool cholesky(const T A[M][M], T L[M][M], T rel_tol, T &pmin, T &pmax
 }
 
 template <typename T, int M>
-__device__ void chol_solve(const T L[M][M], const T b[M], T x[M]) {
+__device__ void chol_solve(const T L[M][M], const T invd[M], const T b[M], T x[M]) {
     T y[M];
 #pragma unroll
     for (int i = 0; i < M; ++i) {
         T s = b[i];
 #pragma unroll
         for (int c = 0; c < i; ++c) s -= L[i][c] * y[c];
-        y[i] = s / L[i][i];
+        y[i] = s * invd[i];
     }
 #pragma unroll
     for (int i = M - 1; i >= 0; --i) {
         T s = y[i];
 #pragma unroll
         for (int c = i + 1; c < M; ++c) s -= L[c][i] * x[c];
-        x[i] = s / L[i][i];
+        x[i] = s * invd[i];
     }
 }
 
@@ -153,15 +186,15 @@ __device__ void assemble(const float mom[15], T A[Basis<DEG>::M][Basis<DEG>::M])
 template <typename T, int DEG>
 __device__ T solve_a0(const float mom[15], const float rhs[6], bool refine, bool &singular, T &cond_est) {
     constexpr int M = Basis<DEG>::M;
-    T A[M][M], L[M][M], b[M], x[M];
+    T A[M][M], L[M][M], invd[M], b[M], x[M];
     assemble<T, DEG>(mom, A);
 #pragma unroll
     for (int r = 0; r < M; ++r) b[r] = (T)rhs[r];
     T pmin, pmax;
-    singular = !cholesky<T, M>(A, L, T(1e-12), pmin, pmax);
+    singular = !cholesky<T, M>(A, L, invd, T(1e-12), pmin, pmax);
     cond_est = (pmax / pmin) * (pmax / pmin);
     if (singular) return T(0);
-    chol_solve<T, M>(L, b, x);
+    chol_solve<T, M>(L, invd, b, x);
     if (refine) {
         T res[M], dx[M];
 #pragma unroll
@@ -171,7 +204,7 @@ __device__ T solve_a0(const float mom[15], const float rhs[6], bool refine, bool
             for (int c = 0; c < M; ++c) s -= A[r][c] * x[c];
             res[r] = s;
         }
-        chol_solve<T, M>(L, res, dx);
+        chol_solve<T, M>(L, invd, res, dx);
 #pragma unroll
         for (int r = 0; r < M; ++r) x[r] += dx[r];
     }

@@ -25,19 +25,21 @@ class Projection:
 
 class Pipeline:
     """Reusable buffers for repeated projections of clouds of one size:
-    the grid handle, the neighbour rows and the outputs."""
+    the grid handle, the neighbour rows (by original index, and by sorted
+    position for the projection in the grid's order) and the outputs."""
 
     def __init__(self, n: int, k: int, device="cuda"):
         self.n, self.k = n, k
         self.grid = None
         self.idx = torch.empty((n, k), dtype=torch.int32, device=device)
+        self.pos = torch.empty((n, k), dtype=torch.int32, device=device)
         self.out_xyz = torch.empty((n, 3), dtype=torch.float32, device=device)
         self.out_normal = torch.empty((n, 3), dtype=torch.float32, device=device)
         self.out_status = torch.empty(n, dtype=torch.uint8, device=device)
 
     def neighbours(self, xyz: torch.Tensor, cell_size: float = 0.0):
         self.grid = capi.mls_build_grid(xyz, cell_size, self.k, grid=self.grid)
-        capi.mls_knn(self.grid, self.k, out_idx=self.idx)
+        capi.mls_knn_sorted(self.grid, self.k, out_pos=self.pos, out_idx=self.idx)
         return self.idx
 
     def bandwidth(self, xyz: torch.Tensor) -> float:
@@ -45,9 +47,14 @@ class Pipeline:
         return 2.0 * float(capi.mls_mean_knn_dist(xyz, self.idx).item())
 
     def project(self, xyz: torch.Tensor, h: float, degree: int = 2, precision: str = "mixed"):
-        order = capi.mls_grid_order(self.grid) if self.grid is not None else None
-        capi.mls_project(xyz, self.idx, h, degree, precision, order=order, out_xyz=self.out_xyz,
-                         out_normal=self.out_normal, out_status=self.out_status)
+        """The projection of the cloud the grid was built on: in the grid's
+        order (mls_project_sorted) for FP32 and mixed, mls_project for FP64."""
+        if precision == "fp64":
+            capi.mls_project(xyz, self.idx, h, degree, precision, order=capi.mls_grid_order(self.grid),
+                             out_xyz=self.out_xyz, out_normal=self.out_normal, out_status=self.out_status)
+        else:
+            capi.mls_project_sorted(self.grid, self.pos, h, degree, precision, out_xyz=self.out_xyz,
+                                    out_normal=self.out_normal, out_status=self.out_status)
         return self.out_xyz, self.out_normal, self.out_status
 
     def close(self):
@@ -57,15 +64,20 @@ class Pipeline:
 
 
 class ProjectFunction(torch.autograd.Function):
-    """Differentiable MLS projection: forward mls_project, backward
+    """Differentiable MLS projection: forward mls_project (or
+    mls_project_sorted when the grid the rows came from and its rows of
+    sorted positions are given: the same results), backward
     mls_project_backward (gradients for the coordinates and h; the neighbour
     rows are constants).  Only xyz, the rows and h are saved: the backward
     recomputes every per-point frame."""
 
     @staticmethod
-    def forward(ctx, xyz, h, idx, degree, precision, order):
+    def forward(ctx, xyz, h, idx, degree, precision, order, grid=None, pos=None):
         hv = float(h)
-        out, nrm, st = capi.mls_project(xyz, idx, hv, degree, precision, order=order)
+        if grid is not None and pos is not None and precision != "fp64":
+            out, nrm, st = capi.mls_project_sorted(grid, pos, hv, degree, precision)
+        else:
+            out, nrm, st = capi.mls_project(xyz, idx, hv, degree, precision, order=order)
         ctx.save_for_backward(xyz, idx, order if order is not None else torch.empty(0, dtype=torch.int32))
         ctx.hv, ctx.degree, ctx.precision, ctx.has_order = hv, degree, precision, order is not None
         ctx.h_shape = h.shape if isinstance(h, torch.Tensor) else None
@@ -81,15 +93,17 @@ class ProjectFunction(torch.autograd.Function):
                                            None if g_n is None else g_n.contiguous(), ctx.degree, ctx.precision,
                                            order=order if ctx.has_order else None)
         gh_out = gh.reshape(ctx.h_shape).to(torch.float32) if ctx.h_shape is not None else None
-        return gx, gh_out, None, None, None, None
+        return gx, gh_out, None, None, None, None, None, None
 
 
 def project_differentiable(xyz: torch.Tensor, idx: torch.Tensor, h, degree: int = 2, precision: str = "mixed",
-                           order: torch.Tensor | None = None):
-    """(xyz', normal, status) with autograd to xyz and h (a tensor)."""
+                           order: torch.Tensor | None = None, grid=None, pos: torch.Tensor | None = None):
+    """(xyz', normal, status) with autograd to xyz and h (a tensor).  With
+    `grid` (built on xyz) and `pos` (its mls_knn_sorted rows) the forward
+    runs in the grid's order."""
     if not isinstance(h, torch.Tensor):
         h = torch.tensor(float(h), dtype=torch.float32, device=xyz.device)
-    return ProjectFunction.apply(xyz, h, idx, degree, precision, order)
+    return ProjectFunction.apply(xyz, h, idx, degree, precision, order, grid, pos)
 
 
 def knn(xyz: torch.Tensor, k: int, with_key: bool = False, cell_size: float = 0.0):

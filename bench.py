@@ -62,9 +62,9 @@ def bwd_flops(k):
 
 
 # The kNN's algorithmic HBM bytes per query: read its float4, write its row
-# of sorted positions and its row of original indices (k int32 each).
+# of sorted positions (k int32).
 def knn_bytes(k):
-    return 16 + 8 * k
+    return 16 + 4 * k
 
 
 GRID_BYTES_PER_POINT = 12 + 16 + 8 + 4
@@ -76,8 +76,8 @@ GRID_BYTES_PER_POINT = 12 + 16 + 8 + 4
 # valid only while the kernel sources they were taken on are unchanged
 # (SHA-256 of each file).
 KNN_MEASURED = {
-    "traffic_bytes_per_query": 338.2,
-    "warp_inst_per_query": 1952.9,
+    "traffic_bytes_per_query": 188.6,
+    "warp_inst_per_query": 1945.0,
     "sources": {
         "paper_2401_03365_gb300/csrc/knn.cu": "ba659bf82c68b49f308525f7fcce2b5156d09f66f4cf882bb5e5bec5f36f775e",
         "paper_2401_03365_gb300/csrc/grid.cuh": "1f26e02fc594d9667d1acb7d9b1153e77edb4a67bdf77bef51e92a978080535d",
@@ -259,24 +259,21 @@ def run_ours(args):
     capi.mls_knn(grid, K, out_idx=idx)
     h = 2.0 * float(capi.mls_mean_knn_dist(x, idx).item())
 
-    # one step: grid build, kNN (rows of sorted positions for the projection
-    # in the grid's order, rows of original indices for the adjoint), the
-    # projection, the adjoint with a fixed cotangent
+    # one step: grid build, kNN (rows of sorted positions), the projection and
+    # the adjoint with a fixed cotangent, both in the grid's order
     def step(xin, ev=None, before_forward_out=None, after_forward=None, before_backward=None):
         nonlocal grid
         if ev: ev[0].record(stream)
         grid = capi.mls_build_grid(xin, 0.0, K, grid=grid)
         if ev: ev[1].record(stream)
-        capi.mls_knn_sorted(grid, K, out_pos=pos, out_idx=idx)
+        capi.mls_knn_sorted(grid, K, out_pos=pos)
         if ev: ev[2].record(stream)
-        order = capi.mls_grid_order(grid)
         if before_forward_out: before_forward_out()
         capi.mls_project_sorted(grid, pos, h, 2, "mixed", out_xyz=out_xyz, out_normal=out_n, out_status=out_st)
         if ev: ev[3].record(stream)
         if after_forward: after_forward()
         if before_backward: before_backward()
-        capi.mls_project_backward(xin, idx, h, gp, gn, 2, "mixed", order=order, out_grad_xyz=grad,
-                                  out_grad_h=grad_h)
+        capi.mls_project_backward_sorted(grid, pos, h, gp, gn, 2, "mixed", out_grad_xyz=grad, out_grad_h=grad_h)
         if ev: ev[4].record(stream)
 
     events = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(args.steps)]
@@ -449,8 +446,8 @@ def run_ours(args):
         "config": {"workload": WORKLOAD if n_pts == N_POINTS else
                    WORKLOAD.replace("2,000,000", f"{n_pts:,}").replace("torus2m", "torus") + " (profiling size)",
                    "points_per_gpu": n_pts, "k": K, "degree": 2, "precision": "mixed",
-                   "h": h, "step": ("grid build + exact kNN (rows by sorted position and by original index) + "
-                                    "MLS projection in the grid's order + backward (fwd+bwd)"),
+                   "h": h, "step": ("grid build + exact kNN (rows by sorted position) + MLS projection and "
+                                    "its backward in the grid's order (fwd+bwd)"),
                    "l2": "flushed before every step (256 MB write, outside the timed events)",
                    "parallelism": f"independent clouds per GPU x{world}"},
         "fwd": {"value": job_throughput(world, n_pts, fwd_ms), "unit": "points/s", "ms_per_step": fwd_ms,
@@ -520,7 +517,7 @@ def stage_kernels(n, k, build_ms, knn_ms, proj_ms, bwd_ms, peaks, mhz):
         "project": {"ms": proj_ms, "calls": "mls_project_sorted (k_project + k_project_deferred)", "bound": "alu",
                     "flops_per_point": proj_flops(k), "achieved_tflops": proj_tf,
                     "frac": proj_tf / peaks["fp32_tflops"]},
-        "backward": {"ms": bwd_ms, "calls": "mls_project_backward (pack, counts, scan, adjoint, bucket sums)",
+        "backward": {"ms": bwd_ms, "calls": "mls_project_backward_sorted (counts, scan, adjoint, bucket sums)",
                      "bound": "alu", "flops_per_point": bwd_flops(k), "achieved_tflops": bwd_tf,
                      "frac": bwd_tf / peaks["fp32_tflops"]},
         "fp32_peak_tflops": peaks["fp32_tflops"],
@@ -662,7 +659,7 @@ def run_differentiable(args, dev, peaks, flush):
         state["grid"] = capi.mls_build_grid(x, 0.0, k, grid=state["grid"])
 
     def knn():
-        capi.mls_knn_sorted(state["grid"], k, out_pos=pos, out_idx=idx)
+        capi.mls_knn_sorted(state["grid"], k, out_pos=pos)
 
     def fwd():
         state["xg"] = x.detach().requires_grad_(True)

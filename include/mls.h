@@ -307,6 +307,21 @@ int mls_project_backward(const float *d_xyz, int64_t n, const int32_t *d_idx, in
                          const float *d_grad_out_normal, float *d_grad_xyz, float *d_grad_h, mls_stream stream);
 
 /*
+ * mls_project_backward_sorted -- mls_project_backward over the grid's sorted
+ * copy of the points and the rows of sorted positions of mls_knn_sorted (the
+ * grid not rebuilt since, its points still the cloud it was built on): the
+ * same gradients bit for bit as mls_project_backward on the matching
+ * original-index rows with the grid's order, without that form's repacking
+ * of the points and translation of the rows.  d_grad_out_xyz,
+ * d_grad_out_normal and d_grad_xyz in the original order, as there.
+ * precision MLS_PREC_FP32 or MLS_PREC_MIXED.  Scratch: about n (32 + 16 k)
+ * bytes.
+ */
+int mls_project_backward_sorted(const mls_grid *g, const int32_t *d_pos, int k, float h, int degree, int precision,
+                                const float *d_grad_out_xyz, const float *d_grad_out_normal, float *d_grad_xyz,
+                                float *d_grad_h, mls_stream stream);
+
+/*
  * mls_mean_knn_dist -- bandwidth helper (not in the paper): the mean distance,
  * in FP64, from each point to the entries of its neighbour row other than
  * itself.  Writes one double to d_out (device).  Typical use: h = 2 * value.

@@ -17,7 +17,7 @@ from .build import library_path
 
 __all__ = [
     "MLSError", "Grid", "lib", "mls_build_grid", "mls_grid_destroy", "mls_grid_size", "mls_grid_order",
-    "mls_knn", "mls_knn_sorted", "mls_knn_deferred", "mls_project_sorted", "mls_project", "mls_project_levin", "mls_project_backward", "mls_radius_neighbors",
+    "mls_knn", "mls_knn_sorted", "mls_knn_deferred", "mls_project_sorted", "mls_project_backward_sorted", "mls_project", "mls_project_levin", "mls_project_backward", "mls_radius_neighbors",
     "mls_project_rows", "mls_compact", "mls_mean_knn_dist", "mls_status_str", "mls_last_error", "mls_kernel_launches", "mls_release_scratch",
     "Batch", "mls_batch_create", "mls_batch_destroy", "mls_batch_set_shape", "mls_batch_get_shape",
     "mls_project_batched", "mls_batch_capture", "mls_batch_replay", "mls_batch_autotune", "mls_batch_tune_results",
@@ -48,6 +48,7 @@ _SIGNATURES = [
     ("mls_knn_deferred", ctypes.c_int64, [_vp, _vp]),
     ("mls_knn_sorted", _int, [_vp, _int, _vp, _vp, _vp, _vp]),
     ("mls_project_sorted", _int, [_vp, _vp, _int, ctypes.c_float, _int, _int, _vp, _vp, _vp, _vp]),
+    ("mls_project_backward_sorted", _int, [_vp, _vp, _int, ctypes.c_float, _int, _int, _vp, _vp, _vp, _vp, _vp]),
     ("mls_project", _int, [_vp, _i64, _vp, _int, _flt, _int, _int, _vp, _vp, _vp, _vp, _vp]),
     ("mls_project_noalloc", _int, [_vp, _i64, _vp, _int, _flt, _int, _int, _vp, _vp, _vp, _vp, _vp]),
     ("mls_project_levin", _int, [_vp, _i64, _vp, _int, _flt, _int, _int, _int, _flt, _vp, _vp, _vp, _vp, _vp]),
@@ -268,6 +269,30 @@ def mls_project_sorted(grid: Grid, pos: torch.Tensor, h: float, degree: int = 2,
                                   _ptr(out_xyz), _ptr(out_normal), _ptr(out_status), _stream(stream))
     _check("mls_project_sorted", rc)
     return out_xyz, out_normal, out_status
+
+
+def mls_project_backward_sorted(grid: Grid, pos: torch.Tensor, h: float, gout_xyz: torch.Tensor,
+                                gout_normal: torch.Tensor | None = None, degree: int = 2, precision: str = "mixed",
+                                out_grad_xyz=None, out_grad_h=None, stream=None):
+    """mls_project_backward over the grid's sorted points and mls_knn_sorted's
+    rows: (dL/dxyz (n, 3), dL/dh (1,)) in the original order."""
+    n = grid.n
+    _need(pos, "pos", torch.int32)
+    if pos.dim() != 2 or pos.shape[0] != n:
+        raise ValueError("pos must be (n, k)")
+    _need(gout_xyz, "gout_xyz", torch.float32, (n, 3))
+    if gout_normal is not None:
+        _need(gout_normal, "gout_normal", torch.float32, (n, 3))
+    dev = grid.xyz.device
+    out_grad_xyz = torch.empty((n, 3), dtype=torch.float32, device=dev) if out_grad_xyz is None else out_grad_xyz
+    out_grad_h = torch.empty(1, dtype=torch.float32, device=dev) if out_grad_h is None else out_grad_h
+    _need(out_grad_xyz, "out_grad_xyz", torch.float32, (n, 3))
+    _need(out_grad_h, "out_grad_h", torch.float32, (1,))
+    rc = lib().mls_project_backward_sorted(grid.handle, _ptr(pos), pos.shape[1], float(h), int(degree),
+                                           PRECISION[precision], _ptr(gout_xyz), _ptr(gout_normal),
+                                           _ptr(out_grad_xyz), _ptr(out_grad_h), _stream(stream))
+    _check("mls_project_backward_sorted", rc)
+    return out_grad_xyz, out_grad_h
 
 
 def mls_knn_deferred(grid: Grid, stream=None) -> int:

@@ -14,6 +14,9 @@ void free_grid_buffers(mls_grid *g);
 int launch_knn(const mls_grid *grid, int k, int32_t *idx, float *key, int32_t *pos, cudaStream_t st);
 int launch_project_sorted(const float4 *pts, int64_t n, const int32_t *pos, int k, float h, int degree,
                           int precision, float *out_xyz, float *out_n, uint8_t *status, cudaStream_t st);
+int launch_backward_sorted(const float4 *pts, const int32_t *order, int64_t n, const int32_t *rows, int k, float h,
+                           int degree, int precision, const float *gp, const float *gn, float *grad_xyz,
+                           float *grad_h, cudaStream_t st);
 int launch_project(const float *xyz, int64_t n, const int32_t *idx, int k, float h, int degree, int precision,
                    const int32_t *order, float *out_xyz, float *out_n, uint8_t *status, cudaStream_t st);
 int launch_radius(const mls_grid *grid, float R2, int32_t *count, const int64_t *offsets, int32_t *rows,
@@ -375,6 +378,31 @@ int mls_project_backward(const float *d_xyz, int64_t n, const int32_t *d_idx, in
         return set_error(MLS_ERR_INVALID_ARG, "mls_project_backward: output aliases an input");
     return mls::launch_backward(d_xyz, n, d_idx, k, h, degree, precision, d_order, d_grad_out_xyz,
                                 d_grad_out_normal, d_grad_xyz, d_grad_h, (cudaStream_t)stream);
+}
+
+int mls_project_backward_sorted(const mls_grid *g, const int32_t *d_pos, int k, float h, int degree, int precision,
+                                const float *d_grad_out_xyz, const float *d_grad_out_normal, float *d_grad_xyz,
+                                float *d_grad_h, mls_stream stream) {
+    mls::g_last_error[0] = 0;
+    if (!g || !d_pos || !d_grad_out_xyz || !d_grad_xyz || !d_grad_h)
+        return set_error(MLS_ERR_INVALID_ARG, "mls_project_backward_sorted: null pointer");
+    if (g->n < 1) return set_error(MLS_ERR_INVALID_ARG, "mls_project_backward_sorted: grid is empty (failed build?)");
+    if (g->n > 0x7fffffffLL / MLS_MAX_K)
+        return set_error(MLS_ERR_TOO_LARGE, "mls_project_backward_sorted: n = %lld", (long long)g->n);
+    if (k < 1 || k > MLS_MAX_K || k > g->n)
+        return set_error(MLS_ERR_K_TOO_LARGE, "mls_project_backward_sorted: k = %d not in [1, min(%d, n)]", k,
+                         MLS_MAX_K);
+    if (!(h > 0.0f) || !std::isfinite(h))
+        return set_error(MLS_ERR_INVALID_ARG, "mls_project_backward_sorted: h = %g must be finite and > 0", (double)h);
+    if (degree < 0 || degree > 2)
+        return set_error(MLS_ERR_UNSUPPORTED_DEGREE, "mls_project_backward_sorted: degree = %d", degree);
+    if (precision != MLS_PREC_FP32 && precision != MLS_PREC_MIXED)
+        return set_error(MLS_ERR_INVALID_ARG, "mls_project_backward_sorted: precision = %d (FP32 or mixed)",
+                         precision);
+    if ((const void *)d_grad_xyz == (const void *)g->xyz || (const void *)d_grad_xyz == (const void *)d_grad_out_xyz)
+        return set_error(MLS_ERR_INVALID_ARG, "mls_project_backward_sorted: output aliases an input");
+    return mls::launch_backward_sorted(g->view.pts, g->perm, g->n, d_pos, k, h, degree, precision, d_grad_out_xyz,
+                                       d_grad_out_normal, d_grad_xyz, d_grad_h, (cudaStream_t)stream);
 }
 
 int mls_mean_knn_dist(const float *d_xyz, int64_t n, const int32_t *d_idx, int k, double *d_out,

@@ -83,7 +83,10 @@ __device__ __forceinline__ void basis(float u, float v, float phi[6]) {
 
 // Six blocks per SM (80 registers): the kernel waits on its neighbour gathers,
 // and more resident warps hide more of that latency than the spills cost.
-template <int DEG, int PREC>
+// With SORTED, xyz4 is the grid's sorted copy of the points, slot s is sorted
+// position s, idx holds rows of sorted positions by sorted position (no
+// translation), and order[s] is the point's original index.
+template <int DEG, int PREC, bool SORTED = false>
 __global__ void __launch_bounds__(kBwdThreads, 6) k_backward_point(
     const float4 *__restrict__ xyz4, int64_t n, const int32_t *__restrict__ idx, int k, float h,
     const int32_t *__restrict__ order, const int32_t *__restrict__ pos, const float *__restrict__ gout_xyz,
@@ -97,15 +100,16 @@ __global__ void __launch_bounds__(kBwdThreads, 6) k_backward_point(
     const int64_t slot = blockIdx.x * (int64_t)kBwdThreads + threadIdx.x;
     const int64_t warp_base = slot - lane;
     const int64_t i = slot < n ? (order ? (int64_t)__ldg(order + slot) : slot) : -1;
+    const int64_t row_of = SORTED ? slot : i;
     const int nrows = (int)min((int64_t)32, n - warp_base);
 #pragma unroll 8
     for (int r = 0; r < 32; ++r) {
-        const int64_t i_r = __shfl_sync(0xffffffffu, i, r);
+        const int64_t i_r = __shfl_sync(0xffffffffu, row_of, r);
         if (r < nrows)
             for (int c = lane; c < k; c += 32) {
                 // the rows as sorted positions (xyz4 is in processing order)
                 const int32_t p = __ldg(idx + i_r * k + c);
-                my_rows[c * 32 + r] = pos ? __ldg(pos + p) : p;
+                my_rows[c * 32 + r] = (!SORTED && pos) ? __ldg(pos + p) : p;
             }
     }
     __syncwarp();
@@ -387,6 +391,9 @@ __global__ void k_count(const int32_t *__restrict__ idx, int64_t ne, const int32
 constexpr int kCountSlots = 256;
 constexpr int kCountWindow = 4096;
 
+// With SORTED, idx holds rows of sorted positions by sorted position (order
+// and pos unused).
+template <bool SORTED = false>
 __global__ void __launch_bounds__(256) k_count_window(const int32_t *__restrict__ idx, int64_t n, int k,
                                                       const int32_t *__restrict__ order,
                                                       const int32_t *__restrict__ pos, int32_t *__restrict__ cnt) {
@@ -398,8 +405,8 @@ __global__ void __launch_bounds__(256) k_count_window(const int32_t *__restrict_
     const int edges = (int)(min(n, s0 + kCountSlots) - s0) * k;
     for (int e = threadIdx.x; e < edges; e += blockDim.x) {
         const int64_t slot = s0 + e / k;
-        const int64_t i = __ldg(order + slot);
-        const int32_t t = __ldg(pos + __ldg(idx + i * k + e % k));
+        const int32_t t = SORTED ? __ldg(idx + slot * k + e % k)
+                                 : __ldg(pos + __ldg(idx + (int64_t)__ldg(order + slot) * k + e % k));
         const int64_t w = (int64_t)t - lo;
         if (w >= 0 && w < kCountWindow)
             atomicAdd(win + w, 1);
@@ -535,12 +542,13 @@ __global__ void __launch_bounds__(1024) k_sum_h(const double *__restrict__ part,
     if (threadIdx.x == 0) *out = (float)red[0];
 }
 
-template <int DEG>
+template <int DEG, bool SORTED = false>
 void launch_point(const float4 *xyz4, int64_t n, const int32_t *idx, int k, float h, int precision,
                   const int32_t *order, const int32_t *pos, const float *gp, const float *gn, const int32_t *off,
                   int32_t *fill, float4 *rec, float4 *self4, double *hp, int blocks, cudaStream_t st) {
     const size_t smem = (size_t)k * 32 * sizeof(int32_t) * (kBwdThreads / 32);
-    auto kern = precision == MLS_PREC_FP32 ? k_backward_point<DEG, MLS_PREC_FP32> : k_backward_point<DEG, MLS_PREC_MIXED>;
+    auto kern = precision == MLS_PREC_FP32 ? k_backward_point<DEG, MLS_PREC_FP32, SORTED>
+                                           : k_backward_point<DEG, MLS_PREC_MIXED, SORTED>;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     kern<<<blocks, kBwdThreads, smem, st>>>(xyz4, n, idx, k, h, order, pos, gp, gn, off, fill, rec, self4, hp);
 }
@@ -575,7 +583,7 @@ int launch_backward(const float *xyz, int64_t n, const int32_t *idx, int k, floa
         ++launches;
     }
     if (order)
-        k_count_window<<<(int)((n + kCountSlots - 1) / kCountSlots), 256, 0, st>>>(idx, n, k, order, pos, cnt);
+        k_count_window<false><<<(int)((n + kCountSlots - 1) / kCountSlots), 256, 0, st>>>(idx, n, k, order, pos, cnt);
     else
         k_count<<<(int)std::min<int64_t>((ne + 255) / 256, (int64_t)sms * 32), 256, 0, st>>>(idx, ne, pos, cnt);
     int rc = device_exclusive_scan(cnt, off, n + 1, st);
@@ -589,6 +597,40 @@ int launch_backward(const float *xyz, int64_t n, const int32_t *idx, int k, floa
         n, order, off, rec, self4, grad_xyz);
     k_sum_h<<<1, 1024, 0, st>>>(hp, blocks, grad_h);
     count_launches(launches + 4);   // + count, point, bucket sum, sum_h (the scan counts its own)
+    MLS_CUDA_TRY(cudaGetLastError());
+    return MLS_OK;
+}
+
+int launch_backward_sorted(const float4 *pts, const int32_t *order, int64_t n, const int32_t *rows, int k, float h,
+                           int degree, int precision, const float *gp, const float *gn, float *grad_xyz,
+                           float *grad_h, cudaStream_t st) {
+    const int64_t ne = n * (int64_t)k;
+    const int blocks = (int)((n + kBwdThreads - 1) / kBwdThreads);
+    float4 *rec = nullptr, *self4 = nullptr;
+    double *hp = nullptr;
+    int32_t *cnt = nullptr, *off = nullptr;
+    ScratchSet scratch(st);     // every buffer freed on every return below
+    MLS_CUDA_TRY(scratch.alloc(&rec, (size_t)ne * sizeof(float4)));
+    MLS_CUDA_TRY(scratch.alloc(&self4, (size_t)n * sizeof(float4)));
+    MLS_CUDA_TRY(scratch.alloc(&hp, (size_t)blocks * sizeof(double)));
+    MLS_CUDA_TRY(scratch.alloc(&cnt, (size_t)(2 * n + 2) * sizeof(int32_t)));
+    MLS_CUDA_TRY(scratch.alloc(&off, (size_t)(n + 1) * sizeof(int32_t)));
+    int32_t *fill = cnt + n + 1;
+    const int sms = sm_count();
+    MLS_CUDA_TRY(cudaMemsetAsync(cnt, 0, (size_t)(2 * n + 2) * sizeof(int32_t), st));
+    k_count_window<true><<<(int)((n + kCountSlots - 1) / kCountSlots), 256, 0, st>>>(rows, n, k, nullptr, nullptr,
+                                                                                      cnt);
+    int rc = device_exclusive_scan(cnt, off, n + 1, st);
+    if (rc != MLS_OK) return rc;
+    switch (degree) {
+        case 0: launch_point<0, true>(pts, n, rows, k, h, precision, order, nullptr, gp, gn, off, fill, rec, self4, hp, blocks, st); break;
+        case 1: launch_point<1, true>(pts, n, rows, k, h, precision, order, nullptr, gp, gn, off, fill, rec, self4, hp, blocks, st); break;
+        default: launch_point<2, true>(pts, n, rows, k, h, precision, order, nullptr, gp, gn, off, fill, rec, self4, hp, blocks, st); break;
+    }
+    k_bucket_sum<kSumLanes, kSumCached><<<(int)std::min<int64_t>((n * kSumLanes + 255) / 256, (int64_t)sms * 32), 256, 0, st>>>(
+        n, order, off, rec, self4, grad_xyz);
+    k_sum_h<<<1, 1024, 0, st>>>(hp, blocks, grad_h);
+    count_launches(4);   // count, point, bucket sum, sum_h (the scan counts its own)
     MLS_CUDA_TRY(cudaGetLastError());
     return MLS_OK;
 }

@@ -64,12 +64,12 @@ class Pipeline:
 
 
 class ProjectFunction(torch.autograd.Function):
-    """Differentiable MLS projection: forward mls_project (or
-    mls_project_sorted when the grid the rows came from and its rows of
-    sorted positions are given: the same results), backward
+    """Differentiable MLS projection: forward mls_project, backward
     mls_project_backward (gradients for the coordinates and h; the neighbour
-    rows are constants).  Only xyz, the rows and h are saved: the backward
-    recomputes every per-point frame."""
+    rows are constants); with the grid the rows came from and its rows of
+    sorted positions, mls_project_sorted and mls_project_backward_sorted (the
+    same results, in the grid's order).  Only xyz, the rows and h are saved:
+    the backward recomputes every per-point frame."""
 
     @staticmethod
     def forward(ctx, xyz, h, idx, degree, precision, order, grid=None, pos=None):
@@ -80,6 +80,7 @@ class ProjectFunction(torch.autograd.Function):
             out, nrm, st = capi.mls_project(xyz, idx, hv, degree, precision, order=order)
         ctx.save_for_backward(xyz, idx, order if order is not None else torch.empty(0, dtype=torch.int32))
         ctx.hv, ctx.degree, ctx.precision, ctx.has_order = hv, degree, precision, order is not None
+        ctx.sorted = (grid, pos) if grid is not None and pos is not None and precision != "fp64" else None
         ctx.h_shape = h.shape if isinstance(h, torch.Tensor) else None
         ctx.mark_non_differentiable(st)
         return out, nrm, st
@@ -89,9 +90,15 @@ class ProjectFunction(torch.autograd.Function):
         xyz, idx, order = ctx.saved_tensors
         if g_out is None:
             g_out = torch.zeros_like(xyz)
-        gx, gh = capi.mls_project_backward(xyz, idx, ctx.hv, g_out.contiguous(),
-                                           None if g_n is None else g_n.contiguous(), ctx.degree, ctx.precision,
-                                           order=order if ctx.has_order else None)
+        if ctx.sorted is not None:
+            grid, pos = ctx.sorted
+            gx, gh = capi.mls_project_backward_sorted(grid, pos, ctx.hv, g_out.contiguous(),
+                                                      None if g_n is None else g_n.contiguous(), ctx.degree,
+                                                      ctx.precision)
+        else:
+            gx, gh = capi.mls_project_backward(xyz, idx, ctx.hv, g_out.contiguous(),
+                                               None if g_n is None else g_n.contiguous(), ctx.degree, ctx.precision,
+                                               order=order if ctx.has_order else None)
         gh_out = gh.reshape(ctx.h_shape).to(torch.float32) if ctx.h_shape is not None else None
         return gx, gh_out, None, None, None, None, None, None
 

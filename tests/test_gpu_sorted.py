@@ -98,3 +98,37 @@ def test_sorted_argument_errors(capi):
     assert e.value.code == -2
     torch.cuda.synchronize()
     grid.close()
+
+
+@pytest.mark.parametrize("precision", ["mixed", "fp32"])
+@pytest.mark.parametrize("degree", [1, 2])
+def test_sorted_backward_equals_mls_project_backward(capi, degree, precision):
+    """The adjoint in the grid's order: bit-identical gradients (coordinates
+    and h) to mls_project_backward with the grid's order."""
+    c = workloads.torus(n=120_000, seed=42)
+    x, grid, pos, idx, _, order = _setup(capi, c.xyz, c.k)
+    h = 2.0 * float(capi.mls_mean_knn_dist(x, idx).item())
+    gen = torch.Generator(device="cuda").manual_seed(43)
+    gp = torch.randn(c.n, 3, device="cuda", generator=gen)
+    gn = 0.1 * torch.randn(c.n, 3, device="cuda", generator=gen)
+    a, ah = capi.mls_project_backward_sorted(grid, pos, h, gp, gn, degree, precision)
+    b, bh = capi.mls_project_backward(x, idx, h, gp, gn, degree, precision, order=order)
+    torch.cuda.synchronize()
+    grid.close()
+    assert torch.equal(a, b) and torch.equal(ah, bh)
+
+
+def test_sorted_autograd_equals_unsorted(capi):
+    from paper_2401_03365_gb300 import mls
+    c = workloads.bumpy_sphere(n=50_000, seed=44)
+    x, grid, pos, idx, _, order = _setup(capi, c.xyz, c.k)
+    grads = []
+    for kw in ({"order": order}, {"order": order, "grid": grid, "pos": pos}):
+        xg = x.clone().requires_grad_(True)
+        ht = torch.tensor(0.03, device="cuda", requires_grad=True)
+        out, nrm, _ = mls.project_differentiable(xg, idx, ht, 2, "fp32", **kw)
+        ((out.norm(dim=1) - 1.0) ** 2).sum().add(0.1 * nrm[:, 2].sum()).backward()
+        grads.append((xg.grad.clone(), ht.grad.clone()))
+    torch.cuda.synchronize()
+    grid.close()
+    assert torch.equal(grads[0][0], grads[1][0]) and torch.equal(grads[0][1], grads[1][1])

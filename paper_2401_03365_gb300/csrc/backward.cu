@@ -96,7 +96,7 @@ __global__ void __launch_bounds__(kBwdThreads, 6) k_backward_point(
     extern __shared__ int32_t rows[];
     __shared__ double hred[kBwdThreads / 32];
     const int lane = threadIdx.x & 31;
-    int32_t *my_rows = rows + (threadIdx.x >> 5) * k * 32;
+    int32_t *my_rows = rows + (threadIdx.x >> 5) * k * kRowStride;
     const int64_t slot = blockIdx.x * (int64_t)kBwdThreads + threadIdx.x;
     const int64_t warp_base = slot - lane;
     const int64_t i = slot < n ? (order ? (int64_t)__ldg(order + slot) : slot) : -1;
@@ -109,7 +109,7 @@ __global__ void __launch_bounds__(kBwdThreads, 6) k_backward_point(
             for (int c = lane; c < k; c += 32) {
                 // the rows as sorted positions (xyz4 is in processing order)
                 const int32_t p = __ldg(idx + i_r * k + c);
-                my_rows[c * 32 + r] = (!SORTED && pos) ? __ldg(pos + p) : p;
+                my_rows[c * kRowStride + r] = (!SORTED && pos) ? __ldg(pos + p) : p;
             }
     }
     __syncwarp();
@@ -123,7 +123,7 @@ __global__ void __launch_bounds__(kBwdThreads, 6) k_backward_point(
         float W = 0.f, m[3] = {0.f, 0.f, 0.f};
         float C[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         for (int j = 0; j < k; ++j) {
-            const float4 p = __ldg(xyz4 + my_rows[j * 32 + lane]);
+            const float4 p = __ldg(xyz4 + my_rows[j * kRowStride + lane]);
             const float d[3] = {p.x - rx, p.y - ry, p.z - rz};
             const float w = exp2f(fmaf(d[0], d[0], fmaf(d[1], d[1], d[2] * d[2])) * neg_scale);
             const float Wn = W + w, c = __fdividef(w, Wn);
@@ -161,7 +161,7 @@ __global__ void __launch_bounds__(kBwdThreads, 6) k_backward_point(
         float rbar[3] = {gp[0], gp[1], gp[2]};
         // a free place in the bucket of neighbour j (its sorted position)
         auto bucket_slot = [&](int j) {
-            const int32_t t = my_rows[j * 32 + lane];
+            const int32_t t = my_rows[j * kRowStride + lane];
             return __ldg(off + t) + atomicAdd(fill + t, 1);
         };
         if (flag & MLS_PT_PLANE_DEGENERATE) {
@@ -178,7 +178,7 @@ __global__ void __launch_bounds__(kBwdThreads, 6) k_backward_point(
 #pragma unroll
             for (int c = 0; c < 6; ++c) rhs[c] = 0.f;
             for (int j = 0; j < k; ++j) {
-                const float4 p = __ldg(xyz4 + my_rows[j * 32 + lane]);
+                const float4 p = __ldg(xyz4 + my_rows[j * kRowStride + lane]);
                 const float d[3] = {p.x - rx, p.y - ry, p.z - rz};
                 const float w = exp2f(fmaf(d[0], d[0], fmaf(d[1], d[1], d[2] * d[2])) * neg_scale);
                 const float u = (e1[0] * d[0] + e1[1] * d[1] + e1[2] * d[2]) * ih;
@@ -235,7 +235,7 @@ __global__ void __launch_bounds__(kBwdThreads, 6) k_backward_point(
             float ofsbar = s0bar;
             if (ok) {
                 for (int j = 0; j < k; ++j) {
-                    const float4 p = __ldg(xyz4 + my_rows[j * 32 + lane]);
+                    const float4 p = __ldg(xyz4 + my_rows[j * kRowStride + lane]);
                     const float d[3] = {p.x - rx, p.y - ry, p.z - rz};
                     const float w = exp2f(fmaf(d[0], d[0], fmaf(d[1], d[1], d[2] * d[2])) * neg_scale);
                     const float u = (e1[0] * d[0] + e1[1] * d[1] + e1[2] * d[2]) * ih;
@@ -298,7 +298,7 @@ __global__ void __launch_bounds__(kBwdThreads, 6) k_backward_point(
             const float iW = 1.f / W;
             for (int j = 0; j < k; ++j) {
                 const int32_t at = bucket_slot(j);      // taken early: its latency overlaps the arithmetic
-                const float4 p = __ldg(xyz4 + my_rows[j * 32 + lane]);
+                const float4 p = __ldg(xyz4 + my_rows[j * kRowStride + lane]);
                 const float d[3] = {p.x - rx, p.y - ry, p.z - rz};
                 const float dd = fmaf(d[0], d[0], fmaf(d[1], d[1], d[2] * d[2]));
                 const float w = exp2f(dd * neg_scale);
@@ -546,7 +546,7 @@ template <int DEG, bool SORTED = false>
 void launch_point(const float4 *xyz4, int64_t n, const int32_t *idx, int k, float h, int precision,
                   const int32_t *order, const int32_t *pos, const float *gp, const float *gn, const int32_t *off,
                   int32_t *fill, float4 *rec, float4 *self4, double *hp, int blocks, cudaStream_t st) {
-    const size_t smem = (size_t)k * 32 * sizeof(int32_t) * (kBwdThreads / 32);
+    const size_t smem = (size_t)k * kRowStride * sizeof(int32_t) * (kBwdThreads / 32);
     auto kern = precision == MLS_PREC_FP32 ? k_backward_point<DEG, MLS_PREC_FP32, SORTED>
                                            : k_backward_point<DEG, MLS_PREC_MIXED, SORTED>;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -88,7 +88,7 @@ __global__ void __launch_bounds__(kBatchMaxThreads, 4) k_project_batched(BatchAr
     const int sub = lane & (G - 1);
     const int grp = threadIdx.x / G;
     const int ppr = blockDim.x / G;
-    int32_t *my_rows = rows + warp * a.k_max * 32;
+    int32_t *my_rows = rows + warp * a.k_max * kRowStride;
     for (;;) {
         if (threadIdx.x == 0) s_tile = (int)atomicAdd(a.counter, 1u);
         __syncthreads();
@@ -130,13 +130,13 @@ __global__ void __launch_bounds__(kBatchMaxThreads, 4) k_project_batched(BatchAr
                 for (int r = 0; r < 32; ++r) {
                     const int64_t i_r = __shfl_sync(0xffffffffu, i, r);
                     if (r < nrows)
-                        for (int c = lane; c < k; c += 32) my_rows[c * 32 + r] = __ldg(idx + i_r * k + c);
+                        for (int c = lane; c < k; c += 32) my_rows[c * kRowStride + r] = __ldg(idx + i_r * k + c);
                 }
                 __syncwarp();
                 if (slot >= end) continue;
                 const float4 r4 = __ldg(x4 + i);
                 st = project_point<DEG, PREC>(
-                    x4, [&](int j) { return my_rows[j * 32 + lane]; }, k, 0, 1, h, r4.x, r4.y, r4.z, out, nf);
+                    x4, [&](int j) { return my_rows[j * kRowStride + lane]; }, k, 0, 1, h, r4.x, r4.y, r4.z, out, nf);
                 write = true;
             } else {
                 // G lanes per point: the whole warp runs the shuffles, lanes
@@ -188,7 +188,7 @@ bool valid_shape(int lanes, int threads, int rounds) {
 }
 
 size_t batch_smem(const mls_batch *b) {
-    return b->lanes == 1 ? (size_t)b->k_max * 32 * sizeof(int32_t) * (b->threads / 32) : 0;
+    return b->lanes == 1 ? (size_t)b->k_max * kRowStride * sizeof(int32_t) * (b->threads / 32) : 0;
 }
 
 // Tile offsets for the current shape, uploaded synchronously.

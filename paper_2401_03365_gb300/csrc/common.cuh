@@ -9,6 +9,12 @@
 namespace mls {
 
 constexpr int kWarp = 32;
+// A warp's 32 neighbour rows staged transposed in shared memory: entry j of
+// lane t at j * kRowStride + t.  A stride of 33 words puts the staging
+// writes (lanes over j, one row at a time) and the reads (lanes over t) in
+// 32 different banks; a stride of 32 made every staging write a 32-way bank
+// conflict.
+constexpr int kRowStride = 33;
 constexpr int kMortonBits = 21;                  // bits per axis of a level-0 cell coordinate
 constexpr uint32_t kAxisCells = 1u << kMortonBits;
 constexpr int kMaxLevels = kMortonBits + 1;      // level L: cell side s0 * 2^L, L = 0..21

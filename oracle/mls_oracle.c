@@ -298,8 +298,9 @@ int oracle_knn_kdtree(const float *xyz, int64_t n, int k, const int64_t *queries
     return 0;
 }
 
-/* Bandwidth helper (not in the paper): twice the mean distance from each point
- * to the members of its neighbour list other than itself, in FP64. */
+/* Bandwidth helper (not in the paper): the mean distance from each point to
+ * the members of its neighbour list other than itself, in FP64 (the
+ * workloads take h = 2 x this mean). */
 double oracle_mean_knn_dist(const float *xyz, int64_t n, const int32_t *idx, int k)
 {
     double sum = 0.0;

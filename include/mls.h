@@ -409,6 +409,21 @@ int mls_batch_autotune(mls_batch *b, const float *d_xyz, const int32_t *d_idx, c
  * (HOST); either may be NULL.  Returns the number of entries. */
 int mls_batch_tune_results(const mls_batch *b, int capacity, int32_t *shapes, float *ms);
 
+/*
+ * mls_points_in_boxes -- the halo test of one cloud split over ranks (the
+ * paper's contiguous segments, Sec. 2.1, exchanged exactly): sets
+ * d_mask[i] = 1 for every point i of the grid's cloud that lies inside at
+ * least one of the m axis-aligned boxes (closed: lo <= x <= hi on each axis),
+ * and leaves every other entry as it was (zero it first).
+ *   d_boxes  device, m x 6 floats: lo x, y, z, hi x, y, z (an empty or NaN
+ *            box selects nothing); m >= 0
+ *   d_mask   device, n bytes, original order
+ * One warp per box over the grid's cells; cost grows with the number of
+ * cells a box covers at the base level (a box far larger than the cloud's
+ * cells is visited at a coarse level).  Asynchronous on `stream`.
+ */
+int mls_points_in_boxes(const mls_grid *g, const float *d_boxes, int64_t m, uint8_t *d_mask, mls_stream stream);
+
 /* Scratch memory.  mls_project, mls_project_backward and the helpers take
  * their per-call buffers, stream-ordered, from a memory pool of the library's
  * own (one per device) that keeps freed memory mapped for the next call

@@ -17,7 +17,7 @@ from .build import library_path
 
 __all__ = [
     "MLSError", "Grid", "lib", "mls_build_grid", "mls_grid_destroy", "mls_grid_size", "mls_grid_order",
-    "mls_knn", "mls_knn_sorted", "mls_knn_deferred", "mls_project_sorted", "mls_project_backward_sorted", "mls_project", "mls_project_levin", "mls_project_backward", "mls_radius_neighbors",
+    "mls_knn", "mls_knn_sorted", "mls_knn_deferred", "mls_points_in_boxes", "mls_project_sorted", "mls_project_backward_sorted", "mls_project", "mls_project_levin", "mls_project_backward", "mls_radius_neighbors",
     "mls_project_rows", "mls_compact", "mls_mean_knn_dist", "mls_status_str", "mls_last_error", "mls_kernel_launches", "mls_release_scratch",
     "Batch", "mls_batch_create", "mls_batch_destroy", "mls_batch_set_shape", "mls_batch_get_shape",
     "mls_project_batched", "mls_batch_capture", "mls_batch_replay", "mls_batch_autotune", "mls_batch_tune_results",
@@ -46,6 +46,7 @@ _SIGNATURES = [
     ("mls_grid_order", _vp, [_vp]),
     ("mls_knn", _int, [_vp, _int, _vp, _vp, _vp]),
     ("mls_knn_deferred", ctypes.c_int64, [_vp, _vp]),
+    ("mls_points_in_boxes", _int, [_vp, _vp, _i64, _vp, _vp]),
     ("mls_knn_sorted", _int, [_vp, _int, _vp, _vp, _vp, _vp]),
     ("mls_project_sorted", _int, [_vp, _vp, _int, ctypes.c_float, _int, _int, _vp, _vp, _vp, _vp]),
     ("mls_project_backward_sorted", _int, [_vp, _vp, _int, ctypes.c_float, _int, _int, _vp, _vp, _vp, _vp, _vp]),
@@ -293,6 +294,22 @@ def mls_project_backward_sorted(grid: Grid, pos: torch.Tensor, h: float, gout_xy
                                            _ptr(out_grad_xyz), _ptr(out_grad_h), _stream(stream))
     _check("mls_project_backward_sorted", rc)
     return out_grad_xyz, out_grad_h
+
+
+def mls_points_in_boxes(grid: Grid, boxes: torch.Tensor, out_mask=None, stream=None):
+    """uint8 mask (n,) over the grid's cloud: 1 where a point lies in any of
+    the boxes (m, 6) float32 (lo xyz, hi xyz)."""
+    n = grid.n
+    boxes = boxes.contiguous()
+    _need(boxes, "boxes", torch.float32)
+    if boxes.dim() != 2 or boxes.shape[1] != 6:
+        raise ValueError("boxes must be (m, 6)")
+    if out_mask is None:
+        out_mask = torch.zeros(n, dtype=torch.uint8, device=grid.xyz.device)
+    _need(out_mask, "out_mask", torch.uint8, (n,))
+    _check("mls_points_in_boxes", lib().mls_points_in_boxes(grid.handle, _ptr(boxes), boxes.shape[0], _ptr(out_mask),
+                                                            _stream(stream)))
+    return out_mask
 
 
 def mls_knn_deferred(grid: Grid, stream=None) -> int:

@@ -14,6 +14,7 @@ void free_grid_buffers(mls_grid *g);
 int launch_knn(const mls_grid *grid, int k, int32_t *idx, float *key, int32_t *pos, cudaStream_t st);
 int launch_project_sorted(const float4 *pts, int64_t n, const int32_t *pos, int k, float h, int degree,
                           int precision, float *out_xyz, float *out_n, uint8_t *status, cudaStream_t st);
+int launch_points_in_boxes(const mls_grid *grid, const float *boxes, int64_t m, uint8_t *mask, cudaStream_t st);
 int launch_backward_sorted(const float4 *pts, const int32_t *order, int64_t n, const int32_t *rows, int k, float h,
                            int degree, int precision, const float *gp, const float *gn, float *grad_xyz,
                            float *grad_h, cudaStream_t st);
@@ -403,6 +404,15 @@ int mls_project_backward_sorted(const mls_grid *g, const int32_t *d_pos, int k, 
         return set_error(MLS_ERR_INVALID_ARG, "mls_project_backward_sorted: output aliases an input");
     return mls::launch_backward_sorted(g->view.pts, g->perm, g->n, d_pos, k, h, degree, precision, d_grad_out_xyz,
                                        d_grad_out_normal, d_grad_xyz, d_grad_h, (cudaStream_t)stream);
+}
+
+int mls_points_in_boxes(const mls_grid *g, const float *d_boxes, int64_t m, uint8_t *d_mask, mls_stream stream) {
+    mls::g_last_error[0] = 0;
+    if (!g || !d_mask || (m > 0 && !d_boxes))
+        return set_error(MLS_ERR_INVALID_ARG, "mls_points_in_boxes: null pointer");
+    if (g->n < 1) return set_error(MLS_ERR_INVALID_ARG, "mls_points_in_boxes: grid is empty (failed build?)");
+    if (m < 0) return set_error(MLS_ERR_INVALID_ARG, "mls_points_in_boxes: m = %lld < 0", (long long)m);
+    return mls::launch_points_in_boxes(g, d_boxes, m, d_mask, (cudaStream_t)stream);
 }
 
 int mls_mean_knn_dist(const float *d_xyz, int64_t n, const int32_t *d_idx, int k, double *d_out,

@@ -1,7 +1,8 @@
 """Sharding of one cloud over CPU ranks (gloo, 127.0.0.1): contiguous ranges
-of a Morton order, one halo exchange, then the local search and projection.
-With the FP64 oracle as every rank's local step, the ranks' rows and
-projected points must equal the single-process oracle's, bit for bit."""
+of a Morton order, one halo exchange of float4 records, then the local search
+and projection.  With the FP64 oracle as every rank's local step, the ranks'
+rows and projected points must equal the single-process oracle's, bit for
+bit, also when a rank holds no points or fewer than k."""
 import os
 import socket
 import sys
@@ -14,16 +15,26 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 class OracleOps:
-    """The oracle as the local step of every rank (test infrastructure)."""
+    """The oracle as the local step of every rank (test infrastructure), on
+    CPU tensors."""
 
     def knn(self, xyz, k):
+        import torch
         import oracle
-        return oracle.knn_kdtree(xyz, k)
+        idx, key = oracle.knn_kdtree(xyz.numpy(), k)
+        return torch.from_numpy(idx), torch.from_numpy(key)
+
+    def in_boxes(self, xyz, boxes):
+        import torch
+        x = xyz.numpy().astype(np.float64)[:, None, :]
+        b = boxes.numpy().astype(np.float64)[None]
+        return torch.from_numpy(((x >= b[..., :3]) & (x <= b[..., 3:])).all(-1).any(-1))
 
     def project(self, xyz, rows, h, degree, precision):
+        import torch
         import oracle
-        out, nrm, st, _ = oracle.project(xyz, rows, h, degree)
-        return out, nrm, st
+        out, nrm, st, _ = oracle.project(xyz.numpy(), rows.numpy(), h, degree)
+        return torch.from_numpy(out), torch.from_numpy(nrm), torch.from_numpy(st)
 
 
 def zorder(xyz, bits=10):
@@ -43,17 +54,22 @@ def _free_port():
         return s.getsockname()[1]
 
 
-def _rank_main(rank, world, port, xyz, k, h, out):
+def _rank_main(rank, world, port, xyz, k, h, out, cuts=None):
     os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
     sys.path.insert(0, ROOT)
+    import torch
     import torch.distributed as dist
     from paper_2401_03365_gb300 import shard
     dist.init_process_group("gloo", rank=rank, world_size=world)
     try:
-        parts = shard.morton_partition(zorder(xyz), world)
-        ids = parts[rank]
-        res = shard.sharded_project(xyz[ids], ids, k, h, OracleOps(), block=64)
-        out[rank] = (res.global_ids, res.rows, res.xyz, res.normal, res.status, res.halo)
+        order = torch.from_numpy(zorder(xyz))
+        if cuts is None:
+            ids = shard.morton_partition(order, world)[rank]
+        else:
+            ids = order[cuts[rank]:cuts[rank + 1]]
+        res = shard.sharded_project(torch.from_numpy(xyz)[ids], ids, k, h, OracleOps(), block=64)
+        out[rank] = tuple(t.numpy() if hasattr(t, "numpy") else t
+                          for t in (res.global_ids, res.rows, res.xyz, res.normal, res.status, res.halo))
         dist.barrier()
     finally:
         dist.destroy_process_group()
@@ -68,14 +84,13 @@ def _cloud():
     return c.xyz, c.k, h, rows
 
 
-@pytest.mark.parametrize("world", [2, 3])
-def test_sharded_rows_and_projection_equal_the_whole_cloud(world):
+def _run(world, cuts=None):
     import oracle
     xyz, k, h, rows = _cloud()
     ref_xyz, ref_n, ref_st, _ = oracle.project(xyz, rows, h, 2)
     with mp.Manager() as mgr:
         out = mgr.dict()
-        mp.spawn(_rank_main, args=(world, _free_port(), xyz, k, h, out), nprocs=world, join=True)
+        mp.spawn(_rank_main, args=(world, _free_port(), xyz, k, h, out, cuts), nprocs=world, join=True)
         res = dict(out)
     seen = np.zeros(xyz.shape[0], int)
     for r in range(world):
@@ -85,8 +100,24 @@ def test_sharded_rows_and_projection_equal_the_whole_cloud(world):
         assert np.array_equal(r_xyz, ref_xyz[ids])
         assert np.array_equal(r_n, ref_n[ids])
         assert np.array_equal(r_st, ref_st[ids])
-        assert 0 < halo < xyz.shape[0]          # a halo, not the whole cloud
     assert np.all(seen == 1)
+    return res, xyz.shape[0]
+
+
+@pytest.mark.parametrize("world", [2, 3])
+def test_sharded_rows_and_projection_equal_the_whole_cloud(world):
+    res, n = _run(world)
+    for r in range(world):
+        assert 0 < res[r][5] < n            # a halo, not the whole cloud
+
+
+def test_a_rank_with_no_points_and_one_with_fewer_than_k():
+    """Three ranks: the first holds nothing (it asks for nothing and returns
+    empty results), the second 5 points (< k = 16: it asks for every point),
+    the third the rest."""
+    res, n = _run(3, cuts=[0, 0, 5, 5000])
+    assert res[0][0].shape[0] == 0 and res[0][1].shape == (0, 16)
+    assert res[1][5] == n - 5               # every other point was sent to it
 
 
 def test_request_boxes_cover_every_neighbour():
@@ -96,11 +127,13 @@ def test_request_boxes_cover_every_neighbour():
     from paper_2401_03365_gb300 import shard
     import oracle
     xyz, k, h, rows = _cloud()
+    import torch
     order = zorder(xyz)
     own = order[: xyz.shape[0] // 2]
     _, key = oracle.knn_kdtree(xyz[own], k)
-    boxes = shard.request_boxes(xyz[own], key[:, k - 1], block=64)
+    boxes = shard.request_boxes(torch.from_numpy(xyz[own]), torch.from_numpy(key[:, k - 1]), block=64)
+    assert boxes.dtype == torch.float32
     for b in range(len(boxes)):
         blk = own[b * 64:(b + 1) * 64]
         nb = np.unique(rows[blk].ravel())
-        assert shard.in_boxes(xyz[nb], boxes[b:b + 1]).all()
+        assert OracleOps().in_boxes(torch.from_numpy(xyz[nb]), boxes[b:b + 1]).all()

@@ -74,13 +74,13 @@ GRID_BYTES_PER_POINT = 12 + 16 + 8 + 4
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) and warp
 # instructions (smsp__inst_executed.sum), each divided by the point count;
 # valid only while the kernel sources they were taken on are unchanged
-# (SHA-256 of each file; common.cuh's digest was renewed after a constant the
-# kNN does not use was added to it).
+# (SHA-256 of each file).
 KNN_MEASURED = {
-    "traffic_bytes_per_query": 188.6,
-    "warp_inst_per_query": 1945.0,
+    "traffic_bytes_per_query": 189.2,
+    "warp_inst_per_query": 1941.0,
     "sources": {
-        "paper_2401_03365_gb300/csrc/knn.cu": "ba659bf82c68b49f308525f7fcce2b5156d09f66f4cf882bb5e5bec5f36f775e",
+        "paper_2401_03365_gb300/csrc/knn_search.cuh": "23ebf51688de2c531c11bf0b32f33ac2d8da2d531ee86599435e2ca41feadf0e",
+        "paper_2401_03365_gb300/csrc/knn.cu": "470f58fe69c1f58563c8f1e454b37c39a0565081610272e985b97499275b7fb2",
         "paper_2401_03365_gb300/csrc/grid.cuh": "1f26e02fc594d9667d1acb7d9b1153e77edb4a67bdf77bef51e92a978080535d",
         "paper_2401_03365_gb300/csrc/common.cuh": "9d6ac0dc2ad528cdc5d1d35b34889db2a24ebc7196733e8c248a68ed29f7d816",
     },
@@ -417,6 +417,21 @@ def run_ours(args):
             rd_ms.append(a.elapsed_time(b))
     rd_mean_nb = float(off_r[-1].item()) / n_pts
     rd_kept = int(kept_r.shape[0])
+
+    # the kNN and the projection in one pass (rows kept on chip, not
+    # written), on the same grid and h, against the timed step's two passes
+    fz = [torch.empty_like(x), torch.empty_like(x), torch.empty(n_pts, dtype=torch.uint8, device=dev)]
+    for _ in range(2):
+        capi.mls_knn_project(grid, K, h, 2, "mixed", out_xyz=fz[0], out_normal=fz[1], out_status=fz[2])
+    fz_ms = []
+    for _ in range(5):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        capi.mls_knn_project(grid, K, h, 2, "mixed", out_xyz=fz[0], out_normal=fz[1], out_status=fz[2])
+        b.record(stream)
+        b.synchronize()
+        fz_ms.append(a.elapsed_time(b))
     grid.close()
     del pos
     if rank != 0:
@@ -468,6 +483,11 @@ def run_ours(args):
                    "step": f"mls_radius_count + mls_radius_rows + mls_project_rows + mls_compact, R = h = {R_ball}, "
                            "mixed, degree 2, outliers (< 3 neighbours) dropped; on the already built grid",
                    "mean_neighbours": rd_mean_nb, "kept": rd_kept},
+        "fused": {"ms": float(np.median(fz_ms)), "points_per_s": n_pts / (float(np.median(fz_ms)) * 1e-3),
+                  "two_pass_ms": knn_ms + proj_ms,
+                  "step": "mls_knn_project: exact kNN + MLS projection in one pass (each warp projects its last 32 "
+                          "queries from an L2-resident row buffer; rows not written), mixed, degree 2, same grid "
+                          "and h; two_pass_ms = the timed step's mls_knn_sorted + mls_project_sorted"},
         "e2e": {"value": e2e_value, "unit": "points/s", "h2d_bytes_per_step": n_pts * 12,
                 "d2h_bytes_per_step": n_pts * (12 + 12 + 1 + 12)},
         "gpu_launches": int(launches),

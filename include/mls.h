@@ -83,6 +83,7 @@ enum mls_point_status {
 };
 
 #define MLS_MAX_K 64
+#define MLS_MAX_K_FUSED 32   /* largest k of mls_knn_project */
 
 /*
  * mls_build_grid -- spatial index for the neighbour search that precedes each
@@ -169,6 +170,30 @@ int mls_knn_sorted(const mls_grid *g, int k, int32_t *d_pos, int32_t *d_idx, flo
  */
 int mls_project_sorted(const mls_grid *g, const int32_t *d_pos, int k, float h, int degree, int precision,
                        float *d_out_xyz, float *d_out_normal, uint8_t *d_status, mls_stream stream);
+
+/*
+ * mls_knn_project -- the neighbour search and the projection in one pass
+ * (Algorithm 1: each point's k nearest neighbours, then steps of Sec. 1.4,
+ * Eq. 1 on them), without writing the rows unless asked: every warp of the
+ * kNN keeps the rows of its last 32 queries in an on-chip-sized buffer and
+ * projects those points when 32 are done.  Results equal those of
+ * mls_knn_sorted followed by mls_project_sorted with the same k, h, degree
+ * and precision (same rows, same per-point arithmetic; the mixed form
+ * finishes its FP64 points in place instead of in a second pass).
+ *   g         grid built on the cloud (mls_build_grid), not rebuilt since
+ *   k         1 <= k <= min(MLS_MAX_K_FUSED, n), else MLS_ERR_K_TOO_LARGE
+ *   h         Gaussian bandwidth of Eq. 1, finite and > 0 (it is not derived
+ *             from the rows here: pass the value the cloud is filtered with)
+ *   degree    0, 1 or 2; precision MLS_PREC_FP32 or MLS_PREC_MIXED
+ *   d_out_xyz device, n x 3 floats, written in the original order (must not
+ *             be the grid's points)
+ *   d_out_normal, d_status  device, n x 3 floats / n bytes, or NULL
+ *   d_pos     device, n x k int32 or NULL: also the rows of sorted positions
+ *             of mls_knn_sorted
+ * Scratch: 128 k bytes per resident warp of the kNN (about 20 MB at k = 32).
+ */
+int mls_knn_project(const mls_grid *g, int k, float h, int degree, int precision, float *d_out_xyz,
+                    float *d_out_normal, uint8_t *d_status, int32_t *d_pos, mls_stream stream);
 
 /* Number of queries the last mls_knn call on this grid handed to its second
  * pass (queries whose first key bound needs a cube above the base level:

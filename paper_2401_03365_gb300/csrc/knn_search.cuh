@@ -105,16 +105,13 @@ struct Cube {
     int *st = nullptr, *ct = nullptr;    // this lane's slots: st[r * 32], ct[r * 32]
 };
 
-// Looks the 125 cells up with the four probes of a lane in flight together.
-__device__ void load_cube(const GridView &g, int lev, const uint32_t c0[3], Cube &cb, int lane) {
-    const int cx = (int)(c0[0] >> lev), cy = (int)(c0[1] >> lev), cz = (int)(c0[2] >> lev);
-    if (cb.lev == lev && cb.cx == cx && cb.cy == cy && cb.cz == cz) return;
-    cb.lev = lev;
-    cb.cx = cx;
-    cb.cy = cy;
-    cb.cz = cz;
-    const LevelTable &t = g.level[lev];
-    const int dims = (int)(kAxisCells >> lev);
+// Looks the 125 cells of the cube around (cx, cy, cz) up in table t (dims
+// cells per axis) with the four probes of a lane in flight together, writes
+// this lane's slots st[r * 32], ct[r * 32] and returns the cube's point
+// count.  Out of line: it runs only when a query's cube differs from the
+// previous one, and one body keeps the search kernels' code small.
+__device__ __noinline__ int fetch_cube(const LevelTable t, int dims, int cx, int cy, int cz, int *st_out,
+                                       int *ct_out, int lane) {
     uint64_t key[kSlots];
     uint32_t h[kSlots];
     bool live[kSlots];
@@ -154,11 +151,23 @@ __device__ void load_cube(const GridView &g, int lev, const uint32_t c0[3], Cube
             st = __ldg(t.cell_start + id[r]);
             ct = __ldg(t.cell_start + id[r] + 1) - st;
         }
-        cb.st[r * 32] = st;
-        cb.ct[r * 32] = ct;
+        st_out[r * 32] = st;
+        ct_out[r * 32] = ct;
         tot += ct;
     }
-    cb.M = warp_sum(tot);
+    return warp_sum(tot);
+}
+
+// The cube of level lev around the query's level-0 cell c0, unless it is the
+// one already cached.
+__device__ __forceinline__ void load_cube(const GridView &g, int lev, const uint32_t c0[3], Cube &cb, int lane) {
+    const int cx = (int)(c0[0] >> lev), cy = (int)(c0[1] >> lev), cz = (int)(c0[2] >> lev);
+    if (cb.lev == lev && cb.cx == cx && cb.cy == cy && cb.cz == cz) return;
+    cb.lev = lev;
+    cb.cx = cx;
+    cb.cy = cy;
+    cb.cz = cz;
+    cb.M = fetch_cube(g.level[lev], (int)(kAxisCells >> lev), cx, cy, cz, cb.st, cb.ct, lane);
 }
 
 // Squared distance from q to the box of this lane's cube cell in slot r.
@@ -506,11 +515,11 @@ struct TopK {
 };
 
 template <int KPL, class Out>
-__device__ float insertion_fallback(const GridView &g, const Cube &cb, WarpBuf &wb, float4 q, float lim2, float tau,
-                                    int k, int lane, int32_t qi, int64_t sp, const Out &out) {
+__device__ float insertion_fallback(const CellGeom geo, const Cube &cb, WarpBuf &wb, float4 q, float lim2,
+                                    float tau, int k, int lane, int32_t qi, int64_t sp, const Out &out) {
     TopK<KPL> top;
     top.init();
-    for_each_point<1>(cell_geom(g, cb), cb, wb, q, lim2, lane, [&](float4 p, bool valid, int pos) {
+    for_each_point<1>(geo, cb, wb, q, lim2, lane, [&](float4 p, bool valid, int pos) {
         const float key = rank_key(p, q.x, q.y, q.z);
         top.offer(valid && key <= tau ? pack(key, p) : ~0ull, pos, k, lane);
     });
@@ -661,7 +670,7 @@ __device__ __forceinline__ float solve_query(const GridView &g, WarpBuf &wb, Cub
             full_hist = false;
             continue;
         }
-        if (iter >= 8) return insertion_fallback<KPL>(g, cb, wb, q, lim2, tau, k, lane, qi, sp, out);
+        if (iter >= 8) return insertion_fallback<KPL>(cell_geom(g, cb), cb, wb, q, lim2, tau, k, lane, qi, sp, out);
         if (full_hist) {        // buckets over every kept word: each round cuts ~32x
             tau = tighten(wb, k, lane, tau, &bstar);
             // the buckets before the k-th key's hold fewer than k keys

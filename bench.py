@@ -47,17 +47,26 @@ K = 32
 # (height-fit reverse 106, covariance 43, centroid 17, weights 18, gather 6)
 # and per point 307 (the solve for z 150, the eigenvector derivative 116,
 # ofs and the rest 41).
+# The timed step saves the forward's fit state for the adjoint: the
+# projection then also solves for A^-1 e_0 (two 6x6 triangular solves, 72),
+# and the adjoint's own work is the 190 per neighbour and, per point, the 307
+# with the z solve (150) replaced by z = a0-bar A^-1 e_0 (6): 163.
 FLOPS_PER_NEIGHBOUR = 97
 FLOPS_PER_POINT = 645
+STATE_FLOPS_PER_POINT = 72
 BWD_FLOPS_PER_NEIGHBOUR = 97 + 190
 BWD_FLOPS_PER_POINT = 645 + 307
+BWD_STATE_FLOPS_PER_NEIGHBOUR = 190
+BWD_STATE_FLOPS_PER_POINT = 307 - 150 + 6
 
 
-def proj_flops(k):
-    return FLOPS_PER_NEIGHBOUR * k + FLOPS_PER_POINT
+def proj_flops(k, state=False):
+    return FLOPS_PER_NEIGHBOUR * k + FLOPS_PER_POINT + (STATE_FLOPS_PER_POINT if state else 0)
 
 
-def bwd_flops(k):
+def bwd_flops(k, state=False):
+    if state:
+        return BWD_STATE_FLOPS_PER_NEIGHBOUR * k + BWD_STATE_FLOPS_PER_POINT
     return BWD_FLOPS_PER_NEIGHBOUR * k + BWD_FLOPS_PER_POINT
 
 
@@ -250,6 +259,7 @@ def run_ours(args):
     out_st = torch.empty(n_pts, dtype=torch.uint8, device=dev)
     grad = torch.empty_like(x)
     grad_h = torch.empty(1, dtype=torch.float32, device=dev)
+    fit_state = torch.empty((capi.FIT_STATE_FLOATS, n_pts), dtype=torch.float32, device=dev)
     gen = torch.Generator(device=dev).manual_seed(cot_seed)
     gp = torch.randn((n_pts, 3), generator=gen, device=dev)          # cotangent of the points
     gn = 0.1 * torch.randn((n_pts, 3), generator=gen, device=dev)    # cotangent of the normals
@@ -270,11 +280,13 @@ def run_ours(args):
         capi.mls_knn_sorted(grid, K, out_pos=pos)
         if ev: ev[2].record(stream)
         if before_forward_out: before_forward_out()
-        capi.mls_project_sorted(grid, pos, h, 2, "mixed", out_xyz=out_xyz, out_normal=out_n, out_status=out_st)
+        capi.mls_project_sorted(grid, pos, h, 2, "mixed", out_xyz=out_xyz, out_normal=out_n, out_status=out_st,
+                                with_state=True, out_state=fit_state)
         if ev: ev[3].record(stream)
         if after_forward: after_forward()
         if before_backward: before_backward()
-        capi.mls_project_backward_sorted(grid, pos, h, gp, gn, 2, "mixed", out_grad_xyz=grad, out_grad_h=grad_h)
+        capi.mls_project_backward_sorted(grid, pos, h, gp, gn, 2, "mixed", out_grad_xyz=grad, out_grad_h=grad_h,
+                                         state=fit_state)
         if ev: ev[4].record(stream)
 
     events = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(args.steps)]
@@ -514,8 +526,8 @@ def run_ours(args):
 def stage_kernels(n, k, build_ms, knn_ms, proj_ms, bwd_ms, peaks, mhz):
     """Per-stage times and roofline fractions of one step over n points."""
     knn_gbs = n * knn_bytes(k) / (knn_ms * 1e-3) / 1e9
-    proj_tf = n * proj_flops(k) / (proj_ms * 1e-3) / 1e12
-    bwd_tf = n * bwd_flops(k) / (bwd_ms * 1e-3) / 1e12
+    proj_tf = n * proj_flops(k, state=True) / (proj_ms * 1e-3) / 1e12
+    bwd_tf = n * bwd_flops(k, state=True) / (bwd_ms * 1e-3) / 1e12
     inst = knn_measured("warp_inst_per_query", n) if k == K else None
     issue_peak = peaks["issue_ginst_per_mhz"] * mhz          # G warp instructions / s
     issue = {"bound": "issue", "unit": "G warp-inst/s", "peak": issue_peak,
@@ -535,11 +547,11 @@ def stage_kernels(n, k, build_ms, knn_ms, proj_ms, bwd_ms, peaks, mhz):
                                  "peak_source": f"{peaks['source']} hbm_gbs (copy)",
                                  "algorithmic_bytes_per_point": knn_bytes(k)},
                 "roofline_issue": issue},
-        "project": {"ms": proj_ms, "calls": "mls_project_sorted (k_project + k_project_deferred)", "bound": "alu",
-                    "flops_per_point": proj_flops(k), "achieved_tflops": proj_tf,
+        "project": {"ms": proj_ms, "calls": "mls_project_sorted (k_project + k_project_deferred), fit state saved", "bound": "alu",
+                    "flops_per_point": proj_flops(k, state=True), "achieved_tflops": proj_tf,
                     "frac": proj_tf / peaks["fp32_tflops"]},
-        "backward": {"ms": bwd_ms, "calls": "mls_project_backward_sorted (counts, scan, adjoint, bucket sums)",
-                     "bound": "alu", "flops_per_point": bwd_flops(k), "achieved_tflops": bwd_tf,
+        "backward": {"ms": bwd_ms, "calls": "mls_project_backward_sorted from the saved fit state (counts, scan, adjoint, bucket sums)",
+                     "bound": "alu", "flops_per_point": bwd_flops(k, state=True), "achieved_tflops": bwd_tf,
                      "frac": bwd_tf / peaks["fp32_tflops"]},
         "fp32_peak_tflops": peaks["fp32_tflops"],
         "fp32_peak_source": f"derived: {peaks['sms']} SM (from the device) x 128 FP32 lanes x 2 flops x max SM clock",

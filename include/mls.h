@@ -84,6 +84,11 @@ enum mls_point_status {
 
 #define MLS_MAX_K 64
 #define MLS_MAX_K_FUSED 32   /* largest k of mls_knn_project */
+/* Floats per point of the fit state mls_project_sorted can save for
+ * mls_project_backward_sorted (component c of sorted position s at
+ * d_state[c * n + s]): W, m (3), n (3), e1 (3), e2 (3), eigenvalues (3),
+ * a (6), A^-1 e_0 (6), status bits (1). */
+#define MLS_FIT_STATE_FLOATS 29
 
 /*
  * mls_build_grid -- spatial index for the neighbour search that precedes each
@@ -167,9 +172,14 @@ int mls_knn_sorted(const mls_grid *g, int k, int32_t *d_pos, int32_t *d_idx, flo
  * (MLS_ERR_INVALID_ARG for MLS_PREC_FP64: use mls_project).  The grid's
  * points must still be the cloud it was built on.  Scratch: in the mixed form
  * the list of the points that need an FP64 step (4 n bytes).
+ *   d_state  device, MLS_FIT_STATE_FLOATS x n floats, or NULL: the fit state
+ *            of every point by sorted position (the frame, the fit and the
+ *            status the adjoint would otherwise recompute), for
+ *            mls_project_backward_sorted; the other outputs are unchanged.
  */
 int mls_project_sorted(const mls_grid *g, const int32_t *d_pos, int k, float h, int degree, int precision,
-                       float *d_out_xyz, float *d_out_normal, uint8_t *d_status, mls_stream stream);
+                       float *d_out_xyz, float *d_out_normal, uint8_t *d_status, float *d_state,
+                       mls_stream stream);
 
 /*
  * mls_knn_project -- the neighbour search and the projection in one pass
@@ -341,10 +351,17 @@ int mls_project_backward(const float *d_xyz, int64_t n, const int32_t *d_idx, in
  * d_grad_out_normal and d_grad_xyz in the original order, as there.
  * precision MLS_PREC_FP32 or MLS_PREC_MIXED.  Scratch: about n (32 + 16 k)
  * bytes.
+ *   d_state  device, MLS_FIT_STATE_FLOATS x n floats, or NULL: the fit state
+ *            mls_project_sorted saved with the same rows, h, degree and
+ *            precision.  Given, the adjoint reads each point's frame, fit and
+ *            status from it instead of recomputing them (two of its four
+ *            passes over the neighbours and the solves): the gradients then
+ *            differ from the recomputing form only by rounding (the saved
+ *            coefficients carry the forward's refinement step).
  */
 int mls_project_backward_sorted(const mls_grid *g, const int32_t *d_pos, int k, float h, int degree, int precision,
                                 const float *d_grad_out_xyz, const float *d_grad_out_normal, float *d_grad_xyz,
-                                float *d_grad_h, mls_stream stream);
+                                float *d_grad_h, const float *d_state, mls_stream stream);
 
 /*
  * mls_mean_knn_dist -- bandwidth helper (not in the paper): the mean distance,

@@ -21,11 +21,12 @@ __all__ = [
     "mls_project_rows", "mls_compact", "mls_mean_knn_dist", "mls_status_str", "mls_last_error", "mls_kernel_launches", "mls_release_scratch",
     "Batch", "mls_batch_create", "mls_batch_destroy", "mls_batch_set_shape", "mls_batch_get_shape",
     "mls_project_batched", "mls_batch_capture", "mls_batch_replay", "mls_batch_autotune", "mls_batch_tune_results",
-    "PRECISION", "MLS_MAX_K", "MLS_PT_OK", "MLS_PT_PLANE_DEGENERATE", "MLS_PT_POLY_SINGULAR",
+    "PRECISION", "MLS_MAX_K", "FIT_STATE_FLOATS", "MLS_PT_OK", "MLS_PT_PLANE_DEGENERATE", "MLS_PT_POLY_SINGULAR",
     "MLS_PT_FP64_USED", "EXPORTED_SYMBOLS",
 ]
 
 MLS_MAX_K = 64
+FIT_STATE_FLOATS = 29       # MLS_FIT_STATE_FLOATS: floats of fit state per point
 MLS_NOALLOC_MAX_POINTS = 262144
 PRECISION = {"fp32": 0, "mixed": 1, "fp64": 2}
 MLS_PT_OK, MLS_PT_PLANE_DEGENERATE, MLS_PT_POLY_SINGULAR, MLS_PT_FP64_USED = 0, 1, 2, 4
@@ -48,9 +49,10 @@ _SIGNATURES = [
     ("mls_knn_deferred", ctypes.c_int64, [_vp, _vp]),
     ("mls_points_in_boxes", _int, [_vp, _vp, _i64, _vp, _vp]),
     ("mls_knn_sorted", _int, [_vp, _int, _vp, _vp, _vp, _vp]),
-    ("mls_project_sorted", _int, [_vp, _vp, _int, ctypes.c_float, _int, _int, _vp, _vp, _vp, _vp]),
+    ("mls_project_sorted", _int, [_vp, _vp, _int, ctypes.c_float, _int, _int, _vp, _vp, _vp, _vp, _vp]),
     ("mls_knn_project", _int, [_vp, _int, ctypes.c_float, _int, _int, _vp, _vp, _vp, _vp, _vp]),
-    ("mls_project_backward_sorted", _int, [_vp, _vp, _int, ctypes.c_float, _int, _int, _vp, _vp, _vp, _vp, _vp]),
+    ("mls_project_backward_sorted", _int, [_vp, _vp, _int, ctypes.c_float, _int, _int, _vp, _vp, _vp, _vp, _vp,
+                                           _vp]),
     ("mls_project", _int, [_vp, _i64, _vp, _int, _flt, _int, _int, _vp, _vp, _vp, _vp, _vp]),
     ("mls_project_noalloc", _int, [_vp, _i64, _vp, _int, _flt, _int, _int, _vp, _vp, _vp, _vp, _vp]),
     ("mls_project_levin", _int, [_vp, _i64, _vp, _int, _flt, _int, _int, _int, _flt, _vp, _vp, _vp, _vp, _vp]),
@@ -253,9 +255,12 @@ def mls_knn_sorted(grid: Grid, k: int, with_idx: bool = False, with_key: bool = 
 
 
 def mls_project_sorted(grid: Grid, pos: torch.Tensor, h: float, degree: int = 2, precision: str = "mixed",
-                       out_xyz=None, out_normal=None, out_status=None, stream=None):
+                       out_xyz=None, out_normal=None, out_status=None, stream=None, with_state: bool = False,
+                       out_state=None):
     """mls_project over the grid's sorted points and mls_knn_sorted's rows;
-    outputs in the original order."""
+    outputs in the original order.  With `with_state` also the fit state
+    (FIT_STATE_FLOATS, n) by sorted position, for mls_project_backward_sorted:
+    (xyz, normal, status[, state])."""
     n = grid.n
     _need(pos, "pos", torch.int32)
     if pos.dim() != 2 or pos.shape[0] != n:
@@ -267,10 +272,15 @@ def mls_project_sorted(grid: Grid, pos: torch.Tensor, h: float, degree: int = 2,
     _need(out_xyz, "out_xyz", torch.float32, (n, 3))
     _need(out_normal, "out_normal", torch.float32, (n, 3))
     _need(out_status, "out_status", torch.uint8, (n,))
+    if with_state:
+        out_state = torch.empty((FIT_STATE_FLOATS, n), dtype=torch.float32, device=dev) if out_state is None \
+            else out_state
+        _need(out_state, "out_state", torch.float32, (FIT_STATE_FLOATS, n))
     rc = lib().mls_project_sorted(grid.handle, _ptr(pos), pos.shape[1], float(h), int(degree), PRECISION[precision],
-                                  _ptr(out_xyz), _ptr(out_normal), _ptr(out_status), _stream(stream))
+                                  _ptr(out_xyz), _ptr(out_normal), _ptr(out_status),
+                                  _ptr(out_state) if with_state else None, _stream(stream))
     _check("mls_project_sorted", rc)
-    return out_xyz, out_normal, out_status
+    return (out_xyz, out_normal, out_status, out_state) if with_state else (out_xyz, out_normal, out_status)
 
 
 def mls_knn_project(grid: Grid, k: int, h: float, degree: int = 2, precision: str = "mixed", with_pos: bool = False,
@@ -298,9 +308,10 @@ def mls_knn_project(grid: Grid, k: int, h: float, degree: int = 2, precision: st
 
 def mls_project_backward_sorted(grid: Grid, pos: torch.Tensor, h: float, gout_xyz: torch.Tensor,
                                 gout_normal: torch.Tensor | None = None, degree: int = 2, precision: str = "mixed",
-                                out_grad_xyz=None, out_grad_h=None, stream=None):
+                                out_grad_xyz=None, out_grad_h=None, stream=None, state: torch.Tensor | None = None):
     """mls_project_backward over the grid's sorted points and mls_knn_sorted's
-    rows: (dL/dxyz (n, 3), dL/dh (1,)) in the original order."""
+    rows: (dL/dxyz (n, 3), dL/dh (1,)) in the original order.  `state`: the
+    fit state mls_project_sorted saved (then not recomputed)."""
     n = grid.n
     _need(pos, "pos", torch.int32)
     if pos.dim() != 2 or pos.shape[0] != n:
@@ -308,6 +319,8 @@ def mls_project_backward_sorted(grid: Grid, pos: torch.Tensor, h: float, gout_xy
     _need(gout_xyz, "gout_xyz", torch.float32, (n, 3))
     if gout_normal is not None:
         _need(gout_normal, "gout_normal", torch.float32, (n, 3))
+    if state is not None:
+        _need(state, "state", torch.float32, (FIT_STATE_FLOATS, n))
     dev = grid.xyz.device
     out_grad_xyz = torch.empty((n, 3), dtype=torch.float32, device=dev) if out_grad_xyz is None else out_grad_xyz
     out_grad_h = torch.empty(1, dtype=torch.float32, device=dev) if out_grad_h is None else out_grad_h
@@ -315,7 +328,7 @@ def mls_project_backward_sorted(grid: Grid, pos: torch.Tensor, h: float, gout_xy
     _need(out_grad_h, "out_grad_h", torch.float32, (1,))
     rc = lib().mls_project_backward_sorted(grid.handle, _ptr(pos), pos.shape[1], float(h), int(degree),
                                            PRECISION[precision], _ptr(gout_xyz), _ptr(gout_normal),
-                                           _ptr(out_grad_xyz), _ptr(out_grad_h), _stream(stream))
+                                           _ptr(out_grad_xyz), _ptr(out_grad_h), _ptr(state), _stream(stream))
     _check("mls_project_backward_sorted", rc)
     return out_grad_xyz, out_grad_h
 

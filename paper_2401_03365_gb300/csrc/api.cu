@@ -13,13 +13,14 @@ int build_grid(mls_grid *g, const float *xyz, int64_t n, float cell_size, int k_
 void free_grid_buffers(mls_grid *g);
 int launch_knn(const mls_grid *grid, int k, int32_t *idx, float *key, int32_t *pos, cudaStream_t st);
 int launch_project_sorted(const float4 *pts, int64_t n, const int32_t *pos, int k, float h, int degree,
-                          int precision, float *out_xyz, float *out_n, uint8_t *status, cudaStream_t st);
+                          int precision, float *out_xyz, float *out_n, uint8_t *status, float *state,
+                          cudaStream_t st);
 int launch_knn_project(const mls_grid *grid, int k, float h, int degree, int precision, float *out_xyz,
                        float *out_n, uint8_t *status, int32_t *pos, cudaStream_t st);
 int launch_points_in_boxes(const mls_grid *grid, const float *boxes, int64_t m, uint8_t *mask, cudaStream_t st);
 int launch_backward_sorted(const float4 *pts, const int32_t *order, int64_t n, const int32_t *rows, int k, float h,
                            int degree, int precision, const float *gp, const float *gn, float *grad_xyz,
-                           float *grad_h, cudaStream_t st);
+                           float *grad_h, const float *state, cudaStream_t st);
 int launch_project(const float *xyz, int64_t n, const int32_t *idx, int k, float h, int degree, int precision,
                    const int32_t *order, float *out_xyz, float *out_n, uint8_t *status, cudaStream_t st);
 int launch_radius(const mls_grid *grid, float R2, int32_t *count, const int64_t *offsets, int32_t *rows,
@@ -215,7 +216,8 @@ int mls_knn_sorted(const mls_grid *g, int k, int32_t *d_pos, int32_t *d_idx, flo
 }
 
 int mls_project_sorted(const mls_grid *g, const int32_t *d_pos, int k, float h, int degree, int precision,
-                       float *d_out_xyz, float *d_out_normal, uint8_t *d_status, mls_stream stream) {
+                       float *d_out_xyz, float *d_out_normal, uint8_t *d_status, float *d_state,
+                       mls_stream stream) {
     mls::g_last_error[0] = 0;
     if (!g || !d_pos || !d_out_xyz) return set_error(MLS_ERR_INVALID_ARG, "mls_project_sorted: null pointer");
     if (g->n < 1) return set_error(MLS_ERR_INVALID_ARG, "mls_project_sorted: grid is empty (failed build?)");
@@ -230,7 +232,7 @@ int mls_project_sorted(const mls_grid *g, const int32_t *d_pos, int k, float h, 
     if ((const void *)d_out_xyz == (const void *)g->xyz)
         return set_error(MLS_ERR_INVALID_ARG, "mls_project_sorted: output aliases the grid's points");
     return mls::launch_project_sorted(g->view.pts, g->n, d_pos, k, h, degree, precision, d_out_xyz, d_out_normal,
-                                      d_status, (cudaStream_t)stream);
+                                      d_status, d_state, (cudaStream_t)stream);
 }
 
 int mls_knn_project(const mls_grid *g, int k, float h, int degree, int precision, float *d_out_xyz,
@@ -405,7 +407,7 @@ int mls_project_backward(const float *d_xyz, int64_t n, const int32_t *d_idx, in
 
 int mls_project_backward_sorted(const mls_grid *g, const int32_t *d_pos, int k, float h, int degree, int precision,
                                 const float *d_grad_out_xyz, const float *d_grad_out_normal, float *d_grad_xyz,
-                                float *d_grad_h, mls_stream stream) {
+                                float *d_grad_h, const float *d_state, mls_stream stream) {
     mls::g_last_error[0] = 0;
     if (!g || !d_pos || !d_grad_out_xyz || !d_grad_xyz || !d_grad_h)
         return set_error(MLS_ERR_INVALID_ARG, "mls_project_backward_sorted: null pointer");
@@ -425,7 +427,7 @@ int mls_project_backward_sorted(const mls_grid *g, const int32_t *d_pos, int k, 
     if ((const void *)d_grad_xyz == (const void *)g->xyz || (const void *)d_grad_xyz == (const void *)d_grad_out_xyz)
         return set_error(MLS_ERR_INVALID_ARG, "mls_project_backward_sorted: output aliases an input");
     return mls::launch_backward_sorted(g->view.pts, g->perm, g->n, d_pos, k, h, degree, precision, d_grad_out_xyz,
-                                       d_grad_out_normal, d_grad_xyz, d_grad_h, (cudaStream_t)stream);
+                                       d_grad_out_normal, d_grad_xyz, d_grad_h, d_state, (cudaStream_t)stream);
 }
 
 int mls_points_in_boxes(const mls_grid *g, const float *d_boxes, int64_t m, uint8_t *d_mask, mls_stream stream) {

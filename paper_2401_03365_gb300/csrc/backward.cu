@@ -28,7 +28,7 @@
 #include <climits>
 
 #include "fixed_point.cuh"
-#include "solve.cuh"
+#include "project_point.cuh"
 
 namespace mls {
 
@@ -86,12 +86,18 @@ __device__ __forceinline__ void basis(float u, float v, float phi[6]) {
 // With SORTED, xyz4 is the grid's sorted copy of the points, slot s is sorted
 // position s, idx holds rows of sorted positions by sorted position (no
 // translation), and order[s] is the point's original index.
-template <int DEG, int PREC, bool SORTED = false>
+// With STATE (SORTED only), the frame, eigenvalues, centroid offset, weight
+// sum, fit coefficients, A^-1 e_0 and status of sorted position s come from
+// state[c * n + s] (FitState, saved by the forward): the recompute passes and
+// solves are skipped, and z = a0-bar A^-1 e_0.
+template <int DEG, int PREC, bool SORTED = false, bool STATE = false>
 __global__ void __launch_bounds__(kBwdThreads, 6) k_backward_point(
     const float4 *__restrict__ xyz4, int64_t n, const int32_t *__restrict__ idx, int k, float h,
     const int32_t *__restrict__ order, const int32_t *__restrict__ pos, const float *__restrict__ gout_xyz,
     const float *__restrict__ gout_n, const int32_t *__restrict__ off, int32_t *__restrict__ fill,
-    float4 *__restrict__ rec, float4 *__restrict__ self4, double *__restrict__ h_part) {
+    float4 *__restrict__ rec, float4 *__restrict__ self4, double *__restrict__ h_part,
+    const float *__restrict__ state = nullptr) {
+    static_assert(!STATE || SORTED, "the fit state is indexed by sorted position");
     constexpr int M = Basis<DEG>::M;
     extern __shared__ int32_t rows[];
     __shared__ double hred[kBwdThreads / 32];
@@ -119,8 +125,23 @@ __global__ void __launch_bounds__(kBwdThreads, 6) k_backward_point(
         const float rx = r4.x, ry = r4.y, rz = r4.z;
         const float h2 = h * h, ih = 1.f / h;
         const float neg_scale = -1.4426950408889634f / h2;
-        // ---- forward recompute: weights, centroid offset, covariance ----
         float W = 0.f, m[3] = {0.f, 0.f, 0.f};
+        float nv[3], e1[3], e2[3], lam[3];
+        int flag = 0;
+        if constexpr (STATE) {
+            const float *sv = state + slot;
+            W = __ldg(sv + kStW * n);
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                m[a] = __ldg(sv + (kStM + a) * n);
+                nv[a] = __ldg(sv + (kStN + a) * n);
+                e1[a] = __ldg(sv + (kStE1 + a) * n);
+                e2[a] = __ldg(sv + (kStE2 + a) * n);
+                lam[a] = __ldg(sv + (kStLam + a) * n);
+            }
+            flag = __float_as_int(__ldg(sv + kStStatus * n));
+        } else {
+        // ---- forward recompute: weights, centroid offset, covariance ----
         float C[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         for (int j = 0; j < k; ++j) {
             const float4 p = __ldg(xyz4 + my_rows[j * kRowStride + lane]);
@@ -142,8 +163,7 @@ __global__ void __launch_bounds__(kBwdThreads, 6) k_backward_point(
             C[5] = fmaf(f * e[2], e[2], C[5]);
             W = Wn;
         }
-        float nv[3], e1[3], e2[3], lam[3];
-        int flag = frame_from<float>(C, nv, e1, e2, lam);
+        flag = frame_from<float>(C, nv, e1, e2, lam);
         if (PREC == MLS_PREC_MIXED && (!(lam[2] > 0.f) || (lam[1] - lam[0]) < kBwdGapFlag * lam[2])) {
             double Cd[6], nd[3], e1d[3], e2d[3], ld[3];
 #pragma unroll
@@ -156,6 +176,7 @@ __global__ void __launch_bounds__(kBwdThreads, 6) k_backward_point(
                 e2[a] = (float)e2d[a];
                 lam[a] = (float)ld[a];
             }
+        }
         }
         const float gp[3] = {gout_xyz[3 * i], gout_xyz[3 * i + 1], gout_xyz[3 * i + 2]};
         float rbar[3] = {gp[0], gp[1], gp[2]};
@@ -171,6 +192,18 @@ __global__ void __launch_bounds__(kBwdThreads, 6) k_backward_point(
             const float gn[3] = {gout_n ? gout_n[3 * i] : 0.f, gout_n ? gout_n[3 * i + 1] : 0.f,
                                  gout_n ? gout_n[3 * i + 2] : 0.f};
             const float ofs = nv[0] * m[0] + nv[1] * m[1] + nv[2] * m[2];
+            const float s0bar = gp[0] * nv[0] + gp[1] * nv[1] + gp[2] * nv[2];
+            float a[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, z[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            bool ok;
+            if constexpr (STATE) {
+                ok = !(flag & MLS_PT_POLY_SINGULAR);
+                const float *sv = state + slot;
+#pragma unroll
+                for (int c = 0; c < M; ++c) {
+                    a[c] = __ldg(sv + (kStA + c) * n);
+                    z[c] = s0bar * __ldg(sv + (kStC0 + c) * n);
+                }
+            } else {
             // ---- height-fit moments and the two solves ----
             float mom[15], rhs[6];
 #pragma unroll
@@ -197,9 +230,6 @@ __global__ void __launch_bounds__(kBwdThreads, 6) k_backward_point(
 #pragma unroll
                 for (int c = 0; c < M; ++c) rhs[c] = fmaf(w * f, phi[c], rhs[c]);
             }
-            const float s0bar = gp[0] * nv[0] + gp[1] * nv[1] + gp[2] * nv[2];
-            float a[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, z[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-            bool ok;
             {
                 float A[M][M], b[M], cond = 0.f;
                 assemble<float, DEG>(mom, A);
@@ -226,6 +256,7 @@ __global__ void __launch_bounds__(kBwdThreads, 6) k_backward_point(
                         z[c] = zf[c];
                     }
                 }
+            }
             }
             // ---- reverse: projection, polynomial (global part) ----
             const float s = ofs + a[0];
@@ -542,15 +573,17 @@ __global__ void __launch_bounds__(1024) k_sum_h(const double *__restrict__ part,
     if (threadIdx.x == 0) *out = (float)red[0];
 }
 
-template <int DEG, bool SORTED = false>
+template <int DEG, bool SORTED = false, bool STATE = false>
 void launch_point(const float4 *xyz4, int64_t n, const int32_t *idx, int k, float h, int precision,
                   const int32_t *order, const int32_t *pos, const float *gp, const float *gn, const int32_t *off,
-                  int32_t *fill, float4 *rec, float4 *self4, double *hp, int blocks, cudaStream_t st) {
+                  int32_t *fill, float4 *rec, float4 *self4, double *hp, int blocks, cudaStream_t st,
+                  const float *state = nullptr) {
     const size_t smem = (size_t)k * kRowStride * sizeof(int32_t) * (kBwdThreads / 32);
-    auto kern = precision == MLS_PREC_FP32 ? k_backward_point<DEG, MLS_PREC_FP32, SORTED>
-                                           : k_backward_point<DEG, MLS_PREC_MIXED, SORTED>;
+    auto kern = precision == MLS_PREC_FP32 ? k_backward_point<DEG, MLS_PREC_FP32, SORTED, STATE>
+                                           : k_backward_point<DEG, MLS_PREC_MIXED, SORTED, STATE>;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    kern<<<blocks, kBwdThreads, smem, st>>>(xyz4, n, idx, k, h, order, pos, gp, gn, off, fill, rec, self4, hp);
+    kern<<<blocks, kBwdThreads, smem, st>>>(xyz4, n, idx, k, h, order, pos, gp, gn, off, fill, rec, self4, hp,
+                                            state);
 }
 
 }  // namespace
@@ -603,7 +636,7 @@ int launch_backward(const float *xyz, int64_t n, const int32_t *idx, int k, floa
 
 int launch_backward_sorted(const float4 *pts, const int32_t *order, int64_t n, const int32_t *rows, int k, float h,
                            int degree, int precision, const float *gp, const float *gn, float *grad_xyz,
-                           float *grad_h, cudaStream_t st) {
+                           float *grad_h, const float *state, cudaStream_t st) {
     const int64_t ne = n * (int64_t)k;
     const int blocks = (int)((n + kBwdThreads - 1) / kBwdThreads);
     float4 *rec = nullptr, *self4 = nullptr;
@@ -622,10 +655,18 @@ int launch_backward_sorted(const float4 *pts, const int32_t *order, int64_t n, c
                                                                                       cnt);
     int rc = device_exclusive_scan(cnt, off, n + 1, st);
     if (rc != MLS_OK) return rc;
-    switch (degree) {
-        case 0: launch_point<0, true>(pts, n, rows, k, h, precision, order, nullptr, gp, gn, off, fill, rec, self4, hp, blocks, st); break;
-        case 1: launch_point<1, true>(pts, n, rows, k, h, precision, order, nullptr, gp, gn, off, fill, rec, self4, hp, blocks, st); break;
-        default: launch_point<2, true>(pts, n, rows, k, h, precision, order, nullptr, gp, gn, off, fill, rec, self4, hp, blocks, st); break;
+    if (state) {
+        switch (degree) {
+            case 0: launch_point<0, true, true>(pts, n, rows, k, h, precision, order, nullptr, gp, gn, off, fill, rec, self4, hp, blocks, st, state); break;
+            case 1: launch_point<1, true, true>(pts, n, rows, k, h, precision, order, nullptr, gp, gn, off, fill, rec, self4, hp, blocks, st, state); break;
+            default: launch_point<2, true, true>(pts, n, rows, k, h, precision, order, nullptr, gp, gn, off, fill, rec, self4, hp, blocks, st, state); break;
+        }
+    } else {
+        switch (degree) {
+            case 0: launch_point<0, true>(pts, n, rows, k, h, precision, order, nullptr, gp, gn, off, fill, rec, self4, hp, blocks, st); break;
+            case 1: launch_point<1, true>(pts, n, rows, k, h, precision, order, nullptr, gp, gn, off, fill, rec, self4, hp, blocks, st); break;
+            default: launch_point<2, true>(pts, n, rows, k, h, precision, order, nullptr, gp, gn, off, fill, rec, self4, hp, blocks, st); break;
+        }
     }
     k_bucket_sum<kSumLanes, kSumCached><<<(int)std::min<int64_t>((n * kSumLanes + 255) / 256, (int64_t)sms * 32), 256, 0, st>>>(
         n, order, off, rec, self4, grad_xyz);

@@ -37,15 +37,17 @@ __global__ void k_pack_xyz4(const float *__restrict__ xyz, int64_t n, float4 *__
 // With SORTED, xyz4 is the grid's sorted copy of the points (w = the point's
 // original index bits), slot s is sorted position s, idx holds the rows of
 // sorted positions by sorted position, and each result goes to the point's
-// original index.
-template <int DEG, int PREC, bool LEVIN = false, bool DEFER = false, bool SORTED = false>
+// original index.  With STATE (SORTED only) each point's fit state goes to
+// state[c * n + slot] (FitState).
+template <int DEG, int PREC, bool LEVIN = false, bool DEFER = false, bool SORTED = false, bool STATE = false>
 __global__ void __launch_bounds__(kProjThreads, LEVIN ? 5 : 8) k_project(const float4 *__restrict__ xyz4, int64_t n,
                                                           const int32_t *__restrict__ idx, int k, float h,
                                                           const int32_t *__restrict__ order,
                                                           float *__restrict__ out_xyz, float *__restrict__ out_n,
                                                           uint8_t *__restrict__ status, int max_iter,
                                                           float tol, int32_t *__restrict__ deferred,
-                                                          int32_t *__restrict__ n_deferred) {
+                                                          int32_t *__restrict__ n_deferred,
+                                                          float *__restrict__ state = nullptr) {
     extern __shared__ int32_t rows[];
     const int lane = threadIdx.x & 31;
     int32_t *my_rows = rows + (threadIdx.x >> 5) * k * kRowStride;
@@ -63,8 +65,9 @@ __global__ void __launch_bounds__(kProjThreads, LEVIN ? 5 : 8) k_project(const f
     if (slot >= n) return;
     const float4 r4 = __ldg(xyz4 + i);
     float out[3], nf[3];
-    const uint8_t st = project_point<DEG, PREC, LEVIN, DEFER>(
-        xyz4, [&](int j) { return my_rows[j * kRowStride + lane]; }, k, 0, 1, h, r4.x, r4.y, r4.z, out, nf, max_iter, tol);
+    const uint8_t st = project_point<DEG, PREC, LEVIN, DEFER, STATE>(
+        xyz4, [&](int j) { return my_rows[j * kRowStride + lane]; }, k, 0, 1, h, r4.x, r4.y, r4.z, out, nf, max_iter, tol,
+        STATE ? state + slot : nullptr, n);
     if (DEFER && st == kDeferFP64) {
         deferred[atomicAdd(n_deferred, 1)] = (int32_t)slot;
         return;
@@ -83,9 +86,9 @@ __global__ void __launch_bounds__(kProjThreads, LEVIN ? 5 : 8) k_project(const f
 
 // The deferred points of the mixed form, one thread each: the same routine
 // with its FP64 steps, rows read from global memory (same values and order
-// as the first pass, so the results are those of a single pass).  SORTED as
-// in k_project.
-template <int DEG, bool SORTED = false>
+// as the first pass, so the results are those of a single pass).  SORTED and
+// STATE as in k_project.
+template <int DEG, bool SORTED = false, bool STATE = false>
 __global__ void __launch_bounds__(kProjThreads) k_project_deferred(const float4 *__restrict__ xyz4, int64_t n,
                                                                   const int32_t *__restrict__ idx, int k, float h,
                                                                   const int32_t *__restrict__ order,
@@ -93,7 +96,8 @@ __global__ void __launch_bounds__(kProjThreads) k_project_deferred(const float4 
                                                                   const int32_t *__restrict__ n_deferred,
                                                                   float *__restrict__ out_xyz,
                                                                   float *__restrict__ out_n,
-                                                                  uint8_t *__restrict__ status) {
+                                                                  uint8_t *__restrict__ status,
+                                                                  float *__restrict__ state = nullptr) {
     const int count = *n_deferred;
     for (int d = blockIdx.x * blockDim.x + threadIdx.x; d < count; d += gridDim.x * blockDim.x) {
         const int64_t slot = deferred[d];
@@ -101,8 +105,9 @@ __global__ void __launch_bounds__(kProjThreads) k_project_deferred(const float4 
         const int32_t *row = idx + i * k;
         const float4 r4 = __ldg(xyz4 + i);
         float out[3], nf[3];
-        const uint8_t st = project_point<DEG, MLS_PREC_MIXED>(
-            xyz4, [&](int j) { return __ldg(row + j); }, k, 0, 1, h, r4.x, r4.y, r4.z, out, nf);
+        const uint8_t st = project_point<DEG, MLS_PREC_MIXED, false, false, STATE>(
+            xyz4, [&](int j) { return __ldg(row + j); }, k, 0, 1, h, r4.x, r4.y, r4.z, out, nf, 1, 0.f,
+            STATE ? state + slot : nullptr, n);
         const int64_t o = SORTED ? (int64_t)__float_as_int(r4.w) : i;
         out_xyz[3 * o] = out[0];
         out_xyz[3 * o + 1] = out[1];
@@ -264,7 +269,7 @@ int launch_deg(const float *xyz, int64_t n, const int32_t *idx, int k, float h, 
             auto kern = k_project<DEG, MLS_PREC_MIXED, false, true>;
             MLS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
             kern<<<blocks, kProjThreads, smem, st>>>(xyz4, n, idx, k, h, order, out_xyz, out_n, status, 1, 0.f,
-                                                     deferred, n_deferred);
+                                                     deferred, n_deferred, nullptr);
             k_project_deferred<DEG><<<sm_count() * 2, kProjThreads, 0, st>>>(xyz4, n, idx, k, h, order, deferred, n_deferred,
                                                                      out_xyz, out_n, status);
             count_launches(3);
@@ -272,7 +277,7 @@ int launch_deg(const float *xyz, int64_t n, const int32_t *idx, int k, float h, 
             auto kern = k_project<DEG, MLS_PREC_FP32>;
             MLS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
             kern<<<blocks, kProjThreads, smem, st>>>(xyz4, n, idx, k, h, order, out_xyz, out_n, status, 1, 0.f,
-                                                     nullptr, nullptr);
+                                                     nullptr, nullptr, nullptr);
             count_launches(2);
         }
     }
@@ -299,9 +304,9 @@ namespace {
 // The projection over the grid's sorted points and rows of sorted positions.
 // (Two lanes per point, as the batched kernel's autotuner prefers, measured
 // slower here: 0.63 ms against 0.56 ms on the 2M-point torus.)
-template <int DEG>
+template <int DEG, bool STATE>
 int launch_sorted_deg(const float4 *pts, int64_t n, const int32_t *pos, int k, float h, int precision,
-                      float *out_xyz, float *out_n, uint8_t *status, cudaStream_t st) {
+                      float *out_xyz, float *out_n, uint8_t *status, float *state, cudaStream_t st) {
     const int blocks = (int)((n + kProjThreads - 1) / kProjThreads);
     const size_t smem = (size_t)k * kRowStride * sizeof(int32_t) * (kProjThreads / 32);
     if (precision == MLS_PREC_MIXED) {
@@ -310,18 +315,18 @@ int launch_sorted_deg(const float4 *pts, int64_t n, const int32_t *pos, int k, f
         MLS_CUDA_TRY(scratch.alloc(&deferred, (size_t)(n + 1) * sizeof(int32_t)));
         int32_t *n_deferred = deferred + n;
         MLS_CUDA_TRY(cudaMemsetAsync(n_deferred, 0, sizeof(int32_t), st));
-        auto kern = k_project<DEG, MLS_PREC_MIXED, false, true, true>;
+        auto kern = k_project<DEG, MLS_PREC_MIXED, false, true, true, STATE>;
         MLS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         kern<<<blocks, kProjThreads, smem, st>>>(pts, n, pos, k, h, nullptr, out_xyz, out_n, status, 1, 0.f,
-                                                 deferred, n_deferred);
-        k_project_deferred<DEG, true><<<sm_count() * 2, kProjThreads, 0, st>>>(pts, n, pos, k, h, nullptr, deferred,
-                                                                                n_deferred, out_xyz, out_n, status);
+                                                 deferred, n_deferred, state);
+        k_project_deferred<DEG, true, STATE><<<sm_count() * 2, kProjThreads, 0, st>>>(
+            pts, n, pos, k, h, nullptr, deferred, n_deferred, out_xyz, out_n, status, state);
         count_launches(2);
     } else {
-        auto kern = k_project<DEG, MLS_PREC_FP32, false, false, true>;
+        auto kern = k_project<DEG, MLS_PREC_FP32, false, false, true, STATE>;
         MLS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         kern<<<blocks, kProjThreads, smem, st>>>(pts, n, pos, k, h, nullptr, out_xyz, out_n, status, 1, 0.f,
-                                                 nullptr, nullptr);
+                                                 nullptr, nullptr, state);
         count_launches(1);
     }
     MLS_CUDA_TRY(cudaGetLastError());
@@ -331,11 +336,19 @@ int launch_sorted_deg(const float4 *pts, int64_t n, const int32_t *pos, int k, f
 }  // namespace
 
 int launch_project_sorted(const float4 *pts, int64_t n, const int32_t *pos, int k, float h, int degree,
-                          int precision, float *out_xyz, float *out_n, uint8_t *status, cudaStream_t st) {
+                          int precision, float *out_xyz, float *out_n, uint8_t *status, float *state,
+                          cudaStream_t st) {
+    if (state) {
+        switch (degree) {
+            case 0: return launch_sorted_deg<0, true>(pts, n, pos, k, h, precision, out_xyz, out_n, status, state, st);
+            case 1: return launch_sorted_deg<1, true>(pts, n, pos, k, h, precision, out_xyz, out_n, status, state, st);
+            default: return launch_sorted_deg<2, true>(pts, n, pos, k, h, precision, out_xyz, out_n, status, state, st);
+        }
+    }
     switch (degree) {
-        case 0: return launch_sorted_deg<0>(pts, n, pos, k, h, precision, out_xyz, out_n, status, st);
-        case 1: return launch_sorted_deg<1>(pts, n, pos, k, h, precision, out_xyz, out_n, status, st);
-        default: return launch_sorted_deg<2>(pts, n, pos, k, h, precision, out_xyz, out_n, status, st);
+        case 0: return launch_sorted_deg<0, false>(pts, n, pos, k, h, precision, out_xyz, out_n, status, nullptr, st);
+        case 1: return launch_sorted_deg<1, false>(pts, n, pos, k, h, precision, out_xyz, out_n, status, nullptr, st);
+        default: return launch_sorted_deg<2, false>(pts, n, pos, k, h, precision, out_xyz, out_n, status, nullptr, st);
     }
 }
 
@@ -384,12 +397,12 @@ int launch_levin_deg(const float *xyz, int64_t n, const int32_t *idx, int k, flo
         auto kern = k_project<DEG, MLS_PREC_MIXED, true>;
         MLS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         kern<<<blocks, kProjThreads, smem, st>>>(xyz4, n, idx, k, h, order, out_xyz, out_n, status, max_iter, tol,
-                                                 nullptr, nullptr);
+                                                 nullptr, nullptr, nullptr);
     } else {
         auto kern = k_project<DEG, MLS_PREC_FP32, true>;
         MLS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         kern<<<blocks, kProjThreads, smem, st>>>(xyz4, n, idx, k, h, order, out_xyz, out_n, status, max_iter, tol,
-                                                 nullptr, nullptr);
+                                                 nullptr, nullptr, nullptr);
     }
     count_launches(2);
     MLS_CUDA_TRY(cudaGetLastError());
@@ -461,12 +474,12 @@ int launch_noalloc(const float *xyz, int64_t n, const int32_t *idx, int k, float
             auto kern = k_project<DEG, MLS_PREC_MIXED>;
             MLS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
             kern<<<blocks, kProjThreads, smem, st>>>(xyz4, n, idx, k, h, order, out_xyz, out_n, status, 1, 0.f,
-                                                     nullptr, nullptr);
+                                                     nullptr, nullptr, nullptr);
         } else {
             auto kern = k_project<DEG, MLS_PREC_FP32>;
             MLS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
             kern<<<blocks, kProjThreads, smem, st>>>(xyz4, n, idx, k, h, order, out_xyz, out_n, status, 1, 0.f,
-                                                     nullptr, nullptr);
+                                                     nullptr, nullptr, nullptr);
         }
         count_launches(2);
     }

@@ -28,6 +28,18 @@ constexpr float kMixedCondFlag = 1e5f;     // FP32 Cholesky trusted below this c
 // step: nothing is computed for it, a later pass runs it without DEFER.
 constexpr uint8_t kDeferFP64 = 0x80;
 
+// The fit state a forward pass can save for the adjoint (MLS_FIT_STATE_FLOATS
+// floats per point, component c of a point at state[c * stride]): the weight
+// sum W, the weighted centroid offset m = c - r, the frame n, e1, e2 and the
+// covariance eigenvalues (ascending), the height-fit coefficients a and the
+// first column of the inverse normal matrix A^-1 e_0 (zero past M and when
+// singular), and the status bits (as the float's bits).
+enum FitState : int {
+    kStW = 0, kStM = 1, kStN = 4, kStE1 = 7, kStE2 = 10, kStLam = 13, kStA = 16, kStC0 = 22, kStStatus = 28,
+    kStFloats = 29
+};
+static_assert(kStFloats == MLS_FIT_STATE_FLOATS, "fit state layout");
+
 // Row: callable, Row(j) = index of the point's neighbour j.  All 32 lanes of
 // the warp must call this together when G > 1 (the merges are warp shuffles,
 // and no lane leaves before the last of them); with G = 1 no lane talks to
@@ -40,15 +52,21 @@ constexpr uint8_t kDeferFP64 = 0x80;
 // max_iter passes, else status bit MLS_PT_NOT_CONVERGED); the height fit
 // then uses the weights about the final q.  Points stop after different
 // numbers of passes, so LEVIN takes one lane per point (G = 1).
-template <int DEG, int PREC, bool LEVIN = false, bool DEFER = false, class Row>
+//
+// STATE (G = 1, not LEVIN) also writes the point's fit state (FitState) to
+// state[c * stride], unless the point is deferred.
+template <int DEG, int PREC, bool LEVIN = false, bool DEFER = false, bool STATE = false, class Row>
 __device__ __forceinline__ uint8_t project_point(const float4 *__restrict__ xyz4, const Row &row, int k, int sub,
                                                  int G, float h, float rx, float ry, float rz, float out[3],
-                                                 float nf[3], int max_iter = 1, float tol = 0.f) {
+                                                 float nf[3], int max_iter = 1, float tol = 0.f,
+                                                 float *__restrict__ state = nullptr, int64_t stride = 0) {
+    static_assert(!(STATE && LEVIN), "the fit state is that of the weights about r");
     // exp(-|d|^2 / h^2) = exp2(-|d|^2 * log2(e) / h^2)
     const float neg_scale = -1.4426950408889634f / (h * h);
     uint8_t st = 0;
     float W, mx, my, mz;
     float e1f[3], e2f[3];
+    float lam_s[3] = {0.f, 0.f, 0.f};     // eigenvalues, kept for the state
     // q = r + tq * (qx, qy, qz): the centre of the weights (r unless LEVIN)
     float tq = 0.f, qx = 0.f, qy = 0.f, qz = 0.f;
     for (int it = 0;; ++it) {
@@ -118,6 +136,10 @@ __device__ __forceinline__ uint8_t project_point(const float4 *__restrict__ xyz4
         {
             float lam[3];
             int deg_flag = frame_from<float>(C, nf, e1f, e2f, lam);
+            if (STATE) {
+#pragma unroll
+                for (int a = 0; a < 3; ++a) lam_s[a] = lam[a];
+            }
             // the FP32 eigenvector error grows like eps * l2 / (l1 - l0): in the
             // mixed form, narrow gaps are solved again in FP64 from the same moments
             if (PREC == MLS_PREC_MIXED && (!(lam[2] > 0.f) || (lam[1] - lam[0]) < kMixedGapFlag * lam[2])) {
@@ -131,6 +153,7 @@ __device__ __forceinline__ uint8_t project_point(const float4 *__restrict__ xyz4
                     nf[a] = (float)nd[a];
                     e1f[a] = (float)e1d[a];
                     e2f[a] = (float)e2d[a];
+                    if (STATE) lam_s[a] = (float)ld[a];
                 }
                 st |= MLS_PT_FP64_USED;
             }
@@ -218,20 +241,43 @@ __device__ __forceinline__ uint8_t project_point(const float4 *__restrict__ xyz4
 #pragma unroll
         for (int c = 0; c < 6; ++c) rhs[c] += __shfl_xor_sync(0xffffffffu, rhs[c], s);
     }
-    if (degenerate) return st;
+    constexpr int M = Basis<DEG>::M;
+    float a_s[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, c0_s[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    // the state of the point (status st, coefficients a_s, column c0_s)
+    auto save = [&]() {
+        if (!STATE) return;
+        const float v[kStFloats] = {W, mx, my, mz, nf[0], nf[1], nf[2], e1f[0], e1f[1], e1f[2], e2f[0], e2f[1],
+                                    e2f[2], lam_s[0], lam_s[1], lam_s[2], a_s[0], a_s[1], a_s[2], a_s[3], a_s[4],
+                                    a_s[5], c0_s[0], c0_s[1], c0_s[2], c0_s[3], c0_s[4], c0_s[5],
+                                    __int_as_float((int)st)};
+#pragma unroll
+        for (int c = 0; c < kStFloats; ++c) state[c * stride] = v[c];
+    };
+    if (degenerate) {
+        save();
+        return st;
+    }
     bool singular;
     float cond;
-    float a0 = solve_a0<float, DEG>(mom, rhs, true, singular, cond);
+    float a0 = solve_a0<float, DEG, STATE>(mom, rhs, true, singular, cond, a_s, c0_s);
     if (PREC == MLS_PREC_MIXED && (singular || !(cond < kMixedCondFlag))) {
         if (DEFER) return kDeferFP64;
-        double condd;
-        a0 = (float)solve_a0<double, DEG>(mom, rhs, false, singular, condd);
+        double condd, ad[6], cd[6];
+        a0 = (float)solve_a0<double, DEG, STATE>(mom, rhs, false, singular, condd, ad, cd);
+        if (STATE) {
+#pragma unroll
+            for (int r = 0; r < M; ++r) {
+                a_s[r] = (float)ad[r];
+                c0_s[r] = (float)cd[r];
+            }
+        }
         st |= MLS_PT_FP64_USED;
     }
     if (singular) {
         st |= MLS_PT_POLY_SINGULAR;
         a0 = 0.f;
     }
+    save();
     const float s = ofs + a0;
     out[0] = fmaf(s, nf[0], rx);
     out[1] = fmaf(s, nf[1], ry);

@@ -182,9 +182,13 @@ __device__ void assemble(const float mom[15], T A[Basis<DEG>::M][Basis<DEG>::M])
         }
 }
 
-// Solve the height fit: returns a0 and whether the system was singular.
-template <typename T, int DEG>
-__device__ T solve_a0(const float mom[15], const float rhs[6], bool refine, bool &singular, T &cond_est) {
+// Solve the height fit A a = b: returns a0 and whether the system was
+// singular.  With FULL, also every coefficient a[0..M) and the first column
+// of A^-1, c0 = A^-1 e_0 (what the adjoint needs: b-bar = a0-bar c0), both
+// zero when singular; a[0] is the returned a0 bit for bit.
+template <typename T, int DEG, bool FULL = false>
+__device__ T solve_a0(const float mom[15], const float rhs[6], bool refine, bool &singular, T &cond_est,
+                      T *a_out = nullptr, T *c0_out = nullptr) {
     constexpr int M = Basis<DEG>::M;
     T A[M][M], L[M][M], invd[M], b[M], x[M];
     assemble<T, DEG>(mom, A);
@@ -193,7 +197,13 @@ __device__ T solve_a0(const float mom[15], const float rhs[6], bool refine, bool
     T pmin, pmax;
     singular = !cholesky<T, M>(A, L, invd, T(1e-12), pmin, pmax);
     cond_est = (pmax / pmin) * (pmax / pmin);
-    if (singular) return T(0);
+    if (singular) {
+        if (FULL) {
+#pragma unroll
+            for (int r = 0; r < M; ++r) a_out[r] = c0_out[r] = T(0);
+        }
+        return T(0);
+    }
     chol_solve<T, M>(L, invd, b, x);
     if (refine) {
         T res[M], dx[M];
@@ -207,6 +217,15 @@ __device__ T solve_a0(const float mom[15], const float rhs[6], bool refine, bool
         chol_solve<T, M>(L, invd, res, dx);
 #pragma unroll
         for (int r = 0; r < M; ++r) x[r] += dx[r];
+    }
+    if (FULL) {
+        T e0[M];
+#pragma unroll
+        for (int r = 0; r < M; ++r) {
+            e0[r] = r == 0 ? T(1) : T(0);
+            a_out[r] = x[r];
+        }
+        chol_solve<T, M>(L, invd, e0, c0_out);
     }
     return x[0];
 }

@@ -68,19 +68,22 @@ class ProjectFunction(torch.autograd.Function):
     mls_project_backward (gradients for the coordinates and h; the neighbour
     rows are constants); with the grid the rows came from and its rows of
     sorted positions, mls_project_sorted and mls_project_backward_sorted (the
-    same results, in the grid's order).  Only xyz, the rows and h are saved:
-    the backward recomputes every per-point frame."""
+    same forward results, in the grid's order).  The plain form saves only
+    xyz, the rows and h, and its backward recomputes every per-point frame;
+    the grid-order form also saves the fit state (MLS_FIT_STATE_FLOATS floats
+    per point), which its backward reads instead."""
 
     @staticmethod
     def forward(ctx, xyz, h, idx, degree, precision, order, grid=None, pos=None):
         hv = float(h)
+        fit_state = None
         if grid is not None and pos is not None and precision != "fp64":
-            out, nrm, st = capi.mls_project_sorted(grid, pos, hv, degree, precision)
+            out, nrm, st, fit_state = capi.mls_project_sorted(grid, pos, hv, degree, precision, with_state=True)
         else:
             out, nrm, st = capi.mls_project(xyz, idx, hv, degree, precision, order=order)
         ctx.save_for_backward(xyz, idx, order if order is not None else torch.empty(0, dtype=torch.int32))
         ctx.hv, ctx.degree, ctx.precision, ctx.has_order = hv, degree, precision, order is not None
-        ctx.sorted = (grid, pos) if grid is not None and pos is not None and precision != "fp64" else None
+        ctx.sorted = (grid, pos, fit_state) if fit_state is not None else None
         ctx.h_shape = h.shape if isinstance(h, torch.Tensor) else None
         ctx.mark_non_differentiable(st)
         return out, nrm, st
@@ -91,10 +94,11 @@ class ProjectFunction(torch.autograd.Function):
         if g_out is None:
             g_out = torch.zeros_like(xyz)
         if ctx.sorted is not None:
-            grid, pos = ctx.sorted
+            grid, pos, fit_state = ctx.sorted
             gx, gh = capi.mls_project_backward_sorted(grid, pos, ctx.hv, g_out.contiguous(),
                                                       None if g_n is None else g_n.contiguous(), ctx.degree,
-                                                      ctx.precision)
+                                                      ctx.precision, state=fit_state)
+            ctx.sorted = None
         else:
             gx, gh = capi.mls_project_backward(xyz, idx, ctx.hv, g_out.contiguous(),
                                                None if g_n is None else g_n.contiguous(), ctx.degree, ctx.precision,

@@ -170,11 +170,26 @@ def _area_uniform_superquadric(rng, n, a, e1, e2):
     return np.concatenate(out)[:n]
 
 
+def _batch_draws(rng, n_min: int, n_max: int, size_scale: float):
+    n = int(round(math.exp(rng.uniform(math.log(n_min), math.log(n_max))) * size_scale))
+    return max(n, 64), int(rng.choice([16, 32, 64]))
+
+
+def batch_cloud_size(b: int, seed0: int = 4, n_min: int = 1_000, n_max: int = 500_000,
+                     size_scale: float = 1.0) -> tuple[int, int]:
+    """(points, k) of cloud b of batch_clouds, without generating it."""
+    return _batch_draws(np.random.default_rng(seed0 + b), n_min, n_max, size_scale)
+
+
+def batch_cloud(b: int, seed0: int = 4, n_min: int = 1_000, n_max: int = 500_000, noise_frac: float = 0.003,
+                size_scale: float = 1.0) -> Cloud:
+    """Cloud b of batch_clouds (same arguments) alone."""
+    return _batch_cloud(b, seed0, n_min, n_max, noise_frac, size_scale)
+
+
 def _batch_cloud(b: int, seed0: int, n_min: int, n_max: int, noise_frac: float, size_scale: float) -> Cloud:
     rng = np.random.default_rng(seed0 + b)
-    n = int(round(math.exp(rng.uniform(math.log(n_min), math.log(n_max))) * size_scale))
-    n = max(n, 64)
-    k = int(rng.choice([16, 32, 64]))
+    n, k = _batch_draws(rng, n_min, n_max, size_scale)
     a = rng.uniform(0.2, 1.0, 3)
     if b % 2 == 0:
         e1 = e2 = 1.0                               # ellipsoid

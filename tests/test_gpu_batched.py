@@ -183,3 +183,33 @@ def test_from_clouds_uses_the_gpu_neighbours(capi):
         g = [t.cpu().numpy() for t in bp.cloud(c)]
         compare_projection(*g, *o, diag_len(cloud.xyz), min_well_posed=0.3)
     bp.close()
+
+
+@pytest.mark.parametrize("shape", [(1, 128, 1), (2, 64, 4)])
+def test_full_size_batch_clouds_sampled_against_oracle(capi, shape):
+    """The largest clouds of the 256-cloud workload at full size (the two
+    largest: 493k points at k = 32 and 472k at k = 16; the two largest with
+    k = 64: 443k and 376k), in one batch at one and two lanes per point: the
+    GPU rows of a seeded sample of 1,500 points per cloud are the oracle's
+    k-d tree rows, and their projections match the oracle's."""
+    from paper_2401_03365_gb300.batched import BatchedProjector
+    sizes = [workloads.batch_cloud_size(b) for b in range(256)]
+    big = sorted(range(256), key=lambda b: -sizes[b][0])[:2]
+    big64 = sorted((b for b in range(256) if sizes[b][1] == 64), key=lambda b: -sizes[b][0])[:2]
+    clouds = [workloads.batch_cloud(b) for b in big + big64]
+    xs = [torch.from_numpy(c.xyz).cuda() for c in clouds]
+    bp = BatchedProjector.from_clouds(xs, [c.k for c in clouds])
+    capi.mls_batch_set_shape(bp.batch, *shape)
+    bp.run()
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(48)
+    for c, cloud in enumerate(clouds):
+        a, e = bp.batch.offsets[c], bp.batch.offsets[c + 1]
+        q = np.sort(rng.choice(cloud.n, 1500, replace=False))
+        rows_o, _ = oracle.knn_kdtree(cloud.xyz, cloud.k, queries=q)
+        rows_g = bp.idx[bp.batch.idx_offset(c):bp.batch.idx_offset(c + 1)].reshape(e - a, cloud.k).cpu().numpy()
+        assert np.array_equal(rows_g[q], rows_o)
+        o = oracle.project(cloud.xyz, rows_o, float(bp.h[c].item()), 2, queries=q)
+        g = [t.cpu().numpy()[q] for t in bp.cloud(c)]
+        compare_projection(*g, *o, diag_len(cloud.xyz), min_well_posed=0.3)
+    bp.close()

@@ -118,17 +118,29 @@ def test_sorted_backward_equals_mls_project_backward(capi, degree, precision):
     assert torch.equal(a, b) and torch.equal(ah, bh)
 
 
-def test_sorted_autograd_equals_unsorted(capi):
+def test_sorted_autograd_equals_the_state_calls(capi):
+    """The autograd Function in the grid's order saves the forward's fit state
+    and its backward reads it: its gradients equal those of
+    mls_project_sorted (with_state) + mls_project_backward_sorted(state) bit
+    for bit, and are within rounding of the recomputing unsorted form's."""
     from paper_2401_03365_gb300 import mls
     c = workloads.bumpy_sphere(n=50_000, seed=44)
     x, grid, pos, idx, _, order = _setup(capi, c.xyz, c.k)
-    grads = []
-    for kw in ({"order": order}, {"order": order, "grid": grid, "pos": pos}):
-        xg = x.clone().requires_grad_(True)
-        ht = torch.tensor(0.03, device="cuda", requires_grad=True)
-        out, nrm, _ = mls.project_differentiable(xg, idx, ht, 2, "fp32", **kw)
-        ((out.norm(dim=1) - 1.0) ** 2).sum().add(0.1 * nrm[:, 2].sum()).backward()
-        grads.append((xg.grad.clone(), ht.grad.clone()))
+    gen = torch.Generator(device="cuda").manual_seed(45)
+    gp = torch.randn(c.n, 3, device="cuda", generator=gen)
+    gn = 0.1 * torch.randn(c.n, 3, device="cuda", generator=gen)
+    xg = x.clone().requires_grad_(True)
+    ht = torch.tensor(0.03, device="cuda", requires_grad=True)
+    out, nrm, _ = mls.project_differentiable(xg, idx, ht, 2, "fp32", order=order, grid=grid, pos=pos)
+    # a linear loss: its cotangents are gp and gn exactly
+    ((out * gp).sum() + (nrm * gn).sum()).backward()
+    o2, n2, _, state = capi.mls_project_sorted(grid, pos, 0.03, 2, "fp32", with_state=True)
+    assert torch.equal(out.detach(), o2) and torch.equal(nrm.detach(), n2)
+    gx, gh = capi.mls_project_backward_sorted(grid, pos, 0.03, gp, gn, 2, "fp32", state=state)
+    gx_u, gh_u = capi.mls_project_backward(x, idx, 0.03, gp, gn, 2, "fp32", order=order)
     torch.cuda.synchronize()
     grid.close()
-    assert torch.equal(grads[0][0], grads[1][0]) and torch.equal(grads[0][1], grads[1][1])
+    assert torch.equal(xg.grad, gx) and torch.equal(ht.grad.reshape(1), gh)
+    scale = gx_u.norm(dim=1).median()
+    assert float((gx - gx_u).norm(dim=1).median()) <= 1e-5 * float(scale)
+    assert abs(float(gh) - float(gh_u)) <= 1e-3 * abs(float(gh_u))

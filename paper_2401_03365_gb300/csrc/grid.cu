@@ -121,15 +121,19 @@ __global__ void k_frame(Misc *m) {
     m->frame = f;
 }
 
-__global__ void k_keys(const float *__restrict__ xyz, int64_t n, const Misc *__restrict__ m,
+// Sort keys: the Hilbert index of each point's level-0 cell, or, for a build
+// that sorts only the levels from `level` up, the index of its level-`level`
+// cell on the coarser curve shifted into place (the same top bits, the bits
+// below zero: points within such a cell keep their input order).
+__global__ void k_keys(const float *__restrict__ xyz, int64_t n, const Misc *__restrict__ m, int level,
                        uint64_t *__restrict__ keys, int32_t *__restrict__ perm) {
     GridFrame f = m->frame;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
         uint32_t c[3];
 #pragma unroll
-        for (int a = 0; a < 3; ++a) c[a] = cell_coord(xyz[3 * i + a], f.origin[a], f.inv_s0);
-        keys[i] = hilbert3(c[0], c[1], c[2], kMortonBits);
+        for (int a = 0; a < 3; ++a) c[a] = cell_coord(xyz[3 * i + a], f.origin[a], f.inv_s0) >> level;
+        keys[i] = hilbert3(c[0], c[1], c[2], kMortonBits - level) << (3 * level);
         perm[i] = (int32_t)i;
     }
 }
@@ -193,13 +197,20 @@ __global__ void __launch_bounds__(1024) k_radix_scan(int32_t *__restrict__ block
     if (threadIdx.x == 0) totals[blockIdx.x] = carry;
 }
 
+// Scatter of one digit pass.  Each warp ranks its 256 keys per digit (stable:
+// item order, then lane); the block's keys are then reordered by digit in
+// shared memory, so that consecutive threads write consecutive positions of
+// one digit's run (coalesced stores instead of one segment per lane).
 __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(
     const uint64_t *__restrict__ keys_in, const int32_t *__restrict__ vals_in, int64_t n, int shift,
     int nblocks, const int32_t *__restrict__ block_off, const int32_t *__restrict__ totals,
     uint64_t *__restrict__ keys_out, int32_t *__restrict__ vals_out) {
     constexpr int kWarps = kSortThreads / 32;
     __shared__ int wcount[kWarps][kDigits];
-    __shared__ int digit_base[kDigits];
+    __shared__ int digit_base[kDigits];     // global start of each digit's run
+    __shared__ int local_start[kDigits];    // start of each digit's run within the block
+    __shared__ uint64_t tile_k[kSortTile];
+    __shared__ int32_t tile_v[kSortTile];
     int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int d = threadIdx.x; d < kDigits * kWarps; d += blockDim.x) (&wcount[0][0])[d] = 0;
     // exclusive scan of the digit totals (256 entries) by warp 0
@@ -220,7 +231,8 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(
     uint64_t k[kSortItems];
     int32_t v[kSortItems];
     int rank[kSortItems];
-    int64_t wbase = (int64_t)blockIdx.x * kSortTile + (int64_t)warp * 32 * kSortItems;
+    const int64_t bbase = (int64_t)blockIdx.x * kSortTile;
+    const int64_t wbase = bbase + (int64_t)warp * 32 * kSortItems;
 #pragma unroll
     for (int it = 0; it < kSortItems; ++it) {
         int64_t i = wbase + it * 32 + lane;
@@ -238,7 +250,7 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(
         __syncwarp();
     }
     __syncthreads();
-    // exclusive scan of each digit's count over the warps of the block
+    // per digit: exclusive scan of its count over the warps, and its total
     for (int d = threadIdx.x; d < kDigits; d += blockDim.x) {
         int s = 0;
 #pragma unroll
@@ -247,17 +259,42 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(
             wcount[w][d] = s;
             s += c;
         }
+        local_start[d] = s;
     }
     __syncthreads();
+    // exclusive scan of the block's digit totals (warp 0)
+    if (warp == 0) {
+        int carry = 0;
+        for (int c = 0; c < kDigits; c += 32) {
+            int v0 = local_start[c + lane], x = v0;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                int y = __shfl_up_sync(0xffffffffu, x, o);
+                if (lane >= o) x += y;
+            }
+            local_start[c + lane] = carry + x - v0;
+            carry += __shfl_sync(0xffffffffu, x, 31);
+        }
+    }
+    __syncthreads();
+    // the block's keys in digit order
 #pragma unroll
     for (int it = 0; it < kSortItems; ++it) {
         int64_t i = wbase + it * 32 + lane;
         if (i >= n) continue;
         int d = (int)((k[it] >> shift) & (kDigits - 1));
-        int64_t pos = (int64_t)digit_base[d] + block_off[(int64_t)d * nblocks + blockIdx.x] +
-                      wcount[warp][d] + rank[it];
-        keys_out[pos] = k[it];
-        vals_out[pos] = v[it];
+        int at = local_start[d] + wcount[warp][d] + rank[it];
+        tile_k[at] = k[it];
+        tile_v[at] = v[it];
+    }
+    __syncthreads();
+    const int count = (int)min((int64_t)kSortTile, n - bbase);
+    for (int t = threadIdx.x; t < count; t += kSortThreads) {
+        const uint64_t key = tile_k[t];
+        const int d = (int)((key >> shift) & (kDigits - 1));
+        const int64_t pos = (int64_t)digit_base[d] + block_off[(int64_t)d * nblocks + blockIdx.x] + (t - local_start[d]);
+        keys_out[pos] = key;
+        vals_out[pos] = tile_v[t];
     }
 }
 
@@ -445,7 +482,6 @@ int build_grid(mls_grid *g, const float *xyz, int64_t n, float cell_size, int k_
     k_init_misc<<<1, 32, 0, st>>>(m);
     k_bbox<<<blocks_for(n, T), T, 0, st>>>(xyz, n, m);
     k_frame<<<1, 32, 0, st>>>(m);
-    k_keys<<<blocks_for(n, T), T, 0, st>>>(xyz, n, m, g->keys, g->perm);
     MLS_CUDA_TRY(cudaGetLastError());
 
     // radix sort of the keys' bits from level sort_level up, 8 bits a pass
@@ -470,6 +506,8 @@ int build_grid(mls_grid *g, const float *xyz, int64_t n, float cell_size, int k_
         // their width allows: the extra low bits order points within the cells
         // more finely at no cost)
         const int passes = (kKeyBits - 3 * sort_level + kDigitBits - 1) / kDigitBits;
+        k_keys<<<blocks_for(n, T), T, 0, st>>>(xyz, n, m, sort_level, g->keys, g->perm);
+        count_launches(1);
         for (int shift = std::max(0, kKeyBits - kDigitBits * passes); shift < kKeyBits; shift += kDigitBits) {
             k_radix_hist<<<nblocks, kSortThreads, 0, st>>>(g->keys, n, shift, nblocks, g->block_hist);
             k_radix_scan<<<kDigits, 1024, 0, st>>>(g->block_hist, nblocks, g->scan_tmp);
@@ -574,7 +612,7 @@ int build_grid(mls_grid *g, const float *xyz, int64_t n, float cell_size, int k_
                                                    dev_ptrs);
     dim3 hg(blocks_for(cells[base], T), nlev);
     k_hash_insert<<<hg, T, 0, st>>>(v, dev_ptrs, base, (int)n);
-    count_launches(4 + 4);     // init, bbox, frame, keys; head count, scan, head write, hash insert
+    count_launches(3 + 4);     // init, bbox, frame; head count, scan, head write, hash insert
     MLS_CUDA_TRY(cudaGetLastError());
     return MLS_OK;
 }

@@ -3,7 +3,10 @@
 // 0 .. 8^bits - 1, the top 3 l bits of a cell's key depend only on its
 // level-l cell (so each cell of each level is one run of consecutive keys),
 // and consecutive keys are face-adjacent cells; on the 21-bit grid the
-// level property holds on random cells.  Prints "failures N".
+// level property holds on random cells, and the index of a cell's level-l
+// cell on the coarse curve of 21 - l levels is the cell's key shifted down
+// by 3 l (what a build that sorts only the levels from l up computes).
+// Prints "failures N".
 #include <cstdint>
 #include <cstdio>
 #include <cstdlib>
@@ -53,8 +56,9 @@ int main() {
         const uint32_t x = r & 0x1fffff, y = (r >> 21) & 0x1fffff, z = (r >> 42) & 0x1fffff;
         const int l = 1 + (int)((next_u64() >> 7) % 20);
         const uint32_t m = ~((1u << l) - 1u);
-        if ((mls::hilbert3(x, y, z, 21) >> (3 * l)) != (mls::hilbert3(x & m, y & m, z & m, 21) >> (3 * l)))
-            ++failures;
+        const uint64_t full = mls::hilbert3(x, y, z, 21);
+        if ((full >> (3 * l)) != (mls::hilbert3(x & m, y & m, z & m, 21) >> (3 * l))) ++failures;
+        if ((full >> (3 * l)) != mls::hilbert3(x >> l, y >> l, z >> l, 21 - l)) ++failures;
     }
     printf("failures %ld\n", failures);
     return failures != 0;

@@ -511,6 +511,8 @@ def run_ours(args):
         line["cpu_baseline_all_cores"] = cpu_baseline_all_cores(cloud.xyz, h, args.cpu_sample)
     del cloud, x, idx, out_xyz, out_n, out_st, grad, gp, gn
     torch.cuda.empty_cache()
+    if world == 1:
+        line["sphere20k_k20"] = run_latency(args, dev)
     if world == 1 and not args.no_scan:
         line["scan50m_k64"] = run_scan(args, dev, peaks, flush)
     if world == 1 and not args.no_differentiable:
@@ -572,6 +574,71 @@ def _timed_stages(fns, reps, stream, flush=None):
             ev[r][i + 1].record(stream)
     torch.cuda.synchronize()
     return [float(np.mean([ev[r][i].elapsed_time(ev[r][i + 1]) for r in range(reps)])) for i in range(len(fns))]
+
+
+def run_latency(args, dev):
+    """The small workload (20,000 points on a noisy unit sphere, k = 20,
+    mixed): the latency of one whole step (grid build + kNN + projection
+    saving the fit state + adjoint from it), from CUDA events on the stream
+    and from the host clock (which adds the launches and the grid build's one
+    stream synchronisation); the cloud stays in L2 between steps."""
+    import torch
+
+    from paper_2401_03365_gb300 import capi, workloads
+    c = workloads.sphere()
+    n, k = c.n, c.k
+    stream = torch.cuda.current_stream()
+    x = torch.from_numpy(c.xyz).to(dev)
+    grid = capi.mls_build_grid(x, 0.0, k)
+    idx, _ = capi.mls_knn(grid, k)
+    h = 2.0 * float(capi.mls_mean_knn_dist(x, idx).item())
+    del idx
+    pos = torch.empty((n, k), dtype=torch.int32, device=dev)
+    out = [torch.empty_like(x), torch.empty_like(x), torch.empty(n, dtype=torch.uint8, device=dev)]
+    fit_state = torch.empty((capi.FIT_STATE_FLOATS, n), dtype=torch.float32, device=dev)
+    gen = torch.Generator(device=dev).manual_seed(5)
+    gp = torch.randn(n, 3, device=dev, generator=gen)
+    gn = 0.1 * torch.randn(n, 3, device=dev, generator=gen)
+    grad = torch.empty_like(x)
+    grad_h = torch.empty(1, dtype=torch.float32, device=dev)
+    state = {"grid": grid}
+
+    def step(ev=None):
+        if ev: ev[0].record(stream)
+        state["grid"] = capi.mls_build_grid(x, 0.0, k, grid=state["grid"])
+        if ev: ev[1].record(stream)
+        capi.mls_knn_sorted(state["grid"], k, out_pos=pos)
+        if ev: ev[2].record(stream)
+        capi.mls_project_sorted(state["grid"], pos, h, 2, "mixed", out_xyz=out[0], out_normal=out[1],
+                                out_status=out[2], with_state=True, out_state=fit_state)
+        if ev: ev[3].record(stream)
+        capi.mls_project_backward_sorted(state["grid"], pos, h, gp, gn, 2, "mixed", out_grad_xyz=grad,
+                                         out_grad_h=grad_h, state=fit_state)
+        if ev: ev[4].record(stream)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    steps = max(args.steps, 20)
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(steps)]
+    wall = []
+    for s in range(steps):
+        t0 = time.perf_counter()
+        step(evs[s])
+        evs[s][4].synchronize()
+        wall.append((time.perf_counter() - t0) * 1e3)
+    stage = np.array([[e[i].elapsed_time(e[i + 1]) for i in range(4)] for e in evs])
+    state["grid"].close()
+    ms = float(np.median(stage.sum(1)))
+    return {"workload": "sphere20k_k20: 20,000 points on a unit sphere, radial noise 0.01, k=20, h = 2 x mean kNN "
+                        "distance, degree 2, mixed",
+            "ms_per_step": ms, "value": n / (ms * 1e-3), "unit": "points/s", "steps": steps,
+            "host_ms_per_step": float(np.median(wall)),
+            "stages_ms": {name: float(np.median(stage[:, i])) for i, name in
+                          enumerate(("grid_build", "knn", "project", "backward"))},
+            "step": "grid build + exact kNN + projection (fit state saved) + adjoint from it, one step at a time "
+                    "(median over the steps); host_ms_per_step: host clock from the first call to the step's end",
+            "l2": "the cloud stays in L2 (20,000 points): a latency figure"}
 
 
 def run_scan(args, dev, peaks, flush):

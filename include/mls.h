@@ -79,7 +79,8 @@ enum mls_point_status {
     MLS_PT_POLY_SINGULAR = 2,
     MLS_PT_FP64_USED = 4,
     MLS_PT_NOT_CONVERGED = 8,  /* mls_project_levin: t still moving after max_iter passes */
-    MLS_PT_OUTLIER = 16        /* mls_project_rows: too few neighbours, not projected */
+    MLS_PT_OUTLIER = 16,       /* mls_project_rows: too few neighbours, not projected */
+    MLS_PT_DEGREE_REDUCED = 32 /* mls_project_rows: fewer points than twice the basis size: a lower degree */
 };
 
 #define MLS_MAX_K 64
@@ -273,7 +274,11 @@ int mls_project_levin(const float *d_xyz, int64_t n, const int32_t *d_idx, int k
  *   over CSR neighbourhoods (d_offsets n + 1 int64, d_rows int32, rows of any
  *   length); a point with fewer than min_neighbors (>= 0) OTHER points in its
  *   row is an outlier: not projected, output = the point, normal = 0, status
- *   MLS_PT_OUTLIER.  precision MLS_PREC_FP32 or MLS_PREC_MIXED.
+ *   MLS_PT_OUTLIER.  A row of m points (the point included) is fitted at the
+ *   highest degree <= `degree` whose basis has at most m / 2 coefficients
+ *   (degree 2 needs m >= 12, degree 1 m >= 6), status MLS_PT_DEGREE_REDUCED
+ *   when lowered: fewer points would be interpolated rather than smoothed.
+ *   precision MLS_PREC_FP32 or MLS_PREC_MIXED.
  * mls_compact: d_kept (capacity n int32) = the indices i with
  *   (d_status[i] & mask) == 0 in increasing order; *d_num_kept (device int64)
  *   = their number (the paper's result drops the outliers: mask =

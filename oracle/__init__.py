@@ -28,13 +28,14 @@ from .build import build_oracle, library_path
 __all__ = [
     "knn_brute", "knn_kdtree", "mean_knn_dist", "project", "project_grad", "project_levin", "fit_height",
     "jacobi_eig", "cholesky_solve", "knn_key", "STATUS_PLANE_DEGENERATE", "STATUS_POLY_SINGULAR",
-    "STATUS_NOT_CONVERGED", "STATUS_OUTLIER", "radius_neighbors", "project_rows",
+    "STATUS_NOT_CONVERGED", "STATUS_OUTLIER", "STATUS_DEGREE_REDUCED", "radius_neighbors", "project_rows",
 ]
 
 STATUS_PLANE_DEGENERATE = 1
 STATUS_POLY_SINGULAR = 2
 STATUS_NOT_CONVERGED = 8
 STATUS_OUTLIER = 16
+STATUS_DEGREE_REDUCED = 32
 
 _lib = None
 
@@ -203,7 +204,9 @@ def radius_neighbors(xyz, R):
 
 
 def project_rows(xyz, offsets, rows, h, degree=2, min_neighbors=3):
-    """Projection over CSR neighbourhoods with the outlier rule (status 16).
+    """Projection over CSR neighbourhoods with the outlier rule (status 16)
+    and, for small neighbourhoods, a lower degree (status 32: fewer than
+    twice the basis size in points).
     Returns (xyz', normal, status, diag) as oracle.project (diag 0 for
     outliers)."""
     xyz = _xyz(xyz)

@@ -946,6 +946,21 @@ int oracle_project_levin(const float *xyz, int64_t n, const int32_t *idx, int k,
 /* ------------------------------------------------------------------------- */
 
 #define ST_OUTLIER 16
+#define ST_DEGREE_REDUCED 32
+
+/* Reading R8b (radius mode): a neighbourhood of m points (the point included)
+ * is fitted at the highest degree d <= the requested one whose basis has at
+ * most m / 2 coefficients (degree 2: 6, so m >= 12; degree 1: 3, so m >= 6;
+ * degree 0 otherwise).  With fewer points the fit would interpolate rather
+ * than smooth, and over 4-6 points a quadratic can move the point far from
+ * its neighbours; degrees 1 and 0 project the point onto its plane. */
+static int radius_degree(int degree, int m)
+{
+    static const int coeffs[3] = {1, 3, 6};
+    int d = degree;
+    while (d > 0 && m < 2 * coeffs[d]) --d;
+    return d;
+}
 
 typedef struct {
     kv_t *a;
@@ -1037,7 +1052,8 @@ int oracle_radius_kdtree(const float *xyz, int64_t n, float R2, const int64_t *o
  * offsets[i + 1])), with Sec. 3.3's outlier rule: a point with fewer than
  * min_neighbors other points in its neighbourhood is not projected (status
  * bit 16, output = the point, to be dropped from the result; diagnostics 0).
- * Everything else as oracle_project. */
+ * A small neighbourhood is fitted at a lower degree (radius_degree; status
+ * bit 32).  Everything else as oracle_project. */
 int oracle_project_rows(const float *xyz, int64_t n, const int64_t *offsets, const int32_t *rows, double h,
                         int degree, int min_neighbors, double *out_xyz, double *out_normal, uint8_t *out_status,
                         double *out_diag)
@@ -1063,12 +1079,13 @@ int oracle_project_rows(const float *xyz, int64_t n, const int64_t *offsets, con
                 for (int c = 0; c < 5; ++c) out_diag[5 * i + c] = 0.0;
             continue;
         }
-        project_point(xyz, rows + offsets[i], k, h, degree, i, &st);
+        const int d = radius_degree(degree, k);
+        project_point(xyz, rows + offsets[i], k, h, d, i, &st);
         for (int a = 0; a < 3; ++a) {
             out_xyz[3 * i + a] = st.out[a];
             if (out_normal) out_normal[3 * i + a] = st.nrm[a];
         }
-        if (out_status) out_status[i] = (uint8_t)st.status;
+        if (out_status) out_status[i] = (uint8_t)(st.status | (d < degree ? ST_DEGREE_REDUCED : 0));
         if (out_diag) {
             out_diag[5 * i + 0] = st.lam[0];
             out_diag[5 * i + 1] = st.lam[1];

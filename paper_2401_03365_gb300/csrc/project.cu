@@ -124,7 +124,9 @@ __global__ void __launch_bounds__(kProjThreads) k_project_deferred(const float4 
 // Variable neighbourhoods (CSR rows, e.g. the radius-R sets of Sec. 1.4),
 // one thread per point, rows read straight from global memory.  A point with
 // fewer than min_nb other points in its row is an outlier (Sec. 3.3): not
-// projected, status MLS_PT_OUTLIER, output = the point, normal = 0.
+// projected, status MLS_PT_OUTLIER, output = the point, normal = 0.  A row of
+// fewer than twice as many points as the basis has coefficients is fitted at
+// the next lower degree that has enough (status MLS_PT_DEGREE_REDUCED).
 template <int DEG, int PREC>
 __global__ void __launch_bounds__(kProjThreads, 8) k_project_rows(const float4 *__restrict__ xyz4, int64_t n,
                                                                const int64_t *__restrict__ off,
@@ -141,9 +143,20 @@ __global__ void __launch_bounds__(kProjThreads, 8) k_project_rows(const float4 *
     const float4 r4 = __ldg(xyz4 + i);
     float out[3] = {r4.x, r4.y, r4.z}, nf[3] = {0.f, 0.f, 0.f};
     uint8_t st = MLS_PT_OUTLIER;
-    if (k - 1 >= min_nb)
-        st = project_point<DEG, PREC>(
-            xyz4, [&](int j) { return __ldg(rows + b + j); }, k, 0, 1, h, r4.x, r4.y, r4.z, out, nf);
+    const auto row = [&](int j) { return __ldg(rows + b + j); };
+    if (k - 1 >= min_nb) {
+        // the highest degree whose basis has at most k / 2 coefficients
+        // (6, 3, 1): a smaller neighbourhood would be interpolated, not
+        // smoothed, and a quadratic over 4-6 points can throw the point far
+        if (DEG == 2 && k >= 12)
+            st = project_point<DEG, PREC>(xyz4, row, k, 0, 1, h, r4.x, r4.y, r4.z, out, nf);
+        else if (DEG >= 1 && k >= 6)
+            st = project_point<1, PREC>(xyz4, row, k, 0, 1, h, r4.x, r4.y, r4.z, out, nf) |
+                 (DEG > 1 ? MLS_PT_DEGREE_REDUCED : 0);
+        else
+            st = project_point<0, PREC>(xyz4, row, k, 0, 1, h, r4.x, r4.y, r4.z, out, nf) |
+                 (DEG > 0 ? MLS_PT_DEGREE_REDUCED : 0);
+    }
     out_xyz[3 * i] = out[0];
     out_xyz[3 * i + 1] = out[1];
     out_xyz[3 * i + 2] = out[2];

@@ -79,8 +79,38 @@ def test_projection_over_radius_rows_and_outliers(capi, precision):
     outl = (o_st & oracle.STATUS_OUTLIER) != 0
     assert 0 < outl.sum() < c.n
     assert np.array_equal((g_st & capi.MLS_PT_OUTLIER) != 0, outl)
+    assert np.array_equal(g_st & 32, o_st & oracle.STATUS_DEGREE_REDUCED)
     assert np.array_equal(kept, np.nonzero(~outl)[0])
     assert np.array_equal(g_xyz.cpu().numpy()[outl], c.xyz[outl])
     keep = ~outl
     compare_projection(g_xyz.cpu().numpy()[keep], g_n.cpu().numpy()[keep], g_st[keep], o_xyz[keep], o_n[keep],
                        o_st[keep] & 3, o_diag[keep], diag_len(c.xyz), min_well_posed=0.3)
+
+
+@pytest.mark.parametrize("precision", ["mixed", "fp32"])
+def test_small_radius_lowers_the_degree_like_the_oracle(capi, precision):
+    """R about twice the point spacing: two thirds of the neighbourhoods hold
+    4-11 points, fitted at degree 1 or 0 (status bit 32, set exactly where the
+    oracle sets it), a third 12 or more; positions and normals within the
+    tolerances on well-posed points."""
+    c = workloads.torus(n=100_000, seed=13)
+    R = 0.02
+    off_o, rows_o = oracle.radius_neighbors(c.xyz, R)
+    h = R
+    o_xyz, o_n, o_st, o_diag = oracle.project_rows(c.xyz, off_o, rows_o, h, 2, min_neighbors=3)
+    x = torch.from_numpy(c.xyz).cuda()
+    grid = capi.mls_build_grid(x, 0.0, 16)
+    off, rows, _ = capi.mls_radius_neighbors(grid, R)
+    order = capi.mls_grid_order(grid)
+    g_xyz, g_n, g_st = capi.mls_project_rows(x, off, rows, h, 2, precision, 3, order=order)
+    torch.cuda.synchronize()
+    grid.close()
+    g_st = g_st.cpu().numpy()
+    red = (o_st & oracle.STATUS_DEGREE_REDUCED) != 0
+    outl = (o_st & oracle.STATUS_OUTLIER) != 0
+    assert red.mean() > 0.5 and (~red & ~outl).mean() > 0.2
+    assert np.array_equal(g_st & (16 | 32), o_st & (16 | 32))
+    keep = ~outl
+    rep = compare_projection(g_xyz.cpu().numpy()[keep], g_n.cpu().numpy()[keep], g_st[keep], o_xyz[keep],
+                             o_n[keep], o_st[keep] & 3, o_diag[keep], diag_len(c.xyz), min_well_posed=0.2)
+    print(rep)

@@ -67,3 +67,42 @@ def test_outlier_rule_counts_the_other_points():
     _, _, st, _ = oracle.project_rows(pts, off, rows, 0.2, 0, min_neighbors=3)
     assert st[0] & oracle.STATUS_OUTLIER == 0
     assert all(st[i] & oracle.STATUS_OUTLIER for i in range(1, 8))
+
+
+def test_small_neighbourhoods_are_fitted_at_a_lower_degree():
+    """Reading R8b: a radius neighbourhood of m points (the point included)
+    is fitted at degree 2 only when m >= 12, at degree 1 when m >= 6, else at
+    degree 0 (status bit 32 when lowered).  Degrees 1 and 0 move the point to
+    its weighted plane, p' = q = r - <n, r - c> n (c the weighted centroid, n
+    the eigenvector of the smallest eigenvalue of the weighted covariance),
+    which is recomputed here with numpy's symmetric eigensolver."""
+    rng = np.random.default_rng(7)
+    clouds, sizes = [], (5, 6, 11, 12, 20)
+    for s, m in enumerate(sizes):
+        c = np.array([10.0 * s, 0.0, 0.0])
+        p = c + 0.05 * rng.standard_normal((m, 3)) * np.array([1.0, 1.0, 0.2])
+        clouds.append(p)
+    xyz = np.concatenate(clouds).astype(np.float32)
+    off, rows = oracle.radius_neighbors(xyz, 1.0)
+    counts = np.diff(off)
+    assert list(counts) == [m for m in sizes for _ in range(m)]
+    h = 0.08
+    out, nrm, st, _ = oracle.project_rows(xyz, off, rows, h, 2, min_neighbors=3)
+    reduced = (st & oracle.STATUS_DEGREE_REDUCED) != 0
+    assert np.array_equal(reduced, counts < 12)
+    x = xyz.astype(np.float64)
+    for i in np.nonzero(counts < 12)[0]:
+        nb = x[rows[off[i]:off[i + 1]]]
+        w = np.exp(-((nb - x[i]) ** 2).sum(1) / h ** 2)
+        c = (w[:, None] * nb).sum(0) / w.sum()
+        d = nb - c
+        C = (w[:, None, None] * d[:, :, None] * d[:, None, :]).sum(0)
+        n = np.linalg.eigh(C)[1][:, 0]
+        q = x[i] - np.dot(n, x[i] - c) * n
+        assert np.linalg.norm(out[i] - q) <= 1e-12, i
+        assert abs(abs(np.dot(nrm[i], n)) - 1.0) <= 1e-12
+    # rows of 6..11 points at degree 2 give the degree-1 result exactly
+    sel = (counts >= 6) & (counts < 12)
+    out1, _, st1, _ = oracle.project_rows(xyz, off, rows, h, 1, min_neighbors=3)
+    assert np.array_equal(out[sel], out1[sel])
+    assert not np.any(st1[sel] & oracle.STATUS_DEGREE_REDUCED)

@@ -270,18 +270,28 @@ def run_ours(args):
     capi.mls_knn(grid, K, out_idx=idx)
     h = 2.0 * float(capi.mls_mean_knn_dist(x, idx).item())
 
-    # one step: grid build, kNN (rows of sorted positions), the projection and
-    # the adjoint with a fixed cotangent, both in the grid's order
-    def step(xin, ev=None, before_forward_out=None, after_forward=None, before_backward=None):
+    # one step: grid build, kNN (rows of sorted positions) and the projection
+    # saving the fit state, pipelined in one call (the projection of the
+    # points the kNN's first pass finished runs beside its second pass), and
+    # the adjoint from the state with a fixed cotangent, all in the grid's
+    # order.  split=True makes the kNN and the projection two calls, for the
+    # per-stage times.
+    def step(xin, ev=None, before_forward_out=None, after_forward=None, before_backward=None, split=False):
         nonlocal grid
         if ev: ev[0].record(stream)
         grid = capi.mls_build_grid(xin, 0.0, K, grid=grid)
         if ev: ev[1].record(stream)
-        capi.mls_knn_sorted(grid, K, out_pos=pos)
-        if ev: ev[2].record(stream)
-        if before_forward_out: before_forward_out()
-        capi.mls_project_sorted(grid, pos, h, 2, "mixed", out_xyz=out_xyz, out_normal=out_n, out_status=out_st,
-                                with_state=True, out_state=fit_state)
+        if split:
+            capi.mls_knn_sorted(grid, K, out_pos=pos)
+            if ev: ev[2].record(stream)
+            if before_forward_out: before_forward_out()
+            capi.mls_project_sorted(grid, pos, h, 2, "mixed", out_xyz=out_xyz, out_normal=out_n,
+                                    out_status=out_st, with_state=True, out_state=fit_state)
+        else:
+            if before_forward_out: before_forward_out()
+            capi.mls_knn_project_sorted(grid, K, h, 2, "mixed", out_pos=pos, out_xyz=out_xyz, out_normal=out_n,
+                                        out_status=out_st, with_state=True, out_state=fit_state)
+            if ev: ev[2].record(stream)
         if ev: ev[3].record(stream)
         if after_forward: after_forward()
         if before_backward: before_backward()
@@ -311,9 +321,18 @@ def run_ours(args):
     launches = capi.mls_kernel_launches() - launches0
     deferred = capi.mls_knn_deferred(grid)
     stage = np.array([[e[i].elapsed_time(e[i + 1]) for i in range(4)] for e in events])  # ms
-    build_ms, knn_ms, proj_ms, bwd_ms = (float(v) for v in stage.mean(0))
+    build_ms, knn_proj_ms, _, bwd_ms = (float(v) for v in stage.mean(0))
     step_ms, fwd_ms, wall_ms = max_over_ranks([stage.sum(1).mean(), stage[:, :3].sum(1).mean(),
                                                wall * 1e3 / args.steps], dev)
+    # the same steps with the kNN and the projection as two calls: their own
+    # times (the kNN's roofline, the projection's FP32 fraction)
+    split_events = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(args.steps)]
+    for s in range(args.steps):
+        flush.zero_()
+        step(x, split_events[s], split=True)
+    torch.cuda.synchronize()
+    split_stage = np.array([[e[i].elapsed_time(e[i + 1]) for i in range(4)] for e in split_events])
+    _, knn_ms, proj_ms, _ = (float(v) for v in split_stage.mean(0))
     value = job_throughput(world, n_pts, step_ms)
     # end to end through the public API with host buffers: every step copies
     # its points in from pinned memory, runs the four calls, and copies the
@@ -456,6 +475,12 @@ def run_ours(args):
     clk = clocks.summary()
     mhz = clk.get("sm_mhz") or float(peaks.get("sm_max_mhz", 2070.0))
     kernels = stage_kernels(n_pts, K, build_ms, knn_ms, proj_ms, bwd_ms, peaks, mhz)
+    kernels["knn_project_pipelined"] = {
+        "ms": knn_proj_ms, "calls": "mls_knn_project_sorted (the timed step's kNN and projection in one call)",
+        "two_calls_ms": knn_ms + proj_ms,
+        "note": "knn and project above are the same work as two calls (mls_knn_sorted, mls_project_sorted), timed "
+                "in as many extra steps right after the timed ones; the pipelined call overlaps the projection of "
+                "the points the kNN's first pass finished with its second (sparse) pass"}
     roofline = dict(kernels["knn"]["roofline_hbm"])
     roofline["issue"] = kernels["knn"]["roofline_issue"]
     line = {
@@ -474,8 +499,9 @@ def run_ours(args):
         "config": {"workload": WORKLOAD if n_pts == N_POINTS else
                    WORKLOAD.replace("2,000,000", f"{n_pts:,}").replace("torus2m", "torus") + " (profiling size)",
                    "points_per_gpu": n_pts, "k": K, "degree": 2, "precision": "mixed",
-                   "h": h, "step": ("grid build + exact kNN (rows by sorted position) + MLS projection and "
-                                    "its backward in the grid's order (fwd+bwd)"),
+                   "h": h, "step": ("grid build + exact kNN (rows by sorted position) and MLS projection saving "
+                                    "the fit state, pipelined in one call, + the adjoint from that state, in the "
+                                    "grid's order (fwd+bwd)"),
                    "l2": "flushed before every step (256 MB write, outside the timed events)",
                    "parallelism": f"independent clouds per GPU x{world}"},
         "fwd": {"value": job_throughput(world, n_pts, fwd_ms), "unit": "points/s", "ms_per_step": fwd_ms,
@@ -499,7 +525,7 @@ def run_ours(args):
                   "two_pass_ms": knn_ms + proj_ms,
                   "step": "mls_knn_project: exact kNN + MLS projection in one pass (each warp projects its last 32 "
                           "queries from an L2-resident row buffer; rows not written), mixed, degree 2, same grid "
-                          "and h; two_pass_ms = the timed step's mls_knn_sorted + mls_project_sorted"},
+                          "and h; two_pass_ms = mls_knn_sorted + mls_project_sorted as separate calls"},
         "e2e": {"value": e2e_value, "unit": "points/s", "h2d_bytes_per_step": n_pts * 12,
                 "d2h_bytes_per_step": n_pts * (12 + 12 + 1 + 12)},
         "gpu_launches": int(launches),

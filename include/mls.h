@@ -206,6 +206,24 @@ int mls_project_sorted(const mls_grid *g, const int32_t *d_pos, int k, float h, 
 int mls_knn_project(const mls_grid *g, int k, float h, int degree, int precision, float *d_out_xyz,
                     float *d_out_normal, uint8_t *d_status, int32_t *d_pos, mls_stream stream);
 
+/*
+ * mls_knn_project_sorted -- mls_knn_sorted followed by mls_project_sorted (the
+ * neighbourhoods of Algorithm 1 and the projection of Sec. 1.4, Eq. 1 over
+ * them), pipelined: once the kNN's first pass has written the rows of all but
+ * the queries in sparse neighbourhoods, the projection of those points runs
+ * on a low-priority stream of the grid's own, beside the kNN's second pass;
+ * the points of the second pass are projected after it.  Outputs (d_pos and
+ * the projection's, d_state included) equal those of the two calls bit for
+ * bit.  Arguments as mls_knn_sorted (d_pos required) and mls_project_sorted.
+ * Scratch: 5 n bytes.  The grid's side stream and two events are created on
+ * the first call and destroyed with the grid; `stream` waits for the side
+ * stream before the call's last kernel, so the call is ordered on `stream`
+ * like any other.
+ */
+int mls_knn_project_sorted(const mls_grid *g, int k, float h, int degree, int precision, int32_t *d_pos,
+                           float *d_out_xyz, float *d_out_normal, uint8_t *d_status, float *d_state,
+                           mls_stream stream);
+
 /* Number of queries the last mls_knn call on this grid handed to its second
  * pass (queries whose first key bound needs a cube above the base level:
  * outliers, sparse regions); a measure of the work, never of the result.

@@ -17,7 +17,7 @@ from .build import library_path
 
 __all__ = [
     "MLSError", "Grid", "lib", "mls_build_grid", "mls_grid_destroy", "mls_grid_size", "mls_grid_order",
-    "mls_knn", "mls_knn_sorted", "mls_knn_deferred", "mls_points_in_boxes", "mls_project_sorted", "mls_knn_project", "mls_project_backward_sorted", "mls_project", "mls_project_levin", "mls_project_backward", "mls_radius_neighbors",
+    "mls_knn", "mls_knn_sorted", "mls_knn_deferred", "mls_points_in_boxes", "mls_project_sorted", "mls_knn_project", "mls_knn_project_sorted", "mls_project_backward_sorted", "mls_project", "mls_project_levin", "mls_project_backward", "mls_radius_neighbors",
     "mls_project_rows", "mls_compact", "mls_mean_knn_dist", "mls_status_str", "mls_last_error", "mls_kernel_launches", "mls_release_scratch",
     "Batch", "mls_batch_create", "mls_batch_destroy", "mls_batch_set_shape", "mls_batch_get_shape",
     "mls_project_batched", "mls_batch_capture", "mls_batch_replay", "mls_batch_autotune", "mls_batch_tune_results",
@@ -51,6 +51,7 @@ _SIGNATURES = [
     ("mls_knn_sorted", _int, [_vp, _int, _vp, _vp, _vp, _vp]),
     ("mls_project_sorted", _int, [_vp, _vp, _int, ctypes.c_float, _int, _int, _vp, _vp, _vp, _vp, _vp]),
     ("mls_knn_project", _int, [_vp, _int, ctypes.c_float, _int, _int, _vp, _vp, _vp, _vp, _vp]),
+    ("mls_knn_project_sorted", _int, [_vp, _int, ctypes.c_float, _int, _int, _vp, _vp, _vp, _vp, _vp, _vp]),
     ("mls_project_backward_sorted", _int, [_vp, _vp, _int, ctypes.c_float, _int, _int, _vp, _vp, _vp, _vp, _vp,
                                            _vp]),
     ("mls_project", _int, [_vp, _i64, _vp, _int, _flt, _int, _int, _vp, _vp, _vp, _vp, _vp]),
@@ -304,6 +305,34 @@ def mls_knn_project(grid: Grid, k: int, h: float, degree: int = 2, precision: st
                                _stream(stream))
     _check("mls_knn_project", rc)
     return (out_xyz, out_normal, out_status, out_pos) if with_pos else (out_xyz, out_normal, out_status)
+
+
+def mls_knn_project_sorted(grid: Grid, k: int, h: float, degree: int = 2, precision: str = "mixed",
+                           out_pos=None, out_xyz=None, out_normal=None, out_status=None, with_state: bool = False,
+                           out_state=None, stream=None):
+    """mls_knn_sorted and mls_project_sorted pipelined (the projection of the
+    points the kNN's first pass finished runs beside its second pass): (pos,
+    xyz, normal, status[, state]), the outputs of the two calls."""
+    n = grid.n
+    dev = grid.xyz.device
+    out_pos = torch.empty((n, k), dtype=torch.int32, device=dev) if out_pos is None else out_pos
+    out_xyz = torch.empty((n, 3), dtype=torch.float32, device=dev) if out_xyz is None else out_xyz
+    out_normal = torch.empty((n, 3), dtype=torch.float32, device=dev) if out_normal is None else out_normal
+    out_status = torch.empty(n, dtype=torch.uint8, device=dev) if out_status is None else out_status
+    _need(out_pos, "out_pos", torch.int32, (n, k))
+    _need(out_xyz, "out_xyz", torch.float32, (n, 3))
+    _need(out_normal, "out_normal", torch.float32, (n, 3))
+    _need(out_status, "out_status", torch.uint8, (n,))
+    if with_state:
+        out_state = torch.empty((FIT_STATE_FLOATS, n), dtype=torch.float32, device=dev) if out_state is None \
+            else out_state
+        _need(out_state, "out_state", torch.float32, (FIT_STATE_FLOATS, n))
+    rc = lib().mls_knn_project_sorted(grid.handle, int(k), float(h), int(degree), PRECISION[precision], _ptr(out_pos),
+                                      _ptr(out_xyz), _ptr(out_normal), _ptr(out_status),
+                                      _ptr(out_state) if with_state else None, _stream(stream))
+    _check("mls_knn_project_sorted", rc)
+    res = (out_pos, out_xyz, out_normal, out_status)
+    return res + (out_state,) if with_state else res
 
 
 def mls_project_backward_sorted(grid: Grid, pos: torch.Tensor, h: float, gout_xyz: torch.Tensor,

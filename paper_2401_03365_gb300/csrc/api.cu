@@ -15,6 +15,8 @@ int launch_knn(const mls_grid *grid, int k, int32_t *idx, float *key, int32_t *p
 int launch_project_sorted(const float4 *pts, int64_t n, const int32_t *pos, int k, float h, int degree,
                           int precision, float *out_xyz, float *out_n, uint8_t *status, float *state,
                           cudaStream_t st);
+int launch_knn_project_sorted(const mls_grid *g, int k, float h, int degree, int precision, int32_t *pos,
+                              float *out_xyz, float *out_n, uint8_t *status, float *state, cudaStream_t st);
 int launch_knn_project(const mls_grid *grid, int k, float h, int degree, int precision, float *out_xyz,
                        float *out_n, uint8_t *status, int32_t *pos, cudaStream_t st);
 int launch_points_in_boxes(const mls_grid *grid, const float *boxes, int64_t m, uint8_t *mask, cudaStream_t st);
@@ -253,6 +255,27 @@ int mls_knn_project(const mls_grid *g, int k, float h, int degree, int precision
         return set_error(MLS_ERR_INVALID_ARG, "mls_knn_project: output aliases the grid's points");
     return mls::launch_knn_project(g, k, h, degree, precision, d_out_xyz, d_out_normal, d_status, d_pos,
                                    (cudaStream_t)stream);
+}
+
+int mls_knn_project_sorted(const mls_grid *g, int k, float h, int degree, int precision, int32_t *d_pos,
+                           float *d_out_xyz, float *d_out_normal, uint8_t *d_status, float *d_state,
+                           mls_stream stream) {
+    mls::g_last_error[0] = 0;
+    if (!g || !d_pos || !d_out_xyz) return set_error(MLS_ERR_INVALID_ARG, "mls_knn_project_sorted: null pointer");
+    if (g->n < 1) return set_error(MLS_ERR_INVALID_ARG, "mls_knn_project_sorted: grid is empty (failed build?)");
+    if (k < 1 || k > MLS_MAX_K || k > g->n)
+        return set_error(MLS_ERR_K_TOO_LARGE, "mls_knn_project_sorted: k = %d not in [1, min(%d, n = %lld)]", k,
+                         MLS_MAX_K, (long long)g->n);
+    if (!(h > 0.0f) || !std::isfinite(h))
+        return set_error(MLS_ERR_INVALID_ARG, "mls_knn_project_sorted: h = %g must be finite and > 0", (double)h);
+    if (degree < 0 || degree > 2)
+        return set_error(MLS_ERR_UNSUPPORTED_DEGREE, "mls_knn_project_sorted: degree = %d not in {0, 1, 2}", degree);
+    if (precision != MLS_PREC_FP32 && precision != MLS_PREC_MIXED)
+        return set_error(MLS_ERR_INVALID_ARG, "mls_knn_project_sorted: precision = %d (FP32 or mixed)", precision);
+    if ((const void *)d_out_xyz == (const void *)g->xyz)
+        return set_error(MLS_ERR_INVALID_ARG, "mls_knn_project_sorted: output aliases the grid's points");
+    return mls::launch_knn_project_sorted(g, k, h, degree, precision, d_pos, d_out_xyz, d_out_normal, d_status,
+                                          d_state, (cudaStream_t)stream);
 }
 
 int64_t mls_knn_deferred(const mls_grid *g, mls_stream stream) {

@@ -426,6 +426,16 @@ int blocks_for(int64_t n, int threads, int per_sm = 16) {
 }  // namespace
 
 void free_grid_buffers(mls_grid *g) {
+    if (g->side) cudaStreamSynchronize(g->side);
+    for (cudaEvent_t &e : g->side_ev)
+        if (e) {
+            cudaEventDestroy(e);
+            e = nullptr;
+        }
+    if (g->side) {
+        cudaStreamDestroy(g->side);
+        g->side = nullptr;
+    }
     cudaFree(g->mkeys);
     cudaFree(g->keys);
     cudaFree(g->keys_alt);

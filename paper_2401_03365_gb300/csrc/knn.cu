@@ -59,16 +59,17 @@ __global__ void __launch_bounds__(kChainThreads) k_radius(GridView g, float R2, 
 
 }  // namespace
 
-int launch_knn(const mls_grid *grid, int k, int32_t *idx, float *key, int32_t *pos, cudaStream_t st) {
+// The kNN's two passes, for callers that put work between them: the chain
+// pass (queries in sparse neighbourhoods listed in grid->work), then the
+// sparse pass over that list (blocks_per_sm > 0: that many blocks per SM
+// instead of a full wave, leaving room for other work beside it).
+int launch_knn_chain_pass(const mls_grid *grid, int k, int32_t *idx, float *key, int32_t *pos, cudaStream_t st) {
     const int64_t n = grid->n;
     const int sms = sm_count();
     auto chain = k <= 32 ? k_knn_chain<1, PlainRows> : k_knn_chain<2, PlainRows>;
-    auto sparse = k <= 32 ? k_knn_sparse<1, PlainRows> : k_knn_sparse<2, PlainRows>;
     // all shared memory to the carveout, so that every block the registers
     // allow is resident; one resident wave of blocks, queries taken dynamically
     MLS_CUDA_TRY(cudaFuncSetAttribute(chain, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                      cudaSharedmemCarveoutMaxShared));
-    MLS_CUDA_TRY(cudaFuncSetAttribute(sparse, cudaFuncAttributePreferredSharedMemoryCarveout,
                                       cudaSharedmemCarveoutMaxShared));
     int per_sm = 1;
     MLS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, chain, kChainThreads, 0));
@@ -77,12 +78,32 @@ int launch_knn(const mls_grid *grid, int k, int32_t *idx, float *key, int32_t *p
     const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)sms * per_sm,
                                                                     (runs + kChainWarps - 1) / kChainWarps));
     MLS_CUDA_TRY(cudaMemsetAsync(grid->work, 0, 8 * sizeof(int), st));
-    const RowOut out{idx, key, pos};
-    chain<<<blocks, kChainThreads, 0, st>>>(grid->view, k, grid->work, out, PlainRows{});
-    sparse<<<sms * per_sm, kChainThreads, 0, st>>>(grid->view, k, grid->work, out, PlainRows{});
-    count_launches(2);
+    chain<<<blocks, kChainThreads, 0, st>>>(grid->view, k, grid->work, RowOut{idx, key, pos}, PlainRows{});
+    count_launches(1);
     MLS_CUDA_TRY(cudaGetLastError());
     return MLS_OK;
+}
+
+int launch_knn_sparse_pass(const mls_grid *grid, int k, int32_t *idx, float *key, int32_t *pos, cudaStream_t st,
+                           int blocks_per_sm) {
+    const int sms = sm_count();
+    auto chain = k <= 32 ? k_knn_chain<1, PlainRows> : k_knn_chain<2, PlainRows>;
+    auto sparse = k <= 32 ? k_knn_sparse<1, PlainRows> : k_knn_sparse<2, PlainRows>;
+    MLS_CUDA_TRY(cudaFuncSetAttribute(sparse, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                      cudaSharedmemCarveoutMaxShared));
+    int per_sm = 1;
+    MLS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, chain, kChainThreads, 0));
+    per_sm = blocks_per_sm > 0 ? blocks_per_sm : std::max(per_sm, 1);
+    sparse<<<sms * per_sm, kChainThreads, 0, st>>>(grid->view, k, grid->work, RowOut{idx, key, pos}, PlainRows{});
+    count_launches(1);
+    MLS_CUDA_TRY(cudaGetLastError());
+    return MLS_OK;
+}
+
+int launch_knn(const mls_grid *grid, int k, int32_t *idx, float *key, int32_t *pos, cudaStream_t st) {
+    const int rc = launch_knn_chain_pass(grid, k, idx, key, pos, st);
+    if (rc != MLS_OK) return rc;
+    return launch_knn_sparse_pass(grid, k, idx, key, pos, st, 0);
 }
 
 }  // namespace mls

@@ -10,6 +10,7 @@
 #include <cmath>
 #include <mutex>
 
+#include "grid.cuh"
 #include "project_point.cuh"
 
 namespace mls {
@@ -38,8 +39,10 @@ __global__ void k_pack_xyz4(const float *__restrict__ xyz, int64_t n, float4 *__
 // original index bits), slot s is sorted position s, idx holds the rows of
 // sorted positions by sorted position, and each result goes to the point's
 // original index.  With STATE (SORTED only) each point's fit state goes to
-// state[c * n + slot] (FitState).
-template <int DEG, int PREC, bool LEVIN = false, bool DEFER = false, bool SORTED = false, bool STATE = false>
+// state[c * n + slot] (FitState).  With SKIP, slots with skip[slot] != 0 are
+// left alone (their rows are not written yet).
+template <int DEG, int PREC, bool LEVIN = false, bool DEFER = false, bool SORTED = false, bool STATE = false,
+          bool SKIP = false>
 __global__ void __launch_bounds__(kProjThreads, LEVIN ? 5 : 8) k_project(const float4 *__restrict__ xyz4, int64_t n,
                                                           const int32_t *__restrict__ idx, int k, float h,
                                                           const int32_t *__restrict__ order,
@@ -47,7 +50,8 @@ __global__ void __launch_bounds__(kProjThreads, LEVIN ? 5 : 8) k_project(const f
                                                           uint8_t *__restrict__ status, int max_iter,
                                                           float tol, int32_t *__restrict__ deferred,
                                                           int32_t *__restrict__ n_deferred,
-                                                          float *__restrict__ state = nullptr) {
+                                                          float *__restrict__ state = nullptr,
+                                                          const uint8_t *__restrict__ skip = nullptr) {
     extern __shared__ int32_t rows[];
     const int lane = threadIdx.x & 31;
     int32_t *my_rows = rows + (threadIdx.x >> 5) * k * kRowStride;
@@ -63,6 +67,7 @@ __global__ void __launch_bounds__(kProjThreads, LEVIN ? 5 : 8) k_project(const f
     }
     __syncwarp();
     if (slot >= n) return;
+    if (SKIP && __ldg(skip + slot)) return;
     const float4 r4 = __ldg(xyz4 + i);
     float out[3], nf[3];
     const uint8_t st = project_point<DEG, PREC, LEVIN, DEFER, STATE>(
@@ -88,7 +93,7 @@ __global__ void __launch_bounds__(kProjThreads, LEVIN ? 5 : 8) k_project(const f
 // with its FP64 steps, rows read from global memory (same values and order
 // as the first pass, so the results are those of a single pass).  SORTED and
 // STATE as in k_project.
-template <int DEG, bool SORTED = false, bool STATE = false>
+template <int DEG, bool SORTED = false, bool STATE = false, int PREC = MLS_PREC_MIXED>
 __global__ void __launch_bounds__(kProjThreads) k_project_deferred(const float4 *__restrict__ xyz4, int64_t n,
                                                                   const int32_t *__restrict__ idx, int k, float h,
                                                                   const int32_t *__restrict__ order,
@@ -105,7 +110,7 @@ __global__ void __launch_bounds__(kProjThreads) k_project_deferred(const float4 
         const int32_t *row = idx + i * k;
         const float4 r4 = __ldg(xyz4 + i);
         float out[3], nf[3];
-        const uint8_t st = project_point<DEG, MLS_PREC_MIXED, false, false, STATE>(
+        const uint8_t st = project_point<DEG, PREC, false, false, STATE>(
             xyz4, [&](int j) { return __ldg(row + j); }, k, 0, 1, h, r4.x, r4.y, r4.z, out, nf, 1, 0.f,
             STATE ? state + slot : nullptr, n);
         const int64_t o = SORTED ? (int64_t)__float_as_int(r4.w) : i;
@@ -282,7 +287,7 @@ int launch_deg(const float *xyz, int64_t n, const int32_t *idx, int k, float h, 
             auto kern = k_project<DEG, MLS_PREC_MIXED, false, true>;
             MLS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
             kern<<<blocks, kProjThreads, smem, st>>>(xyz4, n, idx, k, h, order, out_xyz, out_n, status, 1, 0.f,
-                                                     deferred, n_deferred, nullptr);
+                                                     deferred, n_deferred, nullptr, nullptr);
             k_project_deferred<DEG><<<sm_count() * 2, kProjThreads, 0, st>>>(xyz4, n, idx, k, h, order, deferred, n_deferred,
                                                                      out_xyz, out_n, status);
             count_launches(3);
@@ -290,7 +295,7 @@ int launch_deg(const float *xyz, int64_t n, const int32_t *idx, int k, float h, 
             auto kern = k_project<DEG, MLS_PREC_FP32>;
             MLS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
             kern<<<blocks, kProjThreads, smem, st>>>(xyz4, n, idx, k, h, order, out_xyz, out_n, status, 1, 0.f,
-                                                     nullptr, nullptr, nullptr);
+                                                     nullptr, nullptr, nullptr, nullptr);
             count_launches(2);
         }
     }
@@ -331,7 +336,7 @@ int launch_sorted_deg(const float4 *pts, int64_t n, const int32_t *pos, int k, f
         auto kern = k_project<DEG, MLS_PREC_MIXED, false, true, true, STATE>;
         MLS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         kern<<<blocks, kProjThreads, smem, st>>>(pts, n, pos, k, h, nullptr, out_xyz, out_n, status, 1, 0.f,
-                                                 deferred, n_deferred, state);
+                                                 deferred, n_deferred, state, nullptr);
         k_project_deferred<DEG, true, STATE><<<sm_count() * 2, kProjThreads, 0, st>>>(
             pts, n, pos, k, h, nullptr, deferred, n_deferred, out_xyz, out_n, status, state);
         count_launches(2);
@@ -339,7 +344,7 @@ int launch_sorted_deg(const float4 *pts, int64_t n, const int32_t *pos, int k, f
         auto kern = k_project<DEG, MLS_PREC_FP32, false, false, true, STATE>;
         MLS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         kern<<<blocks, kProjThreads, smem, st>>>(pts, n, pos, k, h, nullptr, out_xyz, out_n, status, 1, 0.f,
-                                                 nullptr, nullptr, state);
+                                                 nullptr, nullptr, state, nullptr);
         count_launches(1);
     }
     MLS_CUDA_TRY(cudaGetLastError());
@@ -410,12 +415,12 @@ int launch_levin_deg(const float *xyz, int64_t n, const int32_t *idx, int k, flo
         auto kern = k_project<DEG, MLS_PREC_MIXED, true>;
         MLS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         kern<<<blocks, kProjThreads, smem, st>>>(xyz4, n, idx, k, h, order, out_xyz, out_n, status, max_iter, tol,
-                                                 nullptr, nullptr, nullptr);
+                                                 nullptr, nullptr, nullptr, nullptr);
     } else {
         auto kern = k_project<DEG, MLS_PREC_FP32, true>;
         MLS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         kern<<<blocks, kProjThreads, smem, st>>>(xyz4, n, idx, k, h, order, out_xyz, out_n, status, max_iter, tol,
-                                                 nullptr, nullptr, nullptr);
+                                                 nullptr, nullptr, nullptr, nullptr);
     }
     count_launches(2);
     MLS_CUDA_TRY(cudaGetLastError());
@@ -487,12 +492,12 @@ int launch_noalloc(const float *xyz, int64_t n, const int32_t *idx, int k, float
             auto kern = k_project<DEG, MLS_PREC_MIXED>;
             MLS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
             kern<<<blocks, kProjThreads, smem, st>>>(xyz4, n, idx, k, h, order, out_xyz, out_n, status, 1, 0.f,
-                                                     nullptr, nullptr, nullptr);
+                                                     nullptr, nullptr, nullptr, nullptr);
         } else {
             auto kern = k_project<DEG, MLS_PREC_FP32>;
             MLS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
             kern<<<blocks, kProjThreads, smem, st>>>(xyz4, n, idx, k, h, order, out_xyz, out_n, status, 1, 0.f,
-                                                     nullptr, nullptr, nullptr);
+                                                     nullptr, nullptr, nullptr, nullptr);
         }
         count_launches(2);
     }
@@ -535,3 +540,97 @@ extern "C" int mls_project_noalloc(const float *d_xyz, int64_t n, const int32_t 
             return mls::launch_noalloc<2>(d_xyz, n, d_idx, k, h, precision, d_order, d_out_xyz, d_out_normal, d_status, st);
     }
 }
+
+namespace mls {
+
+int launch_knn_chain_pass(const mls_grid *grid, int k, int32_t *idx, float *key, int32_t *pos, cudaStream_t st);
+int launch_knn_sparse_pass(const mls_grid *grid, int k, int32_t *idx, float *key, int32_t *pos, cudaStream_t st,
+                           int blocks_per_sm);
+
+namespace {
+
+// The queries the kNN's chain pass left to its sparse pass (the grid's work
+// list): flagged in skip[] and appended to the list of slots projected last.
+__global__ void k_mark_sparse(const int *__restrict__ work, uint8_t *__restrict__ skip, int32_t *__restrict__ list,
+                              int32_t *__restrict__ count) {
+    const int m = work[1];
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
+        const int32_t sp = work[8 + i];
+        skip[sp] = 1;
+        list[atomicAdd(count, 1)] = sp;
+    }
+}
+
+// The kNN and the projection, pipelined: after the chain pass, the kNN's
+// sparse pass (whose tail leaves most of the GPU idle) runs on a
+// high-priority stream of the grid's own while the projection of every point
+// whose row the chain pass wrote runs on the caller's stream beside it; then
+// the points of the sparse pass, and in the mixed form the points that need
+// an FP64 step, are projected from one list.  The same rows and the same
+// per-point arithmetic as mls_knn_sorted followed by mls_project_sorted.
+template <int DEG, int PREC, bool STATE>
+int knn_project_pipelined(const mls_grid *g, int k, float h, int32_t *pos, float *out_xyz, float *out_n,
+                          uint8_t *status, float *state, cudaStream_t st) {
+    const int64_t n = g->n;
+    if (!g->side) {
+        int least = 0, greatest = 0;
+        MLS_CUDA_TRY(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+        MLS_CUDA_TRY(cudaStreamCreateWithPriority(&g->side, cudaStreamNonBlocking, greatest));
+        MLS_CUDA_TRY(cudaEventCreateWithFlags(&g->side_ev[0], cudaEventDisableTiming));
+        MLS_CUDA_TRY(cudaEventCreateWithFlags(&g->side_ev[1], cudaEventDisableTiming));
+    }
+    ScratchSet scratch(st);     // freed on st, after it has waited for the side stream
+    uint8_t *skip = nullptr;
+    int32_t *list = nullptr;
+    MLS_CUDA_TRY(scratch.alloc(&skip, (size_t)n));
+    MLS_CUDA_TRY(scratch.alloc(&list, (size_t)(n + 1) * sizeof(int32_t)));
+    int32_t *count = list + n;
+    MLS_CUDA_TRY(cudaMemsetAsync(skip, 0, (size_t)n, st));
+    MLS_CUDA_TRY(cudaMemsetAsync(count, 0, sizeof(int32_t), st));
+    int rc = launch_knn_chain_pass(g, k, nullptr, nullptr, pos, st);
+    if (rc != MLS_OK) return rc;
+    k_mark_sparse<<<sm_count(), 256, 0, st>>>(g->work, skip, list, count);
+    MLS_CUDA_TRY(cudaEventRecord(g->side_ev[0], st));
+    MLS_CUDA_TRY(cudaStreamWaitEvent(g->side, g->side_ev[0], 0));
+    // a full wave of sparse blocks (fewer, leaving room for the projection
+    // from the start, measured slower: the sparse pass is the longer path)
+    rc = launch_knn_sparse_pass(g, k, nullptr, nullptr, pos, g->side, 0);
+    if (rc != MLS_OK) return rc;
+    MLS_CUDA_TRY(cudaEventRecord(g->side_ev[1], g->side));
+    const int blocks = (int)((n + kProjThreads - 1) / kProjThreads);
+    const size_t smem = (size_t)k * kRowStride * sizeof(int32_t) * (kProjThreads / 32);
+    constexpr bool DEFER = PREC == MLS_PREC_MIXED;
+    auto kern = k_project<DEG, PREC, false, DEFER, true, STATE, true>;
+    MLS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    kern<<<blocks, kProjThreads, smem, st>>>(g->view.pts, n, pos, k, h, nullptr, out_xyz, out_n, status, 1, 0.f,
+                                             list, count, state, skip);
+    MLS_CUDA_TRY(cudaStreamWaitEvent(st, g->side_ev[1], 0));
+    k_project_deferred<DEG, true, STATE, PREC><<<sm_count() * 2, kProjThreads, 0, st>>>(
+        g->view.pts, n, pos, k, h, nullptr, list, count, out_xyz, out_n, status, state);
+    count_launches(3);
+    MLS_CUDA_TRY(cudaGetLastError());
+    return MLS_OK;
+}
+
+template <int PREC, bool STATE>
+int knn_project_deg(const mls_grid *g, int k, float h, int degree, int32_t *pos, float *out_xyz, float *out_n,
+                    uint8_t *status, float *state, cudaStream_t st) {
+    switch (degree) {
+        case 0: return knn_project_pipelined<0, PREC, STATE>(g, k, h, pos, out_xyz, out_n, status, state, st);
+        case 1: return knn_project_pipelined<1, PREC, STATE>(g, k, h, pos, out_xyz, out_n, status, state, st);
+        default: return knn_project_pipelined<2, PREC, STATE>(g, k, h, pos, out_xyz, out_n, status, state, st);
+    }
+}
+
+}  // namespace
+
+int launch_knn_project_sorted(const mls_grid *g, int k, float h, int degree, int precision, int32_t *pos,
+                              float *out_xyz, float *out_n, uint8_t *status, float *state, cudaStream_t st) {
+    if (precision == MLS_PREC_FP32)
+        return state ? knn_project_deg<MLS_PREC_FP32, true>(g, k, h, degree, pos, out_xyz, out_n, status, state, st)
+                     : knn_project_deg<MLS_PREC_FP32, false>(g, k, h, degree, pos, out_xyz, out_n, status, state, st);
+    return state ? knn_project_deg<MLS_PREC_MIXED, true>(g, k, h, degree, pos, out_xyz, out_n, status, state, st)
+                 : knn_project_deg<MLS_PREC_MIXED, false>(g, k, h, degree, pos, out_xyz, out_n, status, state, st);
+}
+
+}  // namespace mls

@@ -260,6 +260,7 @@ def run_ours(args):
     grad = torch.empty_like(x)
     grad_h = torch.empty(1, dtype=torch.float32, device=dev)
     fit_state = torch.empty((capi.FIT_STATE_FLOATS, n_pts), dtype=torch.float32, device=dev)
+    bucket_off = torch.empty(n_pts + 1, dtype=torch.int32, device=dev)
     gen = torch.Generator(device=dev).manual_seed(cot_seed)
     gp = torch.randn((n_pts, 3), generator=gen, device=dev)          # cotangent of the points
     gn = 0.1 * torch.randn((n_pts, 3), generator=gen, device=dev)    # cotangent of the normals
@@ -272,10 +273,11 @@ def run_ours(args):
 
     # one step: grid build, kNN (rows of sorted positions) and the projection
     # saving the fit state, pipelined in one call (the projection of the
-    # points the kNN's first pass finished runs beside its second pass), and
-    # the adjoint from the state with a fixed cotangent, all in the grid's
-    # order.  split=True makes the kNN and the projection two calls, for the
-    # per-stage times.
+    # points the kNN's first pass finished runs beside its second pass, and
+    # the adjoint's bucket offsets are counted beside its tail), and the
+    # adjoint from the state with a fixed cotangent, all in the grid's order.
+    # split=True makes the kNN and the projection two calls and lets the
+    # adjoint count its own offsets, for the per-stage times.
     def step(xin, ev=None, before_forward_out=None, after_forward=None, before_backward=None, split=False):
         nonlocal grid
         if ev: ev[0].record(stream)
@@ -290,13 +292,14 @@ def run_ours(args):
         else:
             if before_forward_out: before_forward_out()
             capi.mls_knn_project_sorted(grid, K, h, 2, "mixed", out_pos=pos, out_xyz=out_xyz, out_normal=out_n,
-                                        out_status=out_st, with_state=True, out_state=fit_state)
+                                        out_status=out_st, with_state=True, out_state=fit_state,
+                                        out_offsets=bucket_off)
             if ev: ev[2].record(stream)
         if ev: ev[3].record(stream)
         if after_forward: after_forward()
         if before_backward: before_backward()
         capi.mls_project_backward_sorted(grid, pos, h, gp, gn, 2, "mixed", out_grad_xyz=grad, out_grad_h=grad_h,
-                                         state=fit_state)
+                                         state=fit_state, offsets=None if split else bucket_off)
         if ev: ev[4].record(stream)
 
     events = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(args.steps)]
@@ -578,7 +581,7 @@ def stage_kernels(n, k, build_ms, knn_ms, proj_ms, bwd_ms, peaks, mhz):
         "project": {"ms": proj_ms, "calls": "mls_project_sorted (k_project + k_project_deferred), fit state saved", "bound": "alu",
                     "flops_per_point": proj_flops(k, state=True), "achieved_tflops": proj_tf,
                     "frac": proj_tf / peaks["fp32_tflops"]},
-        "backward": {"ms": bwd_ms, "calls": "mls_project_backward_sorted from the saved fit state (counts, scan, adjoint, bucket sums)",
+        "backward": {"ms": bwd_ms, "calls": "mls_project_backward_sorted from the saved fit state and the bucket offsets of the pipelined call (adjoint, bucket sums)",
                      "bound": "alu", "flops_per_point": bwd_flops(k, state=True), "achieved_tflops": bwd_tf,
                      "frac": bwd_tf / peaks["fp32_tflops"]},
         "fp32_peak_tflops": peaks["fp32_tflops"],

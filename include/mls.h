@@ -219,10 +219,16 @@ int mls_knn_project(const mls_grid *g, int k, float h, int degree, int precision
  * the first call and destroyed with the grid; `stream` waits for the side
  * stream before the call's last kernel, so the call is ordered on `stream`
  * like any other.
+ *   d_offsets  device, n + 1 int32, or NULL: also the offsets of the
+ *              adjoint's reverse adjacency of these rows (d_offsets[t] = how
+ *              many row entries name sorted positions below t), counted on
+ *              the side stream once the rows are complete, for
+ *              mls_project_backward_sorted; MLS_ERR_TOO_LARGE when n k does
+ *              not fit an int32.
  */
 int mls_knn_project_sorted(const mls_grid *g, int k, float h, int degree, int precision, int32_t *d_pos,
                            float *d_out_xyz, float *d_out_normal, uint8_t *d_status, float *d_state,
-                           mls_stream stream);
+                           int32_t *d_offsets, mls_stream stream);
 
 /* Number of queries the last mls_knn call on this grid handed to its second
  * pass (queries whose first key bound needs a cube above the base level:
@@ -381,10 +387,14 @@ int mls_project_backward(const float *d_xyz, int64_t n, const int32_t *d_idx, in
  *            passes over the neighbours and the solves): the gradients then
  *            differ from the recomputing form only by rounding (the saved
  *            coefficients carry the forward's refinement step).
+ *   d_offsets  device, n + 1 int32, or NULL: the bucket offsets
+ *            mls_knn_project_sorted counted for these rows (else counted
+ *            here); the gradients do not depend on it.
  */
 int mls_project_backward_sorted(const mls_grid *g, const int32_t *d_pos, int k, float h, int degree, int precision,
                                 const float *d_grad_out_xyz, const float *d_grad_out_normal, float *d_grad_xyz,
-                                float *d_grad_h, const float *d_state, mls_stream stream);
+                                float *d_grad_h, const float *d_state, const int32_t *d_offsets,
+                                mls_stream stream);
 
 /*
  * mls_mean_knn_dist -- bandwidth helper (not in the paper): the mean distance,

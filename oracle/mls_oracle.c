@@ -28,8 +28,9 @@
  *     largest magnitude is positive (ties: lowest axis);
  *   - polynomial = full bivariate basis of the requested degree (0, 1, 2) in
  *     coordinates (u, v) scaled by 1/h; heights f are not scaled;
- *   - degenerate plane ((l1 - l0) <= 1e-6 l2, or l2 == 0): output r and the
- *     computed normal, status bit 1; singular polynomial system (a Cholesky
+ *   - degenerate plane ((l1 - l0) <= 1e-6 l2, or l2 <= 2^-40 D^2 with the
+ *     covariance normalised by W and D the largest distance from r to a row
+ *     entry): output r and the computed normal, status bit 1; singular polynomial system (a Cholesky
  *     pivot <= 1e-12 trace): output q, status bit 2.
  *
  * Every computation after the neighbour ranking runs in double precision on
@@ -42,6 +43,14 @@
 #include <string.h>
 
 #define ST_PLANE_DEGENERATE 1
+
+/* Reading R9: a plane whose weighted covariance (normalised by W) has its
+ * largest eigenvalue at most 2^-40 D^2, D the largest distance from the point
+ * to an entry of its row, is degenerate as well: the neighbours' weights are
+ * then negligible beside the point's own (all of them many h away), and the
+ * plane they would define is not resolved by the weights' precision.  Such a
+ * point stays where it is. */
+#define PLANE_MIN_SPREAD 0x1p-40
 #define ST_POLY_SINGULAR 2
 
 /* ------------------------------------------------------------------------- */
@@ -520,7 +529,7 @@ static void project_point(const float *xyz, const int32_t *row, int k, double h,
     for (int a = 0; a < 3; ++a) st->r[a] = (double)xyz[3 * i + a];
     /* weights about r (Eq. 1's theta, Gaussian) */
     st->W = 0.0;
-    double sw[3] = {0, 0, 0};
+    double sw[3] = {0, 0, 0}, D2 = 0.0;
     for (int j = 0; j < k; ++j) {
         int64_t p = row[j];
         double d2 = 0.0;
@@ -529,6 +538,7 @@ static void project_point(const float *xyz, const int32_t *row, int k, double h,
             st->d[3 * j + a] = st->P[3 * j + a] - st->r[a];
             d2 += st->d[3 * j + a] * st->d[3 * j + a];
         }
+        if (d2 > D2) D2 = d2;
         st->w[j] = exp(-d2 / (h * h));
         st->W += st->w[j];
         for (int a = 0; a < 3; ++a) sw[a] += st->w[j] * st->d[3 * j + a];
@@ -559,7 +569,7 @@ static void project_point(const float *xyz, const int32_t *row, int k, double h,
     st->e2[2] = st->nrm[0] * st->e1[1] - st->nrm[1] * st->e1[0];
     memset(st->a, 0, sizeof st->a);
     st->cond = 0.0;
-    if (!(st->lam[2] > 0.0) || (st->lam[1] - st->lam[0]) <= 1e-6 * st->lam[2]) {
+    if (!(st->lam[2] > PLANE_MIN_SPREAD * D2) || (st->lam[1] - st->lam[0]) <= 1e-6 * st->lam[2]) {
         st->status = ST_PLANE_DEGENERATE;
         for (int a = 0; a < 3; ++a) st->out[a] = st->r[a];
         st->ofs = 0.0;
@@ -859,8 +869,15 @@ int oracle_project_levin(const float *xyz, int64_t n, const int32_t *idx, int k,
         const int32_t *row = idx + s * k;
         double r[3], q[3], nrm[3] = {0, 0, 0}, e1[3] = {0, 0, 0}, e2[3] = {0, 0, 0};
         for (int a = 0; a < 3; ++a) r[a] = q[a] = (double)xyz[3 * i + a];
-        for (int j = 0; j < k; ++j)
-            for (int a = 0; a < 3; ++a) P[3 * j + a] = (double)xyz[3 * (int64_t)row[j] + a];
+        double D2 = 0.0;     /* the largest squared distance from r to a row entry (R9) */
+        for (int j = 0; j < k; ++j) {
+            double d2 = 0.0;
+            for (int a = 0; a < 3; ++a) {
+                P[3 * j + a] = (double)xyz[3 * (int64_t)row[j] + a];
+                d2 += (P[3 * j + a] - r[a]) * (P[3 * j + a] - r[a]);
+            }
+            if (d2 > D2) D2 = d2;
+        }
         int status = ST_NOT_CONVERGED, iters = 0;
         double t = 0.0, last_lam[3] = {0, 0, 0}, last_W = 0.0, cond = 0.0;
         for (int it = 0; it < max_iter; ++it) {
@@ -895,7 +912,7 @@ int oracle_project_levin(const float *xyz, int64_t n, const int32_t *idx, int k,
             e2[2] = nrm[0] * e1[1] - nrm[1] * e1[0];
             for (int a = 0; a < 3; ++a) last_lam[a] = lam[a];
             last_W = W;
-            if (!(lam[2] > 0.0) || (lam[1] - lam[0]) <= 1e-6 * lam[2]) {
+            if (!(lam[2] > PLANE_MIN_SPREAD * D2) || (lam[1] - lam[0]) <= 1e-6 * lam[2]) {
                 status = ST_PLANE_DEGENERATE;
                 break;
             }

@@ -51,9 +51,9 @@ _SIGNATURES = [
     ("mls_knn_sorted", _int, [_vp, _int, _vp, _vp, _vp, _vp]),
     ("mls_project_sorted", _int, [_vp, _vp, _int, ctypes.c_float, _int, _int, _vp, _vp, _vp, _vp, _vp]),
     ("mls_knn_project", _int, [_vp, _int, ctypes.c_float, _int, _int, _vp, _vp, _vp, _vp, _vp]),
-    ("mls_knn_project_sorted", _int, [_vp, _int, ctypes.c_float, _int, _int, _vp, _vp, _vp, _vp, _vp, _vp]),
+    ("mls_knn_project_sorted", _int, [_vp, _int, ctypes.c_float, _int, _int, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     ("mls_project_backward_sorted", _int, [_vp, _vp, _int, ctypes.c_float, _int, _int, _vp, _vp, _vp, _vp, _vp,
-                                           _vp]),
+                                           _vp, _vp]),
     ("mls_project", _int, [_vp, _i64, _vp, _int, _flt, _int, _int, _vp, _vp, _vp, _vp, _vp]),
     ("mls_project_noalloc", _int, [_vp, _i64, _vp, _int, _flt, _int, _int, _vp, _vp, _vp, _vp, _vp]),
     ("mls_project_levin", _int, [_vp, _i64, _vp, _int, _flt, _int, _int, _int, _flt, _vp, _vp, _vp, _vp, _vp]),
@@ -309,10 +309,11 @@ def mls_knn_project(grid: Grid, k: int, h: float, degree: int = 2, precision: st
 
 def mls_knn_project_sorted(grid: Grid, k: int, h: float, degree: int = 2, precision: str = "mixed",
                            out_pos=None, out_xyz=None, out_normal=None, out_status=None, with_state: bool = False,
-                           out_state=None, stream=None):
+                           out_state=None, out_offsets=None, stream=None):
     """mls_knn_sorted and mls_project_sorted pipelined (the projection of the
     points the kNN's first pass finished runs beside its second pass): (pos,
-    xyz, normal, status[, state]), the outputs of the two calls."""
+    xyz, normal, status[, state]), the outputs of the two calls; with
+    `out_offsets` (n + 1 int32) also the adjoint's bucket offsets."""
     n = grid.n
     dev = grid.xyz.device
     out_pos = torch.empty((n, k), dtype=torch.int32, device=dev) if out_pos is None else out_pos
@@ -327,9 +328,11 @@ def mls_knn_project_sorted(grid: Grid, k: int, h: float, degree: int = 2, precis
         out_state = torch.empty((FIT_STATE_FLOATS, n), dtype=torch.float32, device=dev) if out_state is None \
             else out_state
         _need(out_state, "out_state", torch.float32, (FIT_STATE_FLOATS, n))
+    if out_offsets is not None:
+        _need(out_offsets, "out_offsets", torch.int32, (n + 1,))
     rc = lib().mls_knn_project_sorted(grid.handle, int(k), float(h), int(degree), PRECISION[precision], _ptr(out_pos),
                                       _ptr(out_xyz), _ptr(out_normal), _ptr(out_status),
-                                      _ptr(out_state) if with_state else None, _stream(stream))
+                                      _ptr(out_state) if with_state else None, _ptr(out_offsets), _stream(stream))
     _check("mls_knn_project_sorted", rc)
     res = (out_pos, out_xyz, out_normal, out_status)
     return res + (out_state,) if with_state else res
@@ -337,7 +340,8 @@ def mls_knn_project_sorted(grid: Grid, k: int, h: float, degree: int = 2, precis
 
 def mls_project_backward_sorted(grid: Grid, pos: torch.Tensor, h: float, gout_xyz: torch.Tensor,
                                 gout_normal: torch.Tensor | None = None, degree: int = 2, precision: str = "mixed",
-                                out_grad_xyz=None, out_grad_h=None, stream=None, state: torch.Tensor | None = None):
+                                out_grad_xyz=None, out_grad_h=None, stream=None, state: torch.Tensor | None = None,
+                                offsets: torch.Tensor | None = None):
     """mls_project_backward over the grid's sorted points and mls_knn_sorted's
     rows: (dL/dxyz (n, 3), dL/dh (1,)) in the original order.  `state`: the
     fit state mls_project_sorted saved (then not recomputed)."""
@@ -350,6 +354,8 @@ def mls_project_backward_sorted(grid: Grid, pos: torch.Tensor, h: float, gout_xy
         _need(gout_normal, "gout_normal", torch.float32, (n, 3))
     if state is not None:
         _need(state, "state", torch.float32, (FIT_STATE_FLOATS, n))
+    if offsets is not None:
+        _need(offsets, "offsets", torch.int32, (n + 1,))
     dev = grid.xyz.device
     out_grad_xyz = torch.empty((n, 3), dtype=torch.float32, device=dev) if out_grad_xyz is None else out_grad_xyz
     out_grad_h = torch.empty(1, dtype=torch.float32, device=dev) if out_grad_h is None else out_grad_h
@@ -357,7 +363,8 @@ def mls_project_backward_sorted(grid: Grid, pos: torch.Tensor, h: float, gout_xy
     _need(out_grad_h, "out_grad_h", torch.float32, (1,))
     rc = lib().mls_project_backward_sorted(grid.handle, _ptr(pos), pos.shape[1], float(h), int(degree),
                                            PRECISION[precision], _ptr(gout_xyz), _ptr(gout_normal),
-                                           _ptr(out_grad_xyz), _ptr(out_grad_h), _ptr(state), _stream(stream))
+                                           _ptr(out_grad_xyz), _ptr(out_grad_h), _ptr(state), _ptr(offsets),
+                                           _stream(stream))
     _check("mls_project_backward_sorted", rc)
     return out_grad_xyz, out_grad_h
 

@@ -16,13 +16,14 @@ int launch_project_sorted(const float4 *pts, int64_t n, const int32_t *pos, int 
                           int precision, float *out_xyz, float *out_n, uint8_t *status, float *state,
                           cudaStream_t st);
 int launch_knn_project_sorted(const mls_grid *g, int k, float h, int degree, int precision, int32_t *pos,
-                              float *out_xyz, float *out_n, uint8_t *status, float *state, cudaStream_t st);
+                              float *out_xyz, float *out_n, uint8_t *status, float *state, int32_t *offsets,
+                              cudaStream_t st);
 int launch_knn_project(const mls_grid *grid, int k, float h, int degree, int precision, float *out_xyz,
                        float *out_n, uint8_t *status, int32_t *pos, cudaStream_t st);
 int launch_points_in_boxes(const mls_grid *grid, const float *boxes, int64_t m, uint8_t *mask, cudaStream_t st);
 int launch_backward_sorted(const float4 *pts, const int32_t *order, int64_t n, const int32_t *rows, int k, float h,
                            int degree, int precision, const float *gp, const float *gn, float *grad_xyz,
-                           float *grad_h, const float *state, cudaStream_t st);
+                           float *grad_h, const float *state, const int32_t *offsets, cudaStream_t st);
 int launch_project(const float *xyz, int64_t n, const int32_t *idx, int k, float h, int degree, int precision,
                    const int32_t *order, float *out_xyz, float *out_n, uint8_t *status, cudaStream_t st);
 int launch_radius(const mls_grid *grid, float R2, int32_t *count, const int64_t *offsets, int32_t *rows,
@@ -259,7 +260,7 @@ int mls_knn_project(const mls_grid *g, int k, float h, int degree, int precision
 
 int mls_knn_project_sorted(const mls_grid *g, int k, float h, int degree, int precision, int32_t *d_pos,
                            float *d_out_xyz, float *d_out_normal, uint8_t *d_status, float *d_state,
-                           mls_stream stream) {
+                           int32_t *d_offsets, mls_stream stream) {
     mls::g_last_error[0] = 0;
     if (!g || !d_pos || !d_out_xyz) return set_error(MLS_ERR_INVALID_ARG, "mls_knn_project_sorted: null pointer");
     if (g->n < 1) return set_error(MLS_ERR_INVALID_ARG, "mls_knn_project_sorted: grid is empty (failed build?)");
@@ -274,8 +275,11 @@ int mls_knn_project_sorted(const mls_grid *g, int k, float h, int degree, int pr
         return set_error(MLS_ERR_INVALID_ARG, "mls_knn_project_sorted: precision = %d (FP32 or mixed)", precision);
     if ((const void *)d_out_xyz == (const void *)g->xyz)
         return set_error(MLS_ERR_INVALID_ARG, "mls_knn_project_sorted: output aliases the grid's points");
+    if (d_offsets && g->n > 0x7fffffffLL / MLS_MAX_K)
+        return set_error(MLS_ERR_TOO_LARGE, "mls_knn_project_sorted: n = %lld too large for the offsets",
+                         (long long)g->n);
     return mls::launch_knn_project_sorted(g, k, h, degree, precision, d_pos, d_out_xyz, d_out_normal, d_status,
-                                          d_state, (cudaStream_t)stream);
+                                          d_state, d_offsets, (cudaStream_t)stream);
 }
 
 int64_t mls_knn_deferred(const mls_grid *g, mls_stream stream) {
@@ -430,7 +434,8 @@ int mls_project_backward(const float *d_xyz, int64_t n, const int32_t *d_idx, in
 
 int mls_project_backward_sorted(const mls_grid *g, const int32_t *d_pos, int k, float h, int degree, int precision,
                                 const float *d_grad_out_xyz, const float *d_grad_out_normal, float *d_grad_xyz,
-                                float *d_grad_h, const float *d_state, mls_stream stream) {
+                                float *d_grad_h, const float *d_state, const int32_t *d_offsets,
+                                mls_stream stream) {
     mls::g_last_error[0] = 0;
     if (!g || !d_pos || !d_grad_out_xyz || !d_grad_xyz || !d_grad_h)
         return set_error(MLS_ERR_INVALID_ARG, "mls_project_backward_sorted: null pointer");
@@ -450,7 +455,8 @@ int mls_project_backward_sorted(const mls_grid *g, const int32_t *d_pos, int k, 
     if ((const void *)d_grad_xyz == (const void *)g->xyz || (const void *)d_grad_xyz == (const void *)d_grad_out_xyz)
         return set_error(MLS_ERR_INVALID_ARG, "mls_project_backward_sorted: output aliases an input");
     return mls::launch_backward_sorted(g->view.pts, g->perm, g->n, d_pos, k, h, degree, precision, d_grad_out_xyz,
-                                       d_grad_out_normal, d_grad_xyz, d_grad_h, d_state, (cudaStream_t)stream);
+                                       d_grad_out_normal, d_grad_xyz, d_grad_h, d_state, d_offsets,
+                                       (cudaStream_t)stream);
 }
 
 int mls_points_in_boxes(const mls_grid *g, const float *d_boxes, int64_t m, uint8_t *d_mask, mls_stream stream) {

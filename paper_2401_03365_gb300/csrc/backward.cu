@@ -143,10 +143,13 @@ __global__ void __launch_bounds__(kBwdThreads, 6) k_backward_point(
         } else {
         // ---- forward recompute: weights, centroid offset, covariance ----
         float C[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        float D2 = 0.f;     // the largest squared distance to a row entry
         for (int j = 0; j < k; ++j) {
             const float4 p = __ldg(xyz4 + my_rows[j * kRowStride + lane]);
             const float d[3] = {p.x - rx, p.y - ry, p.z - rz};
-            const float w = exp2f(fmaf(d[0], d[0], fmaf(d[1], d[1], d[2] * d[2])) * neg_scale);
+            const float dd = fmaf(d[0], d[0], fmaf(d[1], d[1], d[2] * d[2]));
+            D2 = fmaxf(D2, dd);
+            const float w = exp2f(dd * neg_scale);
             const float Wn = W + w, c = __fdividef(w, Wn);
             float e[3];
 #pragma unroll
@@ -177,6 +180,7 @@ __global__ void __launch_bounds__(kBwdThreads, 6) k_backward_point(
                 lam[a] = (float)ld[a];
             }
         }
+        if (!(lam[2] > kMinSpread * W * D2)) flag = MLS_PT_PLANE_DEGENERATE;
         }
         const float gp[3] = {gout_xyz[3 * i], gout_xyz[3 * i + 1], gout_xyz[3 * i + 2]};
         float rbar[3] = {gp[0], gp[1], gp[2]};
@@ -634,27 +638,44 @@ int launch_backward(const float *xyz, int64_t n, const int32_t *idx, int k, floa
     return MLS_OK;
 }
 
+// The offsets of the adjoint's reverse adjacency for rows of sorted
+// positions: off[t] = how many row entries name sorted positions below t
+// (n + 1 int32).
+int launch_backward_offsets(const int32_t *rows, int64_t n, int k, int32_t *off, cudaStream_t st) {
+    int32_t *cnt = nullptr;
+    ScratchSet scratch(st);
+    MLS_CUDA_TRY(scratch.alloc(&cnt, (size_t)(n + 1) * sizeof(int32_t)));
+    MLS_CUDA_TRY(cudaMemsetAsync(cnt, 0, (size_t)(n + 1) * sizeof(int32_t), st));
+    k_count_window<true><<<(int)((n + kCountSlots - 1) / kCountSlots), 256, 0, st>>>(rows, n, k, nullptr, nullptr,
+                                                                                      cnt);
+    count_launches(1);
+    MLS_CUDA_TRY(cudaGetLastError());
+    return device_exclusive_scan(cnt, off, n + 1, st);
+}
+
 int launch_backward_sorted(const float4 *pts, const int32_t *order, int64_t n, const int32_t *rows, int k, float h,
                            int degree, int precision, const float *gp, const float *gn, float *grad_xyz,
-                           float *grad_h, const float *state, cudaStream_t st) {
+                           float *grad_h, const float *state, const int32_t *offsets, cudaStream_t st) {
     const int64_t ne = n * (int64_t)k;
     const int blocks = (int)((n + kBwdThreads - 1) / kBwdThreads);
     float4 *rec = nullptr, *self4 = nullptr;
     double *hp = nullptr;
-    int32_t *cnt = nullptr, *off = nullptr;
+    int32_t *fill = nullptr, *own_off = nullptr;
     ScratchSet scratch(st);     // every buffer freed on every return below
     MLS_CUDA_TRY(scratch.alloc(&rec, (size_t)ne * sizeof(float4)));
     MLS_CUDA_TRY(scratch.alloc(&self4, (size_t)n * sizeof(float4)));
     MLS_CUDA_TRY(scratch.alloc(&hp, (size_t)blocks * sizeof(double)));
-    MLS_CUDA_TRY(scratch.alloc(&cnt, (size_t)(2 * n + 2) * sizeof(int32_t)));
-    MLS_CUDA_TRY(scratch.alloc(&off, (size_t)(n + 1) * sizeof(int32_t)));
-    int32_t *fill = cnt + n + 1;
+    MLS_CUDA_TRY(scratch.alloc(&fill, (size_t)(n + 1) * sizeof(int32_t)));
     const int sms = sm_count();
-    MLS_CUDA_TRY(cudaMemsetAsync(cnt, 0, (size_t)(2 * n + 2) * sizeof(int32_t), st));
-    k_count_window<true><<<(int)((n + kCountSlots - 1) / kCountSlots), 256, 0, st>>>(rows, n, k, nullptr, nullptr,
-                                                                                      cnt);
-    int rc = device_exclusive_scan(cnt, off, n + 1, st);
-    if (rc != MLS_OK) return rc;
+    MLS_CUDA_TRY(cudaMemsetAsync(fill, 0, (size_t)(n + 1) * sizeof(int32_t), st));
+    // the bucket offsets: the caller's (counted beside the forward), else here
+    const int32_t *off = offsets;
+    if (!off) {
+        MLS_CUDA_TRY(scratch.alloc(&own_off, (size_t)(n + 1) * sizeof(int32_t)));
+        const int rc = launch_backward_offsets(rows, n, k, own_off, st);
+        if (rc != MLS_OK) return rc;
+        off = own_off;
+    }
     if (state) {
         switch (degree) {
             case 0: launch_point<0, true, true>(pts, n, rows, k, h, precision, order, nullptr, gp, gn, off, fill, rec, self4, hp, blocks, st, state); break;
@@ -671,7 +692,7 @@ int launch_backward_sorted(const float4 *pts, const int32_t *order, int64_t n, c
     k_bucket_sum<kSumLanes, kSumCached><<<(int)std::min<int64_t>((n * kSumLanes + 255) / 256, (int64_t)sms * 32), 256, 0, st>>>(
         n, order, off, rec, self4, grad_xyz);
     k_sum_h<<<1, 1024, 0, st>>>(hp, blocks, grad_h);
-    count_launches(4);   // count, point, bucket sum, sum_h (the scan counts its own)
+    count_launches(3);   // point, bucket sum, sum_h (the offsets count their own)
     MLS_CUDA_TRY(cudaGetLastError());
     return MLS_OK;
 }

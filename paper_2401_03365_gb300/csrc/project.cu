@@ -188,7 +188,7 @@ __global__ void __launch_bounds__(kProjThreads) k_project_fp64(const float *__re
     const double r[3] = {xyz[3 * i], xyz[3 * i + 1], xyz[3 * i + 2]};
     const int32_t *row = idx + i * k;
     const double hd = (double)h, inv_h2 = 1.0 / (hd * hd);
-    double W = 0, m[3] = {0, 0, 0};
+    double W = 0, m[3] = {0, 0, 0}, D2 = 0;
     for (int j = 0; j < k; ++j) {
         const int64_t p = __ldg(row + j);
         double d[3], dd = 0;
@@ -196,6 +196,7 @@ __global__ void __launch_bounds__(kProjThreads) k_project_fp64(const float *__re
             d[a] = (double)__ldg(xyz + 3 * p + a) - r[a];
             dd += d[a] * d[a];
         }
+        D2 = fmax(D2, dd);
         const double w = exp(-dd * inv_h2);
         W += w;
         for (int a = 0; a < 3; ++a) m[a] += w * d[a];
@@ -220,6 +221,7 @@ __global__ void __launch_bounds__(kProjThreads) k_project_fp64(const float *__re
     }
     double nrm[3], e1[3], e2[3], lam[3];
     uint8_t st = (uint8_t)frame_from<double>(C, nrm, e1, e2, lam);
+    if (!(lam[2] > (double)kMinSpread * W * D2)) st = MLS_PT_PLANE_DEGENERATE;
     double out[3] = {r[0], r[1], r[2]};
     if (!st) {
         constexpr int M = Basis<DEG>::M;
@@ -546,6 +548,7 @@ namespace mls {
 int launch_knn_chain_pass(const mls_grid *grid, int k, int32_t *idx, float *key, int32_t *pos, cudaStream_t st);
 int launch_knn_sparse_pass(const mls_grid *grid, int k, int32_t *idx, float *key, int32_t *pos, cudaStream_t st,
                            int blocks_per_sm);
+int launch_backward_offsets(const int32_t *rows, int64_t n, int k, int32_t *off, cudaStream_t st);
 
 namespace {
 
@@ -568,9 +571,11 @@ __global__ void k_mark_sparse(const int *__restrict__ work, uint8_t *__restrict_
 // the points of the sparse pass, and in the mixed form the points that need
 // an FP64 step, are projected from one list.  The same rows and the same
 // per-point arithmetic as mls_knn_sorted followed by mls_project_sorted.
+// With `offsets`, the adjoint's bucket offsets are counted from the finished
+// rows on the side stream too, beside the projection's tail.
 template <int DEG, int PREC, bool STATE>
 int knn_project_pipelined(const mls_grid *g, int k, float h, int32_t *pos, float *out_xyz, float *out_n,
-                          uint8_t *status, float *state, cudaStream_t st) {
+                          uint8_t *status, float *state, int32_t *offsets, cudaStream_t st) {
     const int64_t n = g->n;
     if (!g->side) {
         int least = 0, greatest = 0;
@@ -596,6 +601,10 @@ int knn_project_pipelined(const mls_grid *g, int k, float h, int32_t *pos, float
     // from the start, measured slower: the sparse pass is the longer path)
     rc = launch_knn_sparse_pass(g, k, nullptr, nullptr, pos, g->side, 0);
     if (rc != MLS_OK) return rc;
+    if (offsets) {
+        rc = launch_backward_offsets(pos, n, k, offsets, g->side);
+        if (rc != MLS_OK) return rc;
+    }
     MLS_CUDA_TRY(cudaEventRecord(g->side_ev[1], g->side));
     const int blocks = (int)((n + kProjThreads - 1) / kProjThreads);
     const size_t smem = (size_t)k * kRowStride * sizeof(int32_t) * (kProjThreads / 32);
@@ -614,23 +623,28 @@ int knn_project_pipelined(const mls_grid *g, int k, float h, int32_t *pos, float
 
 template <int PREC, bool STATE>
 int knn_project_deg(const mls_grid *g, int k, float h, int degree, int32_t *pos, float *out_xyz, float *out_n,
-                    uint8_t *status, float *state, cudaStream_t st) {
+                    uint8_t *status, float *state, int32_t *offsets, cudaStream_t st) {
     switch (degree) {
-        case 0: return knn_project_pipelined<0, PREC, STATE>(g, k, h, pos, out_xyz, out_n, status, state, st);
-        case 1: return knn_project_pipelined<1, PREC, STATE>(g, k, h, pos, out_xyz, out_n, status, state, st);
-        default: return knn_project_pipelined<2, PREC, STATE>(g, k, h, pos, out_xyz, out_n, status, state, st);
+        case 0: return knn_project_pipelined<0, PREC, STATE>(g, k, h, pos, out_xyz, out_n, status, state, offsets, st);
+        case 1: return knn_project_pipelined<1, PREC, STATE>(g, k, h, pos, out_xyz, out_n, status, state, offsets, st);
+        default: return knn_project_pipelined<2, PREC, STATE>(g, k, h, pos, out_xyz, out_n, status, state, offsets, st);
     }
 }
 
 }  // namespace
 
 int launch_knn_project_sorted(const mls_grid *g, int k, float h, int degree, int precision, int32_t *pos,
-                              float *out_xyz, float *out_n, uint8_t *status, float *state, cudaStream_t st) {
+                              float *out_xyz, float *out_n, uint8_t *status, float *state, int32_t *offsets,
+                              cudaStream_t st) {
     if (precision == MLS_PREC_FP32)
-        return state ? knn_project_deg<MLS_PREC_FP32, true>(g, k, h, degree, pos, out_xyz, out_n, status, state, st)
-                     : knn_project_deg<MLS_PREC_FP32, false>(g, k, h, degree, pos, out_xyz, out_n, status, state, st);
-    return state ? knn_project_deg<MLS_PREC_MIXED, true>(g, k, h, degree, pos, out_xyz, out_n, status, state, st)
-                 : knn_project_deg<MLS_PREC_MIXED, false>(g, k, h, degree, pos, out_xyz, out_n, status, state, st);
+        return state ? knn_project_deg<MLS_PREC_FP32, true>(g, k, h, degree, pos, out_xyz, out_n, status, state,
+                                                            offsets, st)
+                     : knn_project_deg<MLS_PREC_FP32, false>(g, k, h, degree, pos, out_xyz, out_n, status, state,
+                                                             offsets, st);
+    return state ? knn_project_deg<MLS_PREC_MIXED, true>(g, k, h, degree, pos, out_xyz, out_n, status, state, offsets,
+                                                         st)
+                 : knn_project_deg<MLS_PREC_MIXED, false>(g, k, h, degree, pos, out_xyz, out_n, status, state,
+                                                          offsets, st);
 }
 
 }  // namespace mls

@@ -24,6 +24,12 @@ namespace mls {
 
 constexpr float kMixedGapFlag = 1e-3f;     // FP32 eigensolve trusted above this gap ratio
 constexpr float kMixedCondFlag = 1e5f;     // FP32 Cholesky trusted below this condition estimate
+// A covariance (unnormalised, weights summing to W) whose largest eigenvalue
+// is at most 2^-40 W D^2, D the largest distance from the point to an entry
+// of its row, is a degenerate plane: the neighbours' weights are then
+// negligible beside the point's own, and FP32 does not resolve the plane
+// they would define (eigenvalues near the subnormal range); the point stays.
+constexpr float kMinSpread = 0x1p-40f;
 // Returned instead of a status when DEFER is set and the point needs an FP64
 // step: nothing is computed for it, a later pass runs it without DEFER.
 constexpr uint8_t kDeferFP64 = 0x80;
@@ -65,6 +71,7 @@ __device__ __forceinline__ uint8_t project_point(const float4 *__restrict__ xyz4
     const float neg_scale = -1.4426950408889634f / (h * h);
     uint8_t st = 0;
     float W, mx, my, mz;
+    float D2 = 0.f;                       // the largest squared distance to a row entry
     float e1f[3], e2f[3];
     float lam_s[3] = {0.f, 0.f, 0.f};     // eigenvalues, kept for the state
     // q = r + tq * (qx, qy, qz): the centre of the weights (r unless LEVIN)
@@ -80,12 +87,14 @@ __device__ __forceinline__ uint8_t project_point(const float4 *__restrict__ xyz4
         for (int j = sub; j < k; j += G) {
             const float4 p = __ldg(xyz4 + row(j));
             const float dx = p.x - rx, dy = p.y - ry, dz = p.z - rz;
+            const float dd = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+            D2 = fmaxf(D2, dd);
             float w;
             if (LEVIN) {
                 const float ax = fmaf(-tq, qx, dx), ay = fmaf(-tq, qy, dy), az = fmaf(-tq, qz, dz);
                 w = exp2f(fmaf(ax, ax, fmaf(ay, ay, az * az)) * neg_scale);
             } else {
-                w = exp2f(fmaf(dx, dx, fmaf(dy, dy, dz * dz)) * neg_scale);
+                w = exp2f(dd * neg_scale);
             }
             const float Wn = W + w;
             const float c = Wn > 0.f ? __fdividef(w, Wn) : 0.f;
@@ -104,6 +113,7 @@ __device__ __forceinline__ uint8_t project_point(const float4 *__restrict__ xyz4
             W = Wn;
         }
         for (int s = 1; s < G; s <<= 1) {
+            D2 = fmaxf(D2, __shfl_xor_sync(0xffffffffu, D2, s));
             const float Wo = __shfl_xor_sync(0xffffffffu, W, s);
             const float mox = __shfl_xor_sync(0xffffffffu, mx, s);
             const float moy = __shfl_xor_sync(0xffffffffu, my, s);
@@ -153,10 +163,12 @@ __device__ __forceinline__ uint8_t project_point(const float4 *__restrict__ xyz4
                     nf[a] = (float)nd[a];
                     e1f[a] = (float)e1d[a];
                     e2f[a] = (float)e2d[a];
+                    lam[a] = (float)ld[a];
                     if (STATE) lam_s[a] = (float)ld[a];
                 }
                 st |= MLS_PT_FP64_USED;
             }
+            if (!(lam[2] > kMinSpread * W * D2)) deg_flag = MLS_PT_PLANE_DEGENERATE;
             st = (uint8_t)((st & ~MLS_PT_PLANE_DEGENERATE) | deg_flag);
         }
         if (!LEVIN || (st & MLS_PT_PLANE_DEGENERATE)) break;

@@ -112,3 +112,30 @@ def test_pipelined_argument_errors(capi):
         assert e.value.code == code
     torch.cuda.synchronize()
     grid.close()
+
+
+@pytest.mark.parametrize("precision", ["mixed", "fp32"])
+def test_offsets_from_the_pipelined_call(capi, precision):
+    """The adjoint's bucket offsets counted beside the forward: the gradients
+    (coordinates and h) equal those of the adjoint counting its own, bit for
+    bit, with and without the fit state."""
+    c = workloads.torus(n=150_000, seed=61)
+    x = torch.from_numpy(c.xyz).cuda()
+    grid = capi.mls_build_grid(x, 0.0, c.k)
+    off = torch.empty(c.n + 1, dtype=torch.int32, device="cuda")
+    pos, _, _, _, state = capi.mls_knn_project_sorted(grid, c.k, 0.012, 2, precision, with_state=True,
+                                                      out_offsets=off)
+    gen = torch.Generator(device="cuda").manual_seed(62)
+    gp = torch.randn(c.n, 3, device="cuda", generator=gen)
+    gn = 0.1 * torch.randn(c.n, 3, device="cuda", generator=gen)
+    for st in (state, None):
+        a, ah = capi.mls_project_backward_sorted(grid, pos, 0.012, gp, gn, 2, precision, state=st, offsets=off)
+        b, bh = capi.mls_project_backward_sorted(grid, pos, 0.012, gp, gn, 2, precision, state=st)
+        assert torch.equal(a, b) and torch.equal(ah, bh)
+    # the offsets are the exclusive prefix of the reverse degrees
+    deg = torch.bincount(pos.reshape(-1).long(), minlength=c.n)
+    ref = torch.zeros(c.n + 1, dtype=torch.int64, device="cuda")
+    ref[1:] = torch.cumsum(deg, 0)
+    torch.cuda.synchronize()
+    grid.close()
+    assert torch.equal(off.long(), ref)

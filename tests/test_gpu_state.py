@@ -166,3 +166,33 @@ def test_state_argument_checks(capi):
                                          state=torch.zeros((capi.FIT_STATE_FLOATS, c.n - 1), device="cuda"))
     torch.cuda.synchronize()
     grid.close()
+
+
+@pytest.mark.parametrize("precision", ["mixed", "fp32"])
+def test_bandwidth_below_the_spacing_gives_finite_gradients(capi, precision):
+    """h below the point spacing (a 150k torus at h = 0.012): outliers whose
+    neighbours all lie many h away get negligible weights, and reading R9
+    makes their planes degenerate (status bit 1 wherever the oracle's
+    normalised covariance is at most 2^-40 D^2, D the largest distance from
+    the point to a row entry).  Every gradient is finite,
+    from the saved state and recomputed, with both cotangents."""
+    c = workloads.torus(n=150_000, seed=61)
+    x, grid, pos, idx, order = _grid(capi, c.xyz, c.k)
+    h = 0.012
+    _, _, st, state = capi.mls_project_sorted(grid, pos, h, 2, precision, with_state=True)
+    gen = torch.Generator(device="cuda").manual_seed(62)
+    gp = torch.randn(c.n, 3, device="cuda", generator=gen)
+    gn = 0.1 * torch.randn(c.n, 3, device="cuda", generator=gen)
+    a, ah = capi.mls_project_backward_sorted(grid, pos, h, gp, gn, 2, precision, state=state)
+    b, bh = capi.mls_project_backward_sorted(grid, pos, h, gp, gn, 2, precision)
+    torch.cuda.synchronize()
+    grid.close()
+    for g in (a, ah, b, bh):
+        assert bool(torch.isfinite(g).all())
+    rows = idx.cpu().numpy()
+    diag = oracle.project(c.xyz, rows, h, 2)[3]
+    x64 = c.xyz.astype(np.float64)
+    D2 = ((x64[rows] - x64[:, None, :]) ** 2).sum(2).max(1)
+    r9 = diag[:, 2] <= 2.0 ** -40 * D2
+    assert r9.sum() > 10
+    assert np.all(st.cpu().numpy()[r9] & 1)

@@ -442,3 +442,31 @@ def test_adjoint_term_norms():
     assert np.all(a_all >= np.linalg.norm(g_all, axis=1) * (1 - 1e-12))
     g_plain, _ = oracle.project_grad(c.xyz, idx, 0.1, 2, gp, gn)
     assert np.array_equal(g_plain, g_all)
+
+
+def test_negligible_neighbour_weights_make_a_degenerate_plane():
+    """Reading R9: when every neighbour lies many h from the point, their
+    Gaussian weights vanish beside the point's own and the weighted
+    covariance (normalised by W) falls below 2^-40 D^2 (D the largest
+    distance from the point to a row entry): the plane is degenerate and the
+    point stays exactly where it is.  The same neighbours 2 h away, or at any
+    distance with h far above it (every weight 1), give a regular plane."""
+    rng = np.random.default_rng(17)
+    h = 0.01
+    for dist, hh, degenerate in ((10 * h, h, True), (2 * h, h, False), (10 * h, 1e5, False)):
+        u = rng.standard_normal((15, 2))
+        u *= dist / np.linalg.norm(u, axis=1, keepdims=True)
+        nb = np.concatenate([u, 0.02 * dist * rng.standard_normal((15, 1))], axis=1)
+        xyz = np.concatenate([np.zeros((1, 3)), nb]).astype(np.float32)
+        rows = np.arange(16, dtype=np.int32)[None, :]
+        out, nrm, st, diag = oracle.project(xyz, rows, hh, 0, queries=np.array([0]))
+        lam_max = diag[0, 2]
+        D2 = (xyz.astype(np.float64) ** 2).sum(1).max()
+        if degenerate:
+            assert st[0] == oracle.STATUS_PLANE_DEGENERATE
+            assert lam_max <= 2.0 ** -40 * D2
+            assert np.array_equal(out[0], xyz[0].astype(np.float64))
+        else:
+            assert st[0] & oracle.STATUS_PLANE_DEGENERATE == 0
+            assert lam_max > 1e-6 * D2
+            assert abs(abs(nrm[0, 2]) - 1.0) < 1e-2      # the neighbours' plane, z nearly normal

@@ -122,9 +122,9 @@ __global__ void k_frame(Misc *m) {
 }
 
 // Sort keys: the Hilbert index of each point's level-0 cell, or, for a build
-// that sorts only the levels from `level` up, the index of its level-`level`
-// cell on the coarser curve shifted into place (the same top bits, the bits
-// below zero: points within such a cell keep their input order).
+// whose radix passes read only the key bits from 3 `level` up, the index of
+// its level-`level` cell on the coarser curve shifted into place: the same
+// bits there (the bits below are zero and not read), so the same order.
 __global__ void k_keys(const float *__restrict__ xyz, int64_t n, const Misc *__restrict__ m, int level,
                        uint64_t *__restrict__ keys, int32_t *__restrict__ perm) {
     GridFrame f = m->frame;
@@ -516,9 +516,10 @@ int build_grid(mls_grid *g, const float *xyz, int64_t n, float cell_size, int k_
         // their width allows: the extra low bits order points within the cells
         // more finely at no cost)
         const int passes = (kKeyBits - 3 * sort_level + kDigitBits - 1) / kDigitBits;
-        k_keys<<<blocks_for(n, T), T, 0, st>>>(xyz, n, m, sort_level, g->keys, g->perm);
+        const int lo_shift = std::max(0, kKeyBits - kDigitBits * passes);     // lowest key bit the passes read
+        k_keys<<<blocks_for(n, T), T, 0, st>>>(xyz, n, m, lo_shift / 3, g->keys, g->perm);
         count_launches(1);
-        for (int shift = std::max(0, kKeyBits - kDigitBits * passes); shift < kKeyBits; shift += kDigitBits) {
+        for (int shift = lo_shift; shift < kKeyBits; shift += kDigitBits) {
             k_radix_hist<<<nblocks, kSortThreads, 0, st>>>(g->keys, n, shift, nblocks, g->block_hist);
             k_radix_scan<<<kDigits, 1024, 0, st>>>(g->block_hist, nblocks, g->scan_tmp);
             k_radix_scatter<<<nblocks, kSortThreads, 0, st>>>(g->keys, g->perm, n, shift, nblocks, g->block_hist,

@@ -33,6 +33,10 @@
  *     work is queued; no entry point aborts, throws or traps.
  *   - Return value: MLS_OK (0) or a negative mls_status_code;
  *     mls_last_error() gives a message for the calling thread's last failure.
+ *   - A grid handle holds per-call work space (the kNN's queue and lists, the
+ *     pipelined call's side stream): calls on one handle must be ordered on
+ *     one stream (or otherwise serialised), never issued from two threads or
+ *     two unordered streams at once; different handles are independent.
  */
 #ifndef MLS_H_
 #define MLS_H_

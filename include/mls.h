@@ -21,7 +21,10 @@
  *                   its largest-magnitude component is positive;
  *   polynomial      full bivariate basis of degree 0, 1 or 2 in local
  *                   coordinates (u, v) / h; heights unscaled;
- *   degenerate      (l1 - l0) <= 1e-6 l2 or l2 == 0: output r, status bit 1;
+ *   degenerate      (l1 - l0) <= 1e-6 l2, or l2 <= 2^-40 D^2 (covariance
+ *                   normalised by the weight sum, D the largest distance from
+ *                   the point to a row entry: the neighbours' weights are
+ *                   negligible beside its own): output r, status bit 1;
  *   singular        a Cholesky pivot <= 1e-12 trace of the normal matrix:
  *                   output q, status bit 2.
  *

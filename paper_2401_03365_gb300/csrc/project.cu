@@ -592,6 +592,11 @@ int knn_project_pipelined(const mls_grid *g, int k, float h, int32_t *pos, float
     int32_t *count = list + n;
     MLS_CUDA_TRY(cudaMemsetAsync(skip, 0, (size_t)n, st));
     MLS_CUDA_TRY(cudaMemsetAsync(count, 0, sizeof(int32_t), st));
+    const int blocks = (int)((n + kProjThreads - 1) / kProjThreads);
+    const size_t smem = (size_t)k * kRowStride * sizeof(int32_t) * (kProjThreads / 32);
+    constexpr bool DEFER = PREC == MLS_PREC_MIXED;
+    auto kern = k_project<DEG, PREC, false, DEFER, true, STATE, true>;
+    MLS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int rc = launch_knn_chain_pass(g, k, nullptr, nullptr, pos, st);
     if (rc != MLS_OK) return rc;
     k_mark_sparse<<<sm_count(), 256, 0, st>>>(g->work, skip, list, count);
@@ -600,17 +605,12 @@ int knn_project_pipelined(const mls_grid *g, int k, float h, int32_t *pos, float
     // a full wave of sparse blocks (fewer, leaving room for the projection
     // from the start, measured slower: the sparse pass is the longer path)
     rc = launch_knn_sparse_pass(g, k, nullptr, nullptr, pos, g->side, 0);
-    if (rc != MLS_OK) return rc;
-    if (offsets) {
-        rc = launch_backward_offsets(pos, n, k, offsets, g->side);
-        if (rc != MLS_OK) return rc;
-    }
+    if (rc == MLS_OK && offsets) rc = launch_backward_offsets(pos, n, k, offsets, g->side);
     MLS_CUDA_TRY(cudaEventRecord(g->side_ev[1], g->side));
-    const int blocks = (int)((n + kProjThreads - 1) / kProjThreads);
-    const size_t smem = (size_t)k * kRowStride * sizeof(int32_t) * (kProjThreads / 32);
-    constexpr bool DEFER = PREC == MLS_PREC_MIXED;
-    auto kern = k_project<DEG, PREC, false, DEFER, true, STATE, true>;
-    MLS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    if (rc != MLS_OK) {     // the caller's stream still waits for what went to the side stream
+        cudaStreamWaitEvent(st, g->side_ev[1], 0);
+        return rc;
+    }
     kern<<<blocks, kProjThreads, smem, st>>>(g->view.pts, n, pos, k, h, nullptr, out_xyz, out_n, status, 1, 0.f,
                                              list, count, state, skip);
     MLS_CUDA_TRY(cudaStreamWaitEvent(st, g->side_ev[1], 0));

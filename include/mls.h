@@ -155,6 +155,8 @@ const int32_t *mls_grid_order(const mls_grid *g);
  *           index, ascending by (key, index); bit-exact and deterministic
  *   d_key   device, n x k floats or NULL: the matching keys
  *   k       1 <= k <= min(MLS_MAX_K, n)
+ * Scratch: from 2^18 points, 5 n + 32 bytes (the queries alone in a cell two
+ * base cells wide, searched first, and their flags).
  */
 int mls_knn(const mls_grid *g, int k, int32_t *d_idx, float *d_key, mls_stream stream);
 
@@ -167,6 +169,7 @@ int mls_knn(const mls_grid *g, int k, int32_t *d_idx, float *d_key, mls_stream s
  *   d_idx   device, n x k int32 or NULL: also the rows of mls_knn (original
  *           indexing, row = original index)
  *   d_key   device, n x k floats or NULL: the keys, in d_idx's layout
+ * Scratch: as mls_knn.
  */
 int mls_knn_sorted(const mls_grid *g, int k, int32_t *d_pos, int32_t *d_idx, float *d_key, mls_stream stream);
 
@@ -217,12 +220,14 @@ int mls_knn_project(const mls_grid *g, int k, float h, int degree, int precision
  * mls_knn_project_sorted -- mls_knn_sorted followed by mls_project_sorted (the
  * neighbourhoods of Algorithm 1 and the projection of Sec. 1.4, Eq. 1 over
  * them), pipelined: once the kNN's first pass has written the rows of all but
- * the queries in sparse neighbourhoods, the projection of those points runs
- * on a low-priority stream of the grid's own, beside the kNN's second pass;
- * the points of the second pass are projected after it.  Outputs (d_pos and
- * the projection's, d_state included) equal those of the two calls bit for
- * bit.  Arguments as mls_knn_sorted (d_pos required) and mls_project_sorted.
- * Scratch: 5 n bytes.  The grid's side stream and two events are created on
+ * the queries in sparse neighbourhoods, the kNN's second pass runs on a
+ * high-priority stream of the grid's own while the projection of the other
+ * points runs on `stream` beside it; the points of the second pass, and the
+ * isolated queries the first pass took before its runs, are projected after
+ * it.  Outputs (d_pos and the projection's, d_state included) equal those of
+ * the two calls bit for bit.  Arguments as mls_knn_sorted (d_pos required)
+ * and mls_project_sorted.
+ * Scratch: 9 n + 32 bytes.  The grid's side stream and two events are created on
  * the first call and destroyed with the grid; `stream` waits for the side
  * stream before the call's last kernel, so the call is ordered on `stream`
  * like any other.
@@ -237,10 +242,12 @@ int mls_knn_project_sorted(const mls_grid *g, int k, float h, int degree, int pr
                            float *d_out_xyz, float *d_out_normal, uint8_t *d_status, float *d_state,
                            int32_t *d_offsets, mls_stream stream);
 
-/* Number of queries the last mls_knn call on this grid handed to its second
- * pass (queries whose first key bound needs a cube above the base level:
- * outliers, sparse regions); a measure of the work, never of the result.
- * Synchronises `stream` (the kNN's stream).  Negative: an error code. */
+/* Number of queries the last kNN call on this grid searched outside the runs
+ * of consecutive queries: the isolated ones (alone in a cell two base cells
+ * wide), taken first, and those handed to its second pass (whose first key
+ * bound needs a cube above the base level: outliers, sparse regions); a
+ * measure of the work, never of the result.  Synchronises `stream` (the
+ * kNN's stream).  Negative: an error code. */
 int64_t mls_knn_deferred(const mls_grid *g, mls_stream stream);
 
 /*

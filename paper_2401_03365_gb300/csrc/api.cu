@@ -285,11 +285,11 @@ int mls_knn_project_sorted(const mls_grid *g, int k, float h, int degree, int pr
 int64_t mls_knn_deferred(const mls_grid *g, mls_stream stream) {
     mls::g_last_error[0] = 0;
     if (!g || !g->work) return set_error(MLS_ERR_INVALID_ARG, "mls_knn_deferred: no kNN on this grid");
-    int count = 0;
+    int head[4] = {0, 0, 0, 0};
     cudaStream_t st = (cudaStream_t)stream;
-    MLS_CUDA_TRY(cudaMemcpyAsync(&count, g->work + 1, sizeof(int), cudaMemcpyDeviceToHost, st));
+    MLS_CUDA_TRY(cudaMemcpyAsync(head, g->work, sizeof(head), cudaMemcpyDeviceToHost, st));
     MLS_CUDA_TRY(cudaStreamSynchronize(st));
-    return count;
+    return (int64_t)head[1] + head[3];     // handed to the second pass + isolated
 }
 
 int mls_project(const float *d_xyz, int64_t n, const int32_t *d_idx, int k, float h, int degree, int precision,

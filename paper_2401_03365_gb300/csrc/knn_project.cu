@@ -182,7 +182,7 @@ int launch_fused(const mls_grid *grid, int k, float h, float *out_xyz, float *ou
     MLS_CUDA_TRY(cudaMemsetAsync(grid->work, 0, 8 * sizeof(int), st));
     const RowOut out{nullptr, nullptr, pos};
     const Fin fin{grid->view.pts, bat, k, h, out_xyz, out_n, status, def};
-    chain<<<chain_blocks, kChainThreads, 0, st>>>(grid->view, k, grid->work, out, fin);
+    chain<<<chain_blocks, kChainThreads, 0, st>>>(grid->view, k, grid->work, out, fin, nullptr, nullptr);
     sparse<<<sparse_blocks, kChainThreads, 0, st>>>(grid->view, k, grid->work, out, fin);
     count_launches(2);
     if (PREC == MLS_PREC_MIXED) {

@@ -731,10 +731,19 @@ struct PlainRows {
     __device__ __forceinline__ void finish(int) {}
 };
 
-template <int KPL, class Fin>
+// SKIP: the queries flagged in skip[] are listed in iso (the work-list
+// layout: count iso[1], next iso[2], sorted positions from iso[8]).  Every
+// warp takes them first, one at a time, each searched in full (never
+// deferred), and then the runs of the queue, stepping over the flagged
+// queries (the chain's bounds hold between any two queries).  The listed
+// queries are the costly ones: taken first by all warps, the longest of them
+// end well before the queue does.
+template <int KPL, class Fin, bool SKIP = false>
 __global__ void __launch_bounds__(kChainThreads, Fin::kBlocksPerSm) k_knn_chain(GridView g, int k,
                                                                                 int *__restrict__ work, RowOut out,
-                                                                                Fin fin) {
+                                                                                Fin fin,
+                                                                                const uint8_t *__restrict__ skip,
+                                                                                int *__restrict__ iso) {
     __shared__ WarpBuf bufs[kChainWarps];
     const int lane = threadIdx.x & 31;
     WarpBuf &wb = bufs[threadIdx.x >> 5];
@@ -745,18 +754,31 @@ __global__ void __launch_bounds__(kChainThreads, Fin::kBlocksPerSm) k_knn_chain(
     cb.st = wb.cube_start + lane;
     cb.ct = wb.cube_count + lane;
     fin.start((blockIdx.x * (int64_t)kChainThreads + threadIdx.x) >> 5, lane);
+    const int n_iso = SKIP ? iso[1] : 0;
+    bool from_iso = SKIP && n_iso > 0;
     for (;;) {
-        // run length from a racy read of the queue: any length is correct,
-        // since every run is reserved by its own atomic add
         long long first = 0, len = 0;
-        if (lane == 0) {
-            const long long left = g.n - (long long)*(volatile unsigned long long *)next_query;
-            len = min((long long)kChunk, max((long long)kMinChunk, left / (2 * n_warps)));
-            first = (long long)atomicAdd(next_query, (unsigned long long)len);
+        if (from_iso) {
+            const int i = warp_take(&iso[2], lane);
+            if (i < n_iso) {
+                first = iso[8 + i];
+                len = 1;
+            } else {
+                from_iso = false;
+            }
         }
-        first = __shfl_sync(kFull, first, 0);
-        len = __shfl_sync(kFull, len, 0);
-        if (first >= g.n) break;
+        if (!from_iso) {
+            // run length from a racy read of the queue: any length is
+            // correct, since every run is reserved by its own atomic add
+            if (lane == 0) {
+                const long long left = g.n - (long long)*(volatile unsigned long long *)next_query;
+                len = min((long long)kChunk, max((long long)kMinChunk, left / (2 * n_warps)));
+                first = (long long)atomicAdd(next_query, (unsigned long long)len);
+            }
+            first = __shfl_sync(kFull, first, 0);
+            len = __shfl_sync(kFull, len, 0);
+            if (first >= g.n) break;
+        }
         // the previous query (its kept points in wb, k-th key k1, position
         // p1) and the one before it (position p2, k-th key k2)
         int n_prev = 0;
@@ -764,6 +786,7 @@ __global__ void __launch_bounds__(kChainThreads, Fin::kBlocksPerSm) k_knn_chain(
         float k1 = 0.f, k2 = 0.f;
         const int64_t end = min((int64_t)g.n, (int64_t)(first + len));
         for (int64_t sp = first; sp < end; ++sp) {
+            if (SKIP && !from_iso && __ldg(skip + sp)) continue;
             const float4 q = __ldg(g.pts + sp);
             const uint64_t key0 = __ldg(g.keys + sp);
             const uint32_t c0[3] = {compact3(key0), compact3(key0 >> 1), compact3(key0 >> 2)};
@@ -773,7 +796,7 @@ __global__ void __launch_bounds__(kChainThreads, Fin::kBlocksPerSm) k_knn_chain(
             // a bound far above the previous query's, or reaching past four
             // base cells, would search a large region: start afresh instead
             if (n_prev == 0 || tau > 9.0f * k1 || tau > big) tau = INFINITY;
-            const float kth = solve_query<KPL, 1>(g, wb, cb, q, __float_as_int(q.w), sp, c0, tau, k, lane, true,
+            const float kth = solve_query<KPL, 1>(g, wb, cb, q, __float_as_int(q.w), sp, c0, tau, k, lane, !from_iso,
                                                   fin.rows(out));
             if (isnan(kth)) {
                 if (lane == 0) work[8 + atomicAdd(&work[1], 1)] = (int)sp;

@@ -545,9 +545,13 @@ extern "C" int mls_project_noalloc(const float *d_xyz, int64_t n, const int32_t 
 
 namespace mls {
 
-int launch_knn_chain_pass(const mls_grid *grid, int k, int32_t *idx, float *key, int32_t *pos, cudaStream_t st);
+int launch_knn_chain_pass(const mls_grid *grid, int k, int32_t *idx, float *key, int32_t *pos, cudaStream_t st,
+                          const uint8_t *skip, int *iso, int blocks_per_sm, bool reset);
 int launch_knn_sparse_pass(const mls_grid *grid, int k, int32_t *idx, float *key, int32_t *pos, cudaStream_t st,
                            int blocks_per_sm);
+int launch_knn_isolated(const mls_grid *grid, uint8_t *skip, int *iso, int32_t *list, int32_t *count,
+                        cudaStream_t st);
+bool knn_isolates(const mls_grid *grid);
 int launch_backward_offsets(const int32_t *rows, int64_t n, int k, int32_t *off, cudaStream_t st);
 
 namespace {
@@ -564,15 +568,19 @@ __global__ void k_mark_sparse(const int *__restrict__ work, uint8_t *__restrict_
     }
 }
 
-// The kNN and the projection, pipelined: after the chain pass, the kNN's
-// sparse pass (whose tail leaves most of the GPU idle) runs on a
-// high-priority stream of the grid's own while the projection of every point
-// whose row the chain pass wrote runs on the caller's stream beside it; then
-// the points of the sparse pass, and in the mixed form the points that need
-// an FP64 step, are projected from one list.  The same rows and the same
-// per-point arithmetic as mls_knn_sorted followed by mls_project_sorted.
-// With `offsets`, the adjoint's bucket offsets are counted from the finished
-// rows on the side stream too, beside the projection's tail.
+// The kNN and the projection, pipelined, on the caller's stream and a
+// high-priority stream of the grid's own.  From a few hundred thousand
+// points, the isolated queries (outliers alone in a cell two base cells wide,
+// whose searches climb to coarse levels and scan many points) are listed
+// first; the chain pass's warps take them before their runs, so that their
+// long searches end under the chain pass instead of after it.  Then the sparse pass over the queries the chain pass
+// left runs on the side stream while the projection of every point whose row
+// the chain pass wrote runs on the caller's stream beside it; last, the
+// isolated and sparse points, and in the mixed form the points that need an
+// FP64 step, are projected from one list.  The same rows and the same per-point arithmetic
+// as mls_knn_sorted followed by mls_project_sorted.  With `offsets`, the
+// adjoint's bucket offsets are counted from the finished rows on the side
+// stream too, beside the projection's tail.
 template <int DEG, int PREC, bool STATE>
 int knn_project_pipelined(const mls_grid *g, int k, float h, int32_t *pos, float *out_xyz, float *out_n,
                           uint8_t *status, float *state, int32_t *offsets, cudaStream_t st) {
@@ -587,17 +595,23 @@ int knn_project_pipelined(const mls_grid *g, int k, float h, int32_t *pos, float
     ScratchSet scratch(st);     // freed on st, after it has waited for the side stream
     uint8_t *skip = nullptr;
     int32_t *list = nullptr;
+    int *iso = nullptr;         // the isolated queries, in the kNN's work-list layout
+    const bool isolate = knn_isolates(g);
     MLS_CUDA_TRY(scratch.alloc(&skip, (size_t)n));
     MLS_CUDA_TRY(scratch.alloc(&list, (size_t)(n + 1) * sizeof(int32_t)));
+    if (isolate) MLS_CUDA_TRY(scratch.alloc(&iso, (size_t)(n + 8) * sizeof(int)));
     int32_t *count = list + n;
-    MLS_CUDA_TRY(cudaMemsetAsync(skip, 0, (size_t)n, st));
+    if (!isolate) MLS_CUDA_TRY(cudaMemsetAsync(skip, 0, (size_t)n, st));
     MLS_CUDA_TRY(cudaMemsetAsync(count, 0, sizeof(int32_t), st));
     const int blocks = (int)((n + kProjThreads - 1) / kProjThreads);
     const size_t smem = (size_t)k * kRowStride * sizeof(int32_t) * (kProjThreads / 32);
     constexpr bool DEFER = PREC == MLS_PREC_MIXED;
     auto kern = k_project<DEG, PREC, false, DEFER, true, STATE, true>;
     MLS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    int rc = launch_knn_chain_pass(g, k, nullptr, nullptr, pos, st);
+    int rc = isolate ? launch_knn_isolated(g, skip, iso, list, count, st) : MLS_OK;
+    if (rc == MLS_OK)
+        rc = isolate ? launch_knn_chain_pass(g, k, nullptr, nullptr, pos, st, skip, iso, 0, false)
+                     : launch_knn_chain_pass(g, k, nullptr, nullptr, pos, st, nullptr, nullptr, 0, true);
     if (rc != MLS_OK) return rc;
     k_mark_sparse<<<sm_count(), 256, 0, st>>>(g->work, skip, list, count);
     MLS_CUDA_TRY(cudaEventRecord(g->side_ev[0], st));

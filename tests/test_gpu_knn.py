@@ -121,3 +121,44 @@ def test_knn_independent_of_cell_size(capi, cell_size):
     grid.close()
     idx_o, _ = oracle.knn_kdtree(xyz, k)
     assert np.array_equal(idx.cpu().numpy(), idx_o)
+
+
+def test_isolated_queries(capi):
+    """From 2^18 points, queries alone in a cell two base cells wide are taken
+    first by the chain pass and searched in full: a 300,000-point torus with
+    1 % outliers, plus single outliers far away and pairs of outliers that
+    share a cell (those go through the chain's own deferral).  Every row and
+    key equals the oracle's, rows of sorted positions included, and the kNN
+    reports at least the planted far outliers as searched outside the runs."""
+    from paper_2401_03365_gb300 import workloads
+    rng = np.random.default_rng(101)
+    c = workloads.torus(n=300_000, seed=100)
+    far = rng.uniform(-1, 1, (30, 3)) * np.array([6.0, 6.0, 3.0]) + np.array([0.0, 0.0, 4.0])
+    pairs = np.repeat(rng.uniform(-1, 1, (10, 3)) * 3.0 + np.array([0.0, 0.0, -4.0]), 2, axis=0)
+    pairs[1::2] += 1e-4
+    xyz = np.concatenate([c.xyz, far, pairs]).astype(np.float32)
+    k = 32
+    idx_o, key_o = oracle.knn_kdtree(xyz, k)
+    x = torch.from_numpy(xyz).cuda()
+    grid = capi.mls_build_grid(x, 0.0, k)
+    idx_g, key_g = capi.mls_knn(grid, k, with_key=True)
+    searched = capi.mls_knn_deferred(grid)
+    pos, idx_s, _ = capi.mls_knn_sorted(grid, k, with_idx=True)
+    order = capi.mls_grid_order(grid).cpu().numpy()
+    torch.cuda.synchronize()
+    grid.close()
+    assert np.array_equal(idx_g.cpu().numpy(), idx_o)
+    assert np.array_equal(key_g.cpu().numpy().view(np.uint32), key_o.view(np.uint32))
+    assert np.array_equal(idx_s.cpu().numpy(), idx_o)
+    p = pos.cpu().numpy()
+    rows = np.empty_like(p)
+    rows[order] = order[p]
+    assert np.array_equal(rows, idx_o)
+    assert searched >= far.shape[0]
+
+
+def test_single_point(capi):
+    """n = k = 1: the one point is alone in every cell; its row is itself."""
+    xyz = np.array([[0.25, -1.5, 3.0]], np.float32)
+    idx, key, order = _gpu_knn(capi, xyz, 1)
+    assert idx.tolist() == [[0]] and key.tolist() == [[0.0]] and order.tolist() == [0]

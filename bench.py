@@ -90,7 +90,7 @@ KNN_MEASURED = {
     "sources": {
         "paper_2401_03365_gb300/csrc/knn_search.cuh": "099d6dc317972f78b50cf17229b5ec1e84de938d472e928d351505d9238b5ee9",
         "paper_2401_03365_gb300/csrc/knn.cu": "ad1382bae4762e19f8d9c33ebd51971c9fb2e239bbb303fd01147bf1f4891d35",
-        "paper_2401_03365_gb300/csrc/grid.cuh": "4f98a36f90915aae6e8e9e41d65b1487a25981288b3898fba6e5a6daac0002a4",
+        "paper_2401_03365_gb300/csrc/grid.cuh": "560013b7ab7f99966e1993aaaeb0c1a1733ec5389faaaa2bc0604f6aafc0ffcc",
         "paper_2401_03365_gb300/csrc/common.cuh": "9d6ac0dc2ad528cdc5d1d35b34889db2a24ebc7196733e8c248a68ed29f7d816",
     },
 }

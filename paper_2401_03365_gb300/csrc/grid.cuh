@@ -87,7 +87,7 @@ struct mls_grid {
     // level (the cells finer than it are never searched): one level below
     // the base level of the last build; 0 (the whole key) at first.
     int sort_level = 0;
-    // side stream (low priority) and events of the pipelined kNN and
+    // side stream (high priority) and events of the pipelined kNN and
     // projection, created on first use
     mutable cudaStream_t side = nullptr;
     mutable cudaEvent_t side_ev[2] = {nullptr, nullptr};

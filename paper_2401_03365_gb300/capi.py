@@ -386,8 +386,9 @@ def mls_points_in_boxes(grid: Grid, boxes: torch.Tensor, out_mask=None, stream=N
 
 
 def mls_knn_deferred(grid: Grid, stream=None) -> int:
-    """Queries the last kNN call on `grid` handed to its second (sparse)
-    pass (synchronises the stream)."""
+    """Queries the last kNN call on `grid` searched outside its runs of
+    consecutive queries: the isolated ones taken first and those handed to
+    its second (sparse) pass (synchronises the stream)."""
     v = int(lib().mls_knn_deferred(grid.handle, _stream(stream)))
     if v < 0:
         _check("mls_knn_deferred", v)
